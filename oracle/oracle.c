@@ -1,0 +1,476 @@
+/*
+ * CPU oracle (test infrastructure only; see oracle.h). Plain sequential C.
+ *
+ * Every function cites the passage of the ABMax paper (arXiv 2508.16508) it
+ * restates. Where the paper is silent, the reading used is written beside the
+ * code; the same readings are listed in the design doc.
+ */
+#include "oracle.h"
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10, from the definition in Salmon et al., "Parallel random
+ * numbers: as easy as 1, 2, 3" (SC'11): ten rounds of two 32x32->64 products
+ * whose halves are xored into the other counter words together with the key;
+ * the key is advanced by the Weyl constants between rounds. */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; round++) {
+    uint64_t prod0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+    uint64_t prod1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+    uint32_t n0 = (uint32_t)(prod1 >> 32) ^ c1 ^ k0;
+    uint32_t n1 = (uint32_t)prod1;
+    uint32_t n2 = (uint32_t)(prod0 >> 32) ^ c3 ^ k1;
+    uint32_t n3 = (uint32_t)prod0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+static uint32_t draw(uint32_t seed, uint32_t model, uint32_t step, uint32_t slot,
+                     uint32_t purpose, uint32_t species, int word) {
+  uint32_t ctr[4] = {step, slot, purpose, species};
+  uint32_t key[2] = {seed, model};
+  uint32_t out[4];
+  orc_philox4x32_10(ctr, key, out);
+  return out[word];
+}
+
+void orc_philox_words(uint32_t seed, uint32_t model, uint32_t step, uint32_t purpose,
+                      uint32_t species, uint32_t slot0, int64_t n, int word, uint32_t* out) {
+  for (int64_t i = 0; i < n; i++)
+    out[i] = draw(seed, model, step, slot0 + (uint32_t)i, purpose, species, word);
+}
+
+/* uniform integer in [0, n): multiply-shift of a 32-bit draw */
+static int32_t uniform_below(uint32_t u, int32_t n) {
+  return (int32_t)(((uint64_t)u * (uint64_t)(uint32_t)n) >> 32);
+}
+
+/* ------------------------------------------------------------------------ */
+/* select_agents (Section 2): indices of the selected agents, in ascending
+ * order -- the "true first, stable" permutation's front part. */
+int64_t orc_flatnonzero(const int32_t* mask, int64_t n, int32_t* out_idx) {
+  int64_t c = 0;
+  for (int64_t i = 0; i < n; i++)
+    if (mask[i]) out_idx[c++] = (int32_t)i;
+  return c;
+}
+
+/* Sort-Count-Iterate (Algorithm 2): r = min of the two selection counts;
+ * the i-th selected target receives the i-th selected update. Rank-Match
+ * (Algorithm 1) computes the same result (reading: ranks match only when
+ * both are nonzero). */
+int64_t orc_assign_ranked(int32_t* a, const int32_t* mask_a, int64_t n,
+                          const int32_t* b, const int32_t* mask_b, int64_t m) {
+  int32_t* ia = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  int32_t* ib = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+  int64_t na = orc_flatnonzero(mask_a, n, ia);
+  int64_t nb = orc_flatnonzero(mask_b, m, ib);
+  int64_t r = na < nb ? na : nb;
+  for (int64_t i = 0; i < r; i++) a[ia[i]] = b[ib[i]];
+  free(ia);
+  free(ib);
+  return r;
+}
+
+/* set_agents_mask (Section 2): independent masked change -- here, removal of
+ * the masked live agents (they become placeholders, Section 4). */
+int64_t orc_remove(int32_t* active, const int32_t* mask, int64_t n) {
+  int64_t removed = 0;
+  for (int64_t i = 0; i < n; i++) {
+    if (active[i] && mask[i]) {
+      active[i] = 0;
+      removed++;
+    }
+  }
+  return removed;
+}
+
+/* Adding agents with distinct initial states (Section 4 toy task, with the
+ * free placeholder slots as targets): record j goes to the j-th free slot in
+ * ascending order, j < r = min(k, #free). id_field >= 0 stamps id_base + j. */
+int64_t orc_add(int32_t* active, int32_t* fields, int64_t n, int F, const int32_t* rec,
+                int64_t k, int id_field, int32_t id_base, int32_t* out_slots) {
+  int64_t j = 0;
+  for (int64_t i = 0; i < n && j < k; i++) {
+    if (active[i]) continue;
+    for (int f = 0; f < F; f++) fields[(int64_t)f * n + i] = rec[j * F + f];
+    if (id_field >= 0) fields[(int64_t)id_field * n + i] = (int32_t)((uint32_t)id_base + (uint32_t)j);
+    active[i] = 1;
+    if (out_slots) out_slots[j] = (int32_t)i;
+    j++;
+  }
+  return j;
+}
+
+/* Distinct updates to the selected agents (Algorithms 1 and 2): the i-th
+ * selected target (ascending slot) gets the i-th selected record. op 0 adds
+ * field-wise with 32-bit wrap-around, op 1 overwrites. */
+int64_t orc_update_distinct(int32_t* fields, int64_t n, int F, const int32_t* target_mask,
+                            const int32_t* rec, const int32_t* rec_mask, int64_t k, int op,
+                            int32_t* out_slots) {
+  int32_t* targets = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  int32_t* recs = (int32_t*)malloc(sizeof(int32_t) * (size_t)(k > 0 ? k : 1));
+  int64_t nt = orc_flatnonzero(target_mask, n, targets);
+  int64_t nr = 0;
+  for (int64_t j = 0; j < k; j++)
+    if (rec_mask == NULL || rec_mask[j]) recs[nr++] = (int32_t)j;
+  int64_t r = nt < nr ? nt : nr;
+  for (int64_t i = 0; i < r; i++) {
+    int64_t slot = targets[i];
+    int64_t j = recs[i];
+    for (int f = 0; f < F; f++) {
+      int32_t* dst = &fields[(int64_t)f * n + slot];
+      if (op == 0)
+        *dst = (int32_t)((uint32_t)*dst + (uint32_t)rec[j * F + f]);
+      else
+        *dst = rec[j * F + f];
+    }
+    if (out_slots) out_slots[i] = (int32_t)slot;
+  }
+  free(targets);
+  free(recs);
+  return r;
+}
+
+/* Conflict resolution (Section 1's shared-resource case; Section 5.2's
+ * per-cell priority): among the claims on one resource, the lexicographically
+ * smallest (priority, claim index) wins. Claims with a resource outside
+ * [0, R) are not claims. */
+void orc_resolve(const int32_t* res, const uint32_t* prio, int64_t M, int64_t R,
+                 int32_t* winner, uint8_t* is_winner) {
+  for (int64_t r = 0; r < R; r++) winner[r] = -1;
+  for (int64_t m = 0; m < M; m++) {
+    int64_t r = res[m];
+    if (r < 0 || r >= R) continue;
+    int32_t w = winner[r];
+    if (w < 0 || prio[m] < prio[w] || (prio[m] == prio[w] && m < w)) winner[r] = (int32_t)m;
+  }
+  for (int64_t m = 0; m < M; m++) {
+    int64_t r = res[m];
+    is_winner[m] = (r >= 0 && r < R && winner[r] == (int32_t)m) ? 1 : 0;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Selective-update microbenchmark (a slab of n slots x F int32 fields). */
+void orc_c1_records(uint32_t seed, uint32_t model, uint32_t step, uint32_t p0, uint32_t p1,
+                    int64_t k, int F, int32_t* out) {
+  for (int64_t j = 0; j < k; j++)
+    for (int f = 0; f < F; f++) {
+      uint32_t purpose = f < 4 ? p0 : p1;
+      out[j * F + f] = (int32_t)draw(seed, model, step, (uint32_t)j, purpose, 0, f & 3);
+    }
+}
+
+/* Initial slab: each slot is live with probability 1/2; every slot's fields
+ * hold its own Philox record (live or not). */
+void orc_c1_init(int32_t* active, int32_t* fields, int64_t n, int F, uint32_t seed, uint32_t model) {
+  for (int64_t i = 0; i < n; i++) {
+    active[i] = draw(seed, model, ORC_INIT_STEP, (uint32_t)i, ORC_P_INIT_ACTIVE, 0, 0) < 0x80000000u;
+    for (int f = 0; f < F; f++) {
+      uint32_t purpose = f < 4 ? ORC_P_NEWREC0 : ORC_P_NEWREC1;
+      fields[(int64_t)f * n + i] = (int32_t)draw(seed, model, ORC_INIT_STEP, (uint32_t)i, purpose, 0, f & 3);
+    }
+  }
+}
+
+/* One microbenchmark call at step c with threshold T and k records:
+ *   1. remove live slots whose MASK draw is below T;
+ *   2. chosen = slots live after 1 whose CHOOSE draw is below T; the i-th
+ *      chosen slot (i < min(k, #chosen)) gets DELTA record i added;
+ *   3. NEWREC record j goes to the j-th slot free after 1, j < min(k, #free).
+ * Steps 2 and 3 touch disjoint slots. out_counts = removed, added, updated. */
+void orc_c1_call(int32_t* active, int32_t* fields, int64_t n, int F, uint32_t seed,
+                 uint32_t model, uint32_t step, uint32_t T, int64_t k, int64_t out_counts[3]) {
+  int32_t* mask = (int32_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
+  int32_t* rec = (int32_t*)calloc((size_t)(k > 0 ? k : 1) * (size_t)F, sizeof(int32_t));
+  for (int64_t i = 0; i < n; i++)
+    mask[i] = draw(seed, model, step, (uint32_t)i, ORC_P_MASK, 0, 0) < T;
+  out_counts[0] = orc_remove(active, mask, n);
+
+  for (int64_t i = 0; i < n; i++)
+    mask[i] = active[i] && draw(seed, model, step, (uint32_t)i, ORC_P_CHOOSE, 0, 0) < T;
+  orc_c1_records(seed, model, step, ORC_P_DELTA0, ORC_P_DELTA1, k, F, rec);
+  out_counts[2] = orc_update_distinct(fields, n, F, mask, rec, NULL, k, 0, NULL);
+
+  orc_c1_records(seed, model, step, ORC_P_NEWREC0, ORC_P_NEWREC1, k, F, rec);
+  out_counts[1] = orc_add(active, fields, n, F, rec, k, -1, 0, NULL);
+  free(mask);
+  free(rec);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Predation (Section 5.1 and Fig. 3: grass, sheep and wolves on a periodic
+ * 2-D lattice; random moves; sheep eat grass, wolves eat sheep; grass regrows
+ * after a fixed delay; asexual reproduction with a given probability, the
+ * child on the parent's cell). Numbers the paper does not give are params:
+ *   0 sheep gain, 1 wolf gain, 2 sheep reproduction threshold (u32),
+ *   3 wolf reproduction threshold (u32), 4 grass regrowth delay,
+ *   5 sheep metabolism, 6 wolf metabolism, 7 initial-grass threshold (u32). */
+struct orc_world {
+  int32_t side, ncells;
+  uint32_t seed, model;
+  int32_t params[8];
+  int32_t cap[2];
+  int32_t* agent[2][5]; /* active, cell, energy, id, age */
+  int32_t* grown;
+  int32_t* countdown;
+  uint64_t* best;      /* per-cell minimum claim key */
+  uint64_t* victim;    /* per-cell minimum victim key */
+  int32_t n_active[2], next_id[2], hw[2], overflow[2];
+  uint32_t t;
+};
+
+enum { A_ACTIVE = 0, A_CELL = 1, A_ENERGY = 2, A_ID = 3, A_AGE = 4 };
+#define NO_KEY 0xFFFFFFFFFFFFFFFFull
+
+orc_world* orc_pred_create(int32_t side, uint32_t seed, uint32_t model, const int32_t params[8],
+                           const int32_t cap[2], const int32_t n0[2]) {
+  if (side <= 0 || (int64_t)side * side > 0x7FFFFFFF) return NULL;
+  orc_world* w = (orc_world*)calloc(1, sizeof(orc_world));
+  w->side = side;
+  w->ncells = side * side;
+  w->seed = seed;
+  w->model = model;
+  memcpy(w->params, params, sizeof(w->params));
+  for (int s = 0; s < 2; s++) {
+    if (n0[s] < 0 || n0[s] > cap[s]) { orc_pred_free(w); return NULL; }
+    w->cap[s] = cap[s];
+    for (int a = 0; a < 5; a++)
+      w->agent[s][a] = (int32_t*)calloc((size_t)(cap[s] > 0 ? cap[s] : 1), sizeof(int32_t));
+  }
+  w->grown = (int32_t*)calloc((size_t)w->ncells, sizeof(int32_t));
+  w->countdown = (int32_t*)calloc((size_t)w->ncells, sizeof(int32_t));
+  w->best = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)w->ncells);
+  w->victim = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)w->ncells);
+
+  /* create_agents (Section 2): agent k of species s sits in slot k; cell and
+   * energy are uniform draws (cell in [0, L^2), energy in [0, 2 gain)). */
+  for (int s = 0; s < 2; s++) {
+    int32_t gain = params[s];
+    for (int32_t k = 0; k < n0[s]; k++) {
+      uint32_t u0 = draw(seed, model, ORC_INIT_STEP, (uint32_t)k, ORC_P_INIT_AGENT, (uint32_t)s, 0);
+      uint32_t u1 = draw(seed, model, ORC_INIT_STEP, (uint32_t)k, ORC_P_INIT_AGENT, (uint32_t)s, 1);
+      w->agent[s][A_ACTIVE][k] = 1;
+      w->agent[s][A_CELL][k] = uniform_below(u0, w->ncells);
+      w->agent[s][A_ENERGY][k] = uniform_below(u1, 2 * gain);
+      w->agent[s][A_ID][k] = k;
+      w->agent[s][A_AGE][k] = 0;
+    }
+    w->n_active[s] = n0[s];
+    w->next_id[s] = n0[s];
+    w->hw[s] = n0[s];
+  }
+  /* grass: grown with the initial-grass probability, countdown uniform in
+   * [0, regrowth) */
+  for (int32_t c = 0; c < w->ncells; c++) {
+    uint32_t u0 = draw(seed, model, ORC_INIT_STEP, (uint32_t)c, ORC_P_GRASS_INIT, 2, 0);
+    uint32_t u1 = draw(seed, model, ORC_INIT_STEP, (uint32_t)c, ORC_P_GRASS_INIT, 2, 1);
+    w->grown[c] = u0 < (uint32_t)params[7];
+    w->countdown[c] = uniform_below(u1, params[4]);
+  }
+  w->t = 0;
+  return w;
+}
+
+void orc_pred_free(orc_world* w) {
+  if (!w) return;
+  for (int s = 0; s < 2; s++)
+    for (int a = 0; a < 5; a++) free(w->agent[s][a]);
+  free(w->grown);
+  free(w->countdown);
+  free(w->best);
+  free(w->victim);
+  free(w);
+}
+
+int32_t* orc_pred_agents(orc_world* w, int species, int which) { return w->agent[species][which]; }
+int32_t* orc_pred_grass(orc_world* w, int which) { return which == 0 ? w->grown : w->countdown; }
+void orc_pred_counters(const orc_world* w, int32_t out[9]) {
+  for (int s = 0; s < 2; s++) {
+    out[0 + s] = w->n_active[s];
+    out[2 + s] = w->next_id[s];
+    out[4 + s] = w->hw[s];
+    out[6 + s] = w->overflow[s];
+  }
+  out[8] = (int32_t)w->t;
+}
+
+/* Neighbour offsets of the 8-neighbourhood, indexed by the top three bits of
+ * the MOVE draw. */
+static const int DX[8] = {-1, 0, 1, -1, 1, -1, 0, 1};
+static const int DY[8] = {-1, -1, -1, 0, 0, 1, 1, 1};
+
+/* step_agents (Section 2): random 8-neighbour move on the periodic lattice,
+ * metabolism, ageing -- for every live agent of the species. */
+static void move_species(orc_world* w, int s) {
+  int32_t L = w->side;
+  int32_t metab = w->params[5 + s];
+  for (int32_t i = 0; i < w->cap[s]; i++) {
+    if (!w->agent[s][A_ACTIVE][i]) continue;
+    uint32_t u = draw(w->seed, w->model, w->t, (uint32_t)i, ORC_P_MOVE, (uint32_t)s, 0);
+    int d = (int)(u >> 29);
+    int32_t cell = w->agent[s][A_CELL][i];
+    int32_t x = cell % L, y = cell / L;
+    x = (x + DX[d] + L) % L;
+    y = (y + DY[d] + L) % L;
+    w->agent[s][A_CELL][i] = y * L + x;
+    w->agent[s][A_ENERGY][i] -= metab;
+    w->agent[s][A_AGE][i] += 1;
+  }
+}
+
+static uint64_t make_key(uint32_t prio, int32_t slot) {
+  return ((uint64_t)prio << 32) | (uint32_t)slot;
+}
+
+/* Sheep eat grass: the live sheep on a grown cell claim it; the smallest
+ * (PRIO draw, slot) key wins (reading: one grass per cell per step). */
+static void sheep_eat(orc_world* w, orc_stats* st) {
+  for (int32_t c = 0; c < w->ncells; c++) w->best[c] = NO_KEY;
+  for (int32_t i = 0; i < w->cap[0]; i++) {
+    if (!w->agent[0][A_ACTIVE][i]) continue;
+    int32_t c = w->agent[0][A_CELL][i];
+    if (!w->grown[c]) continue;
+    uint64_t key = make_key(draw(w->seed, w->model, w->t, (uint32_t)i, ORC_P_PRIO, 0, 0), i);
+    if (key < w->best[c]) w->best[c] = key;
+  }
+  for (int32_t c = 0; c < w->ncells; c++) {
+    if (w->best[c] == NO_KEY) continue;
+    int32_t i = (int32_t)(uint32_t)w->best[c];
+    w->agent[0][A_ENERGY][i] += w->params[0];
+    w->grown[c] = 0;
+    w->countdown[c] = w->params[4];
+    st->grass_eaten++;
+  }
+}
+
+/* Reproduction = select + compact + distinct update + add (Section 4's
+ * predation example): parents are live agents with energy >= 0 whose REPRO
+ * draw is below the threshold, in ascending slot order; the i-th parent
+ * (i < r = min(#parents, #free)) places a child in the i-th free slot. The
+ * child takes floor(e/2) of the parent's energy e, the parent keeps the rest;
+ * the child sits on the parent's cell with age 0 and id next_id + i. */
+static void reproduce(orc_world* w, int s, orc_stats* st) {
+  int32_t cap = w->cap[s];
+  int32_t* parents = (int32_t*)malloc(sizeof(int32_t) * (size_t)(cap > 0 ? cap : 1));
+  int32_t* freeslots = (int32_t*)malloc(sizeof(int32_t) * (size_t)(cap > 0 ? cap : 1));
+  int32_t np = 0, nf = 0;
+  for (int32_t i = 0; i < cap; i++) {
+    if (w->agent[s][A_ACTIVE][i]) {
+      if (w->agent[s][A_ENERGY][i] >= 0 &&
+          draw(w->seed, w->model, w->t, (uint32_t)i, ORC_P_REPRO, (uint32_t)s, 0) < (uint32_t)w->params[2 + s])
+        parents[np++] = i;
+    } else {
+      freeslots[nf++] = i;
+    }
+  }
+  int32_t r = np < nf ? np : nf;
+  if (np > nf) w->overflow[s] = 1;
+  for (int32_t j = 0; j < r; j++) {
+    int32_t p = parents[j], c = freeslots[j];
+    int32_t e = w->agent[s][A_ENERGY][p];
+    int32_t half = e >> 1;
+    w->agent[s][A_ENERGY][p] = e - half;
+    w->agent[s][A_ACTIVE][c] = 1;
+    w->agent[s][A_CELL][c] = w->agent[s][A_CELL][p];
+    w->agent[s][A_ENERGY][c] = half;
+    w->agent[s][A_ID][c] = w->next_id[s] + j;
+    w->agent[s][A_AGE][c] = 0;
+  }
+  w->next_id[s] += r;
+  w->n_active[s] += r;
+  if (w->n_active[s] > w->hw[s]) w->hw[s] = w->n_active[s];
+  st->parents[s] = np;
+  st->births[s] = r;
+  free(parents);
+  free(freeslots);
+}
+
+/* Death: live agents with negative energy become placeholders. */
+static void die(orc_world* w, int s, orc_stats* st) {
+  for (int32_t i = 0; i < w->cap[s]; i++) {
+    if (w->agent[s][A_ACTIVE][i] && w->agent[s][A_ENERGY][i] < 0) {
+      w->agent[s][A_ACTIVE][i] = 0;
+      w->n_active[s]--;
+      st->starved[s]++;
+    }
+  }
+}
+
+/* Wolves eat sheep: on every cell, the live sheep with the smallest (VICTIM
+ * draw, slot) key is that cell's victim; the live wolves on cells with a
+ * victim claim it, and the smallest (PRIO draw, slot) wolf wins (reading: at
+ * most one wolf eats per cell per step). The winner gains energy, the victim
+ * is removed. */
+static void wolves_eat(orc_world* w, orc_stats* st) {
+  for (int32_t c = 0; c < w->ncells; c++) {
+    w->victim[c] = NO_KEY;
+    w->best[c] = NO_KEY;
+  }
+  for (int32_t i = 0; i < w->cap[0]; i++) {
+    if (!w->agent[0][A_ACTIVE][i]) continue;
+    int32_t c = w->agent[0][A_CELL][i];
+    uint64_t key = make_key(draw(w->seed, w->model, w->t, (uint32_t)i, ORC_P_VICTIM, 0, 0), i);
+    if (key < w->victim[c]) w->victim[c] = key;
+  }
+  for (int32_t i = 0; i < w->cap[1]; i++) {
+    if (!w->agent[1][A_ACTIVE][i]) continue;
+    int32_t c = w->agent[1][A_CELL][i];
+    if (w->victim[c] == NO_KEY) continue;
+    uint64_t key = make_key(draw(w->seed, w->model, w->t, (uint32_t)i, ORC_P_PRIO, 1, 0), i);
+    if (key < w->best[c]) w->best[c] = key;
+  }
+  for (int32_t c = 0; c < w->ncells; c++) {
+    if (w->best[c] == NO_KEY) continue;
+    int32_t wolf = (int32_t)(uint32_t)w->best[c];
+    int32_t sheep = (int32_t)(uint32_t)w->victim[c];
+    w->agent[1][A_ENERGY][wolf] += w->params[1];
+    w->agent[0][A_ACTIVE][sheep] = 0;
+    w->n_active[0]--;
+    st->eaten++;
+  }
+}
+
+/* Grass regrowth after a fixed delay: a cell eaten at step t is grown again
+ * from step t + delay on. */
+static void grass(orc_world* w) {
+  for (int32_t c = 0; c < w->ncells; c++) {
+    if (w->grown[c]) continue;
+    w->countdown[c] -= 1;
+    if (w->countdown[c] <= 0) w->grown[c] = 1;
+  }
+}
+
+/* One step of Sim.step (Section 3), species order of Wilensky's model:
+ * sheep move, eat, reproduce, die; wolves move, eat, reproduce, die; grass. */
+void orc_pred_step(orc_world* w, orc_stats* st) {
+  memset(st, 0, sizeof(*st));
+  st->n_start[0] = w->n_active[0];
+  st->n_start[1] = w->n_active[1];
+  move_species(w, 0);
+  sheep_eat(w, st);
+  reproduce(w, 0, st);
+  die(w, 0, st);
+  move_species(w, 1);
+  wolves_eat(w, st);
+  reproduce(w, 1, st);
+  die(w, 1, st);
+  grass(w);
+  w->t++;
+  for (int s = 0; s < 2; s++) {
+    st->n_end[s] = w->n_active[s];
+    st->hw[s] = w->hw[s];
+    st->overflow[s] = w->overflow[s];
+    int64_t e = 0;
+    for (int32_t i = 0; i < w->cap[s]; i++)
+      if (w->agent[s][A_ACTIVE][i]) e += w->agent[s][A_ENERGY][i];
+    st->energy[s] = e;
+  }
+}
