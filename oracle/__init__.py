@@ -25,7 +25,7 @@ _lib = None
 
 # Philox purposes (counter word c2); species word c3: 0 sheep/slab, 1 wolf, 2 grass.
 P_MOVE, P_PRIO, P_REPRO, P_VICTIM = 1, 2, 3, 4
-P_INIT_AGENT, P_GRASS_INIT, P_MASK, P_CHOOSE = 5, 6, 7, 8
+P_INIT_AGENT, P_GRASS_INIT, P_MASK = 5, 6, 7
 P_NEWREC0, P_NEWREC1, P_DELTA0, P_DELTA1 = 9, 10, 11, 12
 P_RESOURCE, P_INIT_ACTIVE = 13, 14
 INIT_STEP = 0xFFFFFFFF

@@ -180,9 +180,10 @@ void orc_c1_init(int32_t* active, int32_t* fields, int64_t n, int F, uint32_t se
   }
 }
 
-/* One microbenchmark call at step c with threshold T and k records:
- *   1. remove live slots whose MASK draw is below T;
- *   2. chosen = slots live after 1 whose CHOOSE draw is below T; the i-th
+/* One microbenchmark call at step c with threshold T and k records. Each slot
+ * takes one MASK draw per call: word 0 decides removal, word 1 the choice.
+ *   1. remove live slots whose word 0 is below T;
+ *   2. chosen = slots live after 1 whose word 1 is below T; the i-th
  *      chosen slot (i < min(k, #chosen)) gets DELTA record i added;
  *   3. NEWREC record j goes to the j-th slot free after 1, j < min(k, #free).
  * Steps 2 and 3 touch disjoint slots. out_counts = removed, added, updated. */
@@ -195,7 +196,7 @@ void orc_c1_call(int32_t* active, int32_t* fields, int64_t n, int F, uint32_t se
   out_counts[0] = orc_remove(active, mask, n);
 
   for (int64_t i = 0; i < n; i++)
-    mask[i] = active[i] && draw(seed, model, step, (uint32_t)i, ORC_P_CHOOSE, 0, 0) < T;
+    mask[i] = active[i] && draw(seed, model, step, (uint32_t)i, ORC_P_MASK, 0, 1) < T;
   orc_c1_records(seed, model, step, ORC_P_DELTA0, ORC_P_DELTA1, k, F, rec);
   out_counts[2] = orc_update_distinct(fields, n, F, mask, rec, NULL, k, 0, NULL);
 

@@ -32,7 +32,7 @@ void orc_philox_words(uint32_t seed, uint32_t model, uint32_t step, uint32_t pur
 /* Purposes (the c2 counter word). Species word c3: 0 sheep / slab, 1 wolf, 2 grass. */
 enum {
   ORC_P_MOVE = 1, ORC_P_PRIO = 2, ORC_P_REPRO = 3, ORC_P_VICTIM = 4,
-  ORC_P_INIT_AGENT = 5, ORC_P_GRASS_INIT = 6, ORC_P_MASK = 7, ORC_P_CHOOSE = 8,
+  ORC_P_INIT_AGENT = 5, ORC_P_GRASS_INIT = 6, ORC_P_MASK = 7,
   ORC_P_NEWREC0 = 9, ORC_P_NEWREC1 = 10, ORC_P_DELTA0 = 11, ORC_P_DELTA1 = 12,
   ORC_P_RESOURCE = 13, ORC_P_INIT_ACTIVE = 14
 };

@@ -208,7 +208,7 @@ def c1_call_brute(active, fields, seed, step, T, k):
     mask = oracle.philox_words(seed, 0, step, oracle.P_MASK, 0, 0, n) < T
     removed = int(np.sum(active.astype(bool) & mask))
     active[mask] = 0
-    choose = oracle.philox_words(seed, 0, step, oracle.P_CHOOSE, 0, 0, n) < T
+    choose = oracle.philox_words(seed, 0, step, oracle.P_MASK, 0, 0, n, word=1) < T
     chosen = np.flatnonzero(active.astype(bool) & choose)
     free = np.flatnonzero(active == 0)
     d = oracle.c1_records(seed, 0, step, oracle.P_DELTA0, oracle.P_DELTA1, k, F)
