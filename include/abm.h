@@ -1,0 +1,290 @@
+/*
+ * abm.h -- C ABI of the GB300 selective-update engine for agent-based models.
+ *
+ * The engine implements the hot path of ABMax (Chaturvedi, El-Gazzar, van
+ * Gerven, arXiv 2508.16508): distinct updates to a dynamically selected,
+ * variable-size subset of agents held in fixed-capacity arrays (Section 4),
+ * driven by the wolf-sheep-grass predation model (Section 5.1).
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns an abm_status; ABM_OK is 0. abm_strerror() names it.
+ *  - Pointers documented as "device" are CUDA device (or managed) pointers;
+ *    "host" pointers are ordinary CPU memory. Nothing takes ownership of a
+ *    caller's buffer; handles own the memory they allocate and free it in
+ *    their destroy call.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream). All work is enqueued asynchronously on it; device outputs are
+ *    valid once the stream reaches that point. Calls that return host values
+ *    synchronise the stream and say so.
+ *  - Counts returned through device pointers are int32. A NULL output pointer
+ *    means "not wanted" unless the argument is documented as required.
+ *  - Argument errors (NULL where required, negative sizes, sizes beyond a
+ *    documented limit) return ABM_ERR_ARG before anything is enqueued.
+ *  - Spin-waits inside kernels are bounded. A wait that runs out sets a
+ *    device error word and the kernel returns; abm_*_check() reports
+ *    ABM_ERR_DEVICE_TIMEOUT and the handle's results are then undefined.
+ *  - Randomness is Philox4x32-10 (Salmon et al., SC'11) with counter
+ *    (step, slot, purpose, species) and key (seed, model); a probability p is
+ *    an integer threshold T = floor(p * 2^32) and an event happens iff the
+ *    32-bit draw is below T.
+ */
+#ifndef ABM_H
+#define ABM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t abm_status;
+#define ABM_OK 0
+#define ABM_ERR_ARG 1            /* invalid argument; nothing was enqueued */
+#define ABM_ERR_OOM 2            /* device allocation failed */
+#define ABM_ERR_CUDA 3           /* a CUDA runtime call failed */
+#define ABM_ERR_DEVICE_TIMEOUT 4 /* a bounded device-side wait ran out */
+#define ABM_ERR_OVERFLOW 5       /* informational: more agents asked for a slot than were free */
+#define ABM_ERR_STATE 6          /* operation not valid for this handle */
+
+const char* abm_strerror(abm_status s);
+/* Library version: major * 10000 + minor * 100 + patch. */
+int32_t abm_version(void);
+
+/* Philox purposes (counter word 2). Species word 3: 0 sheep or generic slab,
+ * 1 wolf, 2 grass. Initialisation draws use step ABM_INIT_STEP. */
+#define ABM_P_MOVE 1
+#define ABM_P_PRIO 2
+#define ABM_P_REPRO 3
+#define ABM_P_VICTIM 4
+#define ABM_P_INIT_AGENT 5
+#define ABM_P_GRASS_INIT 6
+#define ABM_P_MASK 7
+#define ABM_P_NEWREC0 9
+#define ABM_P_NEWREC1 10
+#define ABM_P_DELTA0 11
+#define ABM_P_DELTA1 12
+#define ABM_P_RESOURCE 13
+#define ABM_P_INIT_ACTIVE 14
+#define ABM_INIT_STEP 0xFFFFFFFFu
+
+/* ========================================================================== */
+/* Generic fixed-capacity agent set ("Set", Section 2)                        */
+/* ========================================================================== */
+/*
+ * A slab holds `capacity` slots. Slot i has an int32 live flag and F int32
+ * fields. Device layout: active[capacity] (int32, 0/1) and fields stored
+ * agent-major, capacity x Fp int32 with Fp = F rounded up to a multiple of 4
+ * (so one agent's fields are one 16/32-byte run). Placeholders (inactive
+ * slots) keep their last field values. Limits: 1 <= capacity <= 2^28 - 1,
+ * 1 <= F <= 16.
+ */
+typedef struct abm_slab abm_slab;
+
+#define ABM_INIT_EMPTY 0     /* all slots free, fields zero */
+#define ABM_INIT_HALF_LIVE 1 /* slot i live iff draw(INIT_STEP, i, INIT_ACTIVE, 0).w0 < 2^31;
+                                field f = word f%4 of draw(INIT_STEP, i, NEWREC0 + f/4, 0) */
+
+abm_status abm_slab_create(int32_t capacity, int32_t n_fields, uint32_t seed, uint32_t model,
+                           int32_t init, void* stream, abm_slab** out);
+abm_status abm_slab_destroy(abm_slab* s);
+/* Synchronises `stream`, then reports any device-side error recorded for the slab. */
+abm_status abm_slab_check(abm_slab* s, void* stream);
+/* Device pointers to the slab's arrays (valid until destroy). */
+abm_status abm_slab_arrays(abm_slab* s, int32_t** active, int32_t** fields, int32_t* fields_stride);
+/* Copy `n` slots starting at slot 0 of field `field` (or the live flags for
+ * field = -1) into / out of a device buffer of n int32. */
+abm_status abm_slab_read(abm_slab* s, int32_t field, int32_t* dst, int32_t n, void* stream);
+abm_status abm_slab_write(abm_slab* s, int32_t field, const int32_t* src, int32_t n, void* stream);
+
+/* Selection predicates (select_agents, Section 2; the masks of Algorithms 1/2). */
+#define ABM_PRED_LIVE 0      /* live slots */
+#define ABM_PRED_FREE 1      /* placeholder slots */
+#define ABM_PRED_BERNOULLI 2 /* live and word 0 of draw(step, slot, purpose, species) < threshold */
+#define ABM_PRED_MASK 3      /* live and mask[slot] != 0 (device int32[capacity]) */
+#define ABM_PRED_FIELD 4     /* live and ((field value & and_mask) <cmp> value) */
+#define ABM_CMP_EQ 0
+#define ABM_CMP_NE 1
+#define ABM_CMP_LT 2
+#define ABM_CMP_GE 3
+typedef struct abm_pred {
+  int32_t kind;
+  uint32_t threshold, step, purpose, species; /* BERNOULLI */
+  const int32_t* mask;                        /* MASK (device) */
+  int32_t field, cmp, and_mask, value;        /* FIELD */
+} abm_pred;
+
+/* select_agents (Section 2): the slots satisfying `pred`, ascending, written
+ * to out_idx[0..count) (device int32[capacity], required); the count goes to
+ * *out_count (device int32, required). Stable stream compaction. */
+abm_status abm_select(abm_slab* s, const abm_pred* pred, int32_t* out_idx, int32_t* out_count,
+                      void* stream);
+
+/* set_agents_mask (Section 2) as removal: every slot satisfying `pred` becomes
+ * a placeholder. *out_removed (device, nullable) = number removed. */
+abm_status abm_remove(abm_slab* s, const abm_pred* pred, int32_t* out_removed, void* stream);
+
+/* Adding agents with distinct initial states (Section 4 toy task with free
+ * slots as targets; Algorithm 1 rank matching): record j (records = device
+ * int32[k][F], row-major) goes to the j-th free slot in ascending order, for
+ * j < r = min(k, #free). If id_field >= 0 that field is set to the slab's
+ * next id + j and next id advances by r. out_slots (device int32[k],
+ * nullable) receives the slots; *out_added (device, nullable) = r. When
+ * k > #free the slab's overflow flag is set (abm_slab_counters). */
+abm_status abm_add(abm_slab* s, const int32_t* records, int32_t k, int32_t id_field,
+                   int32_t* out_slots, int32_t* out_added, void* stream);
+
+/* Distinct updates (Algorithms 1 and 2, set_agents_rm / set_agents_sci): the
+ * i-th slot satisfying `pred` (ascending) receives the i-th selected record,
+ * for i < r = min(#selected slots, #selected records). Records are device
+ * int32[k][F]; record_mask (device int32[k], nullable = all) selects records.
+ * op ABM_OP_ADD adds field-wise with 32-bit wrap-around; ABM_OP_SET
+ * overwrites. out_slots (device int32[min(k,capacity)], nullable) gets the
+ * updated slots; *out_applied (device, nullable) = r. A non-NULL record_mask
+ * needs k <= capacity. */
+#define ABM_OP_ADD 0
+#define ABM_OP_SET 1
+abm_status abm_update_distinct(abm_slab* s, const abm_pred* pred, const int32_t* records,
+                               const int32_t* record_mask, int32_t k, int32_t op,
+                               int32_t* out_slots, int32_t* out_applied, void* stream);
+
+/* Selective-update call, fused into one pass over the slab (the microbenchmark
+ * of the selection / add / remove / distinct-update primitives). With one
+ * draw u = draw(step, slot, MASK, 0) per slot:
+ *   1. remove every live slot with u.w0 < threshold;
+ *   2. the i-th slot still live with u.w1 < threshold (ascending) gets delta
+ *      record i added field-wise (wrapping), i < min(k, #chosen);
+ *   3. record j goes to the j-th free slot (after 1), j < min(k, #free).
+ * Steps 2 and 3 touch disjoint slots, so the result equals abm_remove,
+ * abm_update_distinct and abm_add issued in that order with those
+ * predicates. records and deltas are device int32[k][F]. out_counts (device
+ * int32[3], nullable) = removed, added, updated. */
+abm_status abm_selective_update(abm_slab* s, uint32_t step, uint32_t threshold,
+                                const int32_t* records, const int32_t* deltas, int32_t k,
+                                int32_t* out_counts, void* stream);
+
+/* Fill out[k][F] (device int32) with record j field f = word f%4 of
+ * draw(step, j, purpose0 + (f >= 4 ? purpose1 - purpose0 : 0), 0) under the
+ * slab's key -- the Philox-generated records of the microbenchmark. */
+abm_status abm_philox_records(abm_slab* s, uint32_t step, uint32_t purpose0, uint32_t purpose1,
+                              int32_t k, int32_t* out, void* stream);
+
+typedef struct abm_slab_counters {
+  int32_t n_active, next_id, overflow, reserved;
+} abm_slab_counters;
+/* Host copy of the slab's counters (synchronises `stream`). */
+abm_status abm_slab_counters_get(abm_slab* s, abm_slab_counters* out, void* stream);
+
+/* ========================================================================== */
+/* Conflict resolution (Section 1: several agents claim one resource;         */
+/* Section 5.2: per-cell priority)                                            */
+/* ========================================================================== */
+/* Claim m (0 <= m < M) asks for resource claim_res[m]; a claim whose resource
+ * is outside [0, R) is ignored. Per resource the claim with the
+ * lexicographically smallest (claim_prio[m], m) wins.
+ *  claim_res, claim_prio: device int32[M] / uint32[M] (required when M > 0).
+ *  table: device uint64[R] scratch; every entry must be 0xFFFFFFFFFFFFFFFF
+ *         before the call (abm_resolve_table_init) and is left so after it.
+ *  out_winner: device int32[R] (required): winning claim index or -1.
+ *  out_is_winner: device uint8[M] (nullable): 1 for winning claims.
+ * Limits: 0 <= M, 1 <= R <= 2^31 - 1. */
+abm_status abm_resolve_table_init(uint64_t* table, int32_t R, void* stream);
+abm_status abm_resolve(const int32_t* claim_res, const uint32_t* claim_prio, int32_t M, int32_t R,
+                       uint64_t* table, int32_t* out_winner, uint8_t* out_is_winner, void* stream);
+
+/* ========================================================================== */
+/* Predation model (Section 5.1, Fig. 3)                                      */
+/* ========================================================================== */
+/*
+ * Wolves, sheep and grass on a periodic side x side lattice (cell = y*side+x).
+ * Per step, in this order: sheep move to a random 8-neighbour (word 0 of the
+ * MOVE draw, top 3 bits), lose `metabolism` energy, age by 1; sheep on grown
+ * grass claim it and the smallest (PRIO draw, slot) sheep per cell eats
+ * (+gain, grass regrows `regrowth` steps later); live sheep with energy >= 0
+ * and REPRO draw < T reproduce in ascending slot order into the lowest free
+ * slots (r = min(parents, free); child on the parent's cell with floor(e/2)
+ * energy, age 0, id next_id + i; the parent keeps e - floor(e/2)); sheep with
+ * energy < 0 die. Wolves then do the same, except that eating means: per
+ * cell, the live sheep with the smallest (VICTIM draw, slot) is the victim
+ * and the smallest (PRIO draw, slot) wolf on that cell eats it (+gain, the
+ * sheep is removed).
+ *
+ * params[8] (int32; thresholds are u32 bit patterns): sheep gain, wolf gain,
+ * sheep reproduction T, wolf reproduction T, grass regrowth delay, sheep
+ * metabolism, wolf metabolism, initial-grass T. Initial agent k of species s
+ * sits in slot k with cell = (w0 * side^2) >> 32 and energy =
+ * (w1 * 2 * gain) >> 32 of draw(INIT_STEP, k, INIT_AGENT, s); cell c's grass
+ * is grown iff w0 < initial-grass T and otherwise waits (w1 * regrowth) >> 32
+ * steps, from draw(INIT_STEP, c, GRASS_INIT, 2).
+ *
+ * Limits: 1 <= side <= 46340, 0 <= n0[s] <= cap[s] <= 2^28 - 1.
+ */
+typedef struct abm_world abm_world;
+
+typedef struct abm_config {
+  int32_t side;
+  uint32_t seed, model;
+  int32_t params[8];
+  int32_t cap[2];
+  int32_t n0[2];
+} abm_config;
+
+/* Per-step statistics, written by the device (one record per step). */
+typedef struct abm_step_stats {
+  int32_t n_start[2];   /* live agents when the step started */
+  int32_t parents[2];   /* agents selected to reproduce */
+  int32_t births[2];    /* children placed */
+  int32_t starved[2];   /* agents removed with energy < 0 */
+  int32_t eaten;        /* sheep eaten by wolves */
+  int32_t grass_eaten;  /* cells grazed */
+  int32_t n_end[2];     /* live agents at the end of the step */
+  int32_t hw[2];        /* maximum post-birth population so far */
+  int32_t overflow[2];  /* 1 once parents outnumbered free slots */
+  int32_t step;         /* index of this step */
+  int32_t extent[2];    /* highest slot ever used + 1, when the step started */
+  int32_t reserved;
+  int64_t energy[2];    /* total live energy at the end of the step (only when requested) */
+} abm_step_stats;
+
+abm_status abm_create(const abm_config* cfg, void* stream, abm_world** out);
+abm_status abm_destroy(abm_world* w);
+/* Advance `nsteps` steps. stats: device abm_step_stats[nsteps] (nullable).
+ * want_energy != 0 also fills the energy totals (one extra reduction per step). */
+abm_status abm_step(abm_world* w, int32_t nsteps, abm_step_stats* stats, int32_t want_energy,
+                    void* stream);
+/* Capture `nsteps` steps into a CUDA graph once and replay it `reps` times
+ * (stats, if given, is device abm_step_stats[nsteps] and is overwritten by each replay). */
+abm_status abm_step_graph(abm_world* w, int32_t nsteps, int32_t reps, abm_step_stats* stats,
+                          void* stream);
+/* abm_step that also times each kernel with CUDA events recorded on `stream`
+ * between the launches. phase_ms (host float[8], required) receives the
+ * milliseconds summed over the steps per kernel: [0] sheep move, [1] sheep
+ * eat/select/compact, [2] sheep births, [3] wolf move, [4] wolf
+ * eat/select/compact, [5] wolf births, [7] first to last event; [6] = 0.
+ * Synchronises `stream`. */
+abm_status abm_step_profiled(abm_world* w, int32_t nsteps, abm_step_stats* stats, float* phase_ms,
+                             void* stream);
+/* Synchronises `stream`; reports a recorded device error (e.g. a timed-out wait). */
+abm_status abm_world_check(abm_world* w, void* stream);
+
+/* State export into device int32 buffers of the slab capacity (agents) or
+ * side^2 (grass). which: 0 active, 1 cell, 2 energy, 3 id, 4 age. Grass:
+ * 0 grown (0/1), 1 wait = steps until the cell is edible (0 when grown). */
+abm_status abm_read_agents(abm_world* w, int32_t species, int32_t which, int32_t* dst, void* stream);
+abm_status abm_read_grass(abm_world* w, int32_t which, int32_t* dst, void* stream);
+typedef struct abm_world_counters {
+  int32_t n_active[2], next_id[2], hw[2], overflow[2], extent[2], step, reserved;
+} abm_world_counters;
+/* Host copy of the counters (synchronises `stream`). */
+abm_status abm_world_counters_get(abm_world* w, abm_world_counters* out, void* stream);
+
+/* Checkpoint: the whole state as a flat byte image in host memory.
+ * abm_save with buf = NULL returns the size in *bytes. abm_load restores a
+ * world created with the same config. Both synchronise `stream`. */
+abm_status abm_save(abm_world* w, void* buf, size_t* bytes, void* stream);
+abm_status abm_load(abm_world* w, const void* buf, size_t bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ABM_H */

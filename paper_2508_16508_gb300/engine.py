@@ -1,0 +1,220 @@
+"""Thin object layer over the C ABI for torch users (marshalling only).
+
+Device buffers are torch tensors on the current CUDA device; every method
+enqueues library calls on the current torch stream (or the one given).
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import abm
+from .abm import call, ptr
+
+
+def _stream(stream):
+    return abm.stream_handle(stream)
+
+
+class Slab:
+    """Fixed-capacity agent set with F int32 fields per slot (ABMax `Set`)."""
+
+    def __init__(self, capacity: int, n_fields: int, seed: int = 0, model: int = 0,
+                 init: int = abm.INIT_EMPTY, stream=None):
+        self.capacity, self.F = int(capacity), int(n_fields)
+        self.seed, self.model = seed, model
+        h = C.c_void_p()
+        call("abm_slab_create", self.capacity, self.F, seed & 0xFFFFFFFF, model & 0xFFFFFFFF,
+             init, _stream(stream), C.byref(h))
+        self.h = h
+        dev = torch.cuda.current_device()
+        self._i32 = dict(dtype=torch.int32, device=f"cuda:{dev}")
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            abm.lib().abm_slab_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, stream=None):
+        call("abm_slab_check", self.h, _stream(stream))
+
+    def read(self, field: int, n: int | None = None, stream=None) -> torch.Tensor:
+        n = self.capacity if n is None else n
+        out = torch.empty(n, **self._i32)
+        call("abm_slab_read", self.h, field, ptr(out), n, _stream(stream))
+        return out
+
+    def write(self, field: int, src: torch.Tensor, stream=None):
+        src = src.to(torch.int32).contiguous()
+        call("abm_slab_write", self.h, field, ptr(src), src.numel(), _stream(stream))
+
+    def fields(self, stream=None) -> torch.Tensor:
+        return torch.stack([self.read(f, stream=stream) for f in range(self.F)])
+
+    def counters(self, stream=None) -> dict:
+        c = abm.abm_slab_counters()
+        call("abm_slab_counters_get", self.h, C.byref(c), _stream(stream))
+        return {"n_active": c.n_active, "next_id": c.next_id, "overflow": c.overflow}
+
+    def select(self, p: abm.abm_pred, stream=None):
+        idx = torch.empty(self.capacity, **self._i32)
+        cnt = torch.zeros(1, **self._i32)
+        call("abm_select", self.h, C.byref(p), ptr(idx), ptr(cnt), _stream(stream))
+        return idx, cnt
+
+    def remove(self, p: abm.abm_pred, stream=None) -> torch.Tensor:
+        cnt = torch.zeros(1, **self._i32)
+        call("abm_remove", self.h, C.byref(p), ptr(cnt), _stream(stream))
+        return cnt
+
+    def add(self, records: torch.Tensor, id_field: int = -1, stream=None):
+        rec = records.to(torch.int32).contiguous()
+        k = rec.shape[0] if rec.numel() else 0
+        slots = torch.empty(max(k, 1), **self._i32)
+        cnt = torch.zeros(1, **self._i32)
+        call("abm_add", self.h, ptr(rec) if k else None, k, id_field, ptr(slots), ptr(cnt),
+             _stream(stream))
+        return slots, cnt
+
+    def update_distinct(self, p: abm.abm_pred, records: torch.Tensor, record_mask=None,
+                        op: int = abm.OP_ADD, stream=None):
+        rec = records.to(torch.int32).contiguous()
+        k = rec.shape[0] if rec.numel() else 0
+        rm = None if record_mask is None else record_mask.to(torch.int32).contiguous()
+        slots = torch.empty(max(min(k, self.capacity), 1), **self._i32)
+        cnt = torch.zeros(1, **self._i32)
+        call("abm_update_distinct", self.h, C.byref(p), ptr(rec) if k else None, ptr(rm), k, op,
+             ptr(slots), ptr(cnt), _stream(stream))
+        return slots, cnt
+
+    def selective_update(self, step: int, threshold: int, records: torch.Tensor,
+                         deltas: torch.Tensor, out_counts: torch.Tensor | None = None, stream=None):
+        k = records.shape[0]
+        out = torch.zeros(3, **self._i32) if out_counts is None else out_counts
+        call("abm_selective_update", self.h, step & 0xFFFFFFFF, threshold & 0xFFFFFFFF,
+             ptr(records), ptr(deltas), k, ptr(out), _stream(stream))
+        return out
+
+    def philox_records(self, step: int, purpose0: int, purpose1: int, k: int, out=None,
+                       stream=None) -> torch.Tensor:
+        out = torch.empty((max(k, 1), self.F), **self._i32) if out is None else out
+        call("abm_philox_records", self.h, step & 0xFFFFFFFF, purpose0, purpose1, k, ptr(out),
+             _stream(stream))
+        return out[:k]
+
+
+class Resolver:
+    """Per-resource conflict resolution with a reusable scratch table."""
+
+    def __init__(self, R: int, stream=None):
+        self.R = int(R)
+        dev = torch.cuda.current_device()
+        self.table = torch.empty(self.R, dtype=torch.int64, device=f"cuda:{dev}")
+        self.winner = torch.empty(self.R, dtype=torch.int32, device=f"cuda:{dev}")
+        call("abm_resolve_table_init", ptr(self.table), self.R, _stream(stream))
+
+    def __call__(self, res: torch.Tensor, prio: torch.Tensor, is_winner: torch.Tensor | None = None,
+                 stream=None):
+        M = res.numel()
+        call("abm_resolve", ptr(res), ptr(prio), M, self.R, ptr(self.table), ptr(self.winner),
+             ptr(is_winner), _stream(stream))
+        return self.winner
+
+
+AGENT_FIELDS = ("active", "cell", "energy", "id", "age")
+
+
+class World:
+    """One predation model (wolf-sheep-grass) on the GPU."""
+
+    def __init__(self, side, seed, model, params, cap, n0, stream=None):
+        cfg = abm.abm_config()
+        cfg.side, cfg.seed, cfg.model = int(side), seed & 0xFFFFFFFF, model & 0xFFFFFFFF
+        for i in range(8):
+            cfg.params[i] = int(params[i])
+        for s in range(2):
+            cfg.cap[s], cfg.n0[s] = int(cap[s]), int(n0[s])
+        h = C.c_void_p()
+        call("abm_create", C.byref(cfg), _stream(stream), C.byref(h))
+        self.h = h
+        self.side, self.cap = int(side), [int(cap[0]), int(cap[1])]
+        self.dev = f"cuda:{torch.cuda.current_device()}"
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            abm.lib().abm_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, nsteps: int = 1, stats: torch.Tensor | None = None, want_energy=False,
+             stream=None):
+        call("abm_step", self.h, nsteps, ptr(stats), 1 if want_energy else 0, _stream(stream))
+
+    def step_graph(self, nsteps: int, reps: int = 1, stats: torch.Tensor | None = None,
+                   stream=None):
+        call("abm_step_graph", self.h, nsteps, reps, ptr(stats), _stream(stream))
+
+    def step_profiled(self, nsteps: int, stats: torch.Tensor | None = None, stream=None) -> list:
+        """Steps with per-kernel CUDA-event timing; returns the 8 phase sums (ms)."""
+        ms = (C.c_float * 8)()
+        call("abm_step_profiled", self.h, nsteps, ptr(stats), ms, _stream(stream))
+        return list(ms)
+
+    def new_stats(self, nsteps: int) -> torch.Tensor:
+        return torch.zeros((nsteps, abm.STATS_WORDS), dtype=torch.int32, device=self.dev)
+
+    def check(self, stream=None):
+        call("abm_world_check", self.h, _stream(stream))
+
+    def agents(self, species: int, which: str, stream=None) -> torch.Tensor:
+        out = torch.empty(self.cap[species], dtype=torch.int32, device=self.dev)
+        call("abm_read_agents", self.h, species, AGENT_FIELDS.index(which), ptr(out), _stream(stream))
+        return out
+
+    def grass(self, which: str, stream=None) -> torch.Tensor:
+        out = torch.empty(self.side * self.side, dtype=torch.int32, device=self.dev)
+        call("abm_read_grass", self.h, 0 if which == "grown" else 1, ptr(out), _stream(stream))
+        return out
+
+    def counters(self, stream=None) -> dict:
+        c = abm.abm_world_counters()
+        call("abm_world_counters_get", self.h, C.byref(c), _stream(stream))
+        return {"n_active": list(c.n_active), "next_id": list(c.next_id), "hw": list(c.hw),
+                "overflow": list(c.overflow), "extent": list(c.extent), "step": c.step}
+
+    def save(self, stream=None) -> bytes:
+        n = C.c_size_t(0)
+        call("abm_save", self.h, None, C.byref(n), _stream(stream))
+        buf = C.create_string_buffer(n.value)
+        call("abm_save", self.h, buf, C.byref(n), _stream(stream))
+        return buf.raw
+
+    def load(self, image: bytes, stream=None):
+        buf = C.create_string_buffer(image, len(image))
+        call("abm_load", self.h, buf, len(image), _stream(stream))
+
+
+def decode_stats(t: torch.Tensor) -> list[dict]:
+    """Device stats rows (int32 words) -> list of dicts."""
+    rows = t.cpu().contiguous()
+    out = []
+    for r in rows:
+        s = abm.abm_step_stats.from_buffer_copy(r.numpy().tobytes())
+        d = {}
+        for name, _ in s._fields_:
+            v = getattr(s, name)
+            d[name] = list(v) if hasattr(v, "__len__") else int(v)
+        out.append(d)
+    return out

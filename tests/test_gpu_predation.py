@@ -1,0 +1,194 @@
+"""GPU parity: the predation step (Section 5.1) vs the sequential oracle.
+
+The whole state -- every slot of both species (live flag, cell, energy, id,
+age, including the stale fields of placeholders), the grass (grown flag and
+steps until edible), the counters and the per-step statistics -- is compared
+bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("active", "cell", "energy", "id", "age")
+
+
+@pytest.fixture(scope="module")
+def eng():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2508_16508_gb300 import abm, engine
+    abm.lib()
+    return engine
+
+
+def oracle_wait(ow):
+    grown = ow.grass("grown")
+    cd = ow.grass("countdown")
+    return grown, np.where(grown != 0, 0, np.maximum(cd, 1))
+
+
+def compare_state(gw, ow, where=""):
+    torch.cuda.synchronize()
+    for s, name in ((0, "sheep"), (1, "wolf")):
+        for f in FIELDS:
+            g = gw.agents(s, f).cpu().numpy()
+            o = ow.agents(s, f)
+            if not np.array_equal(g, o):
+                bad = np.flatnonzero(g != o)
+                raise AssertionError(f"{where} {name}.{f}: {bad.size} slots differ, first {bad[:5]} "
+                                     f"gpu {g[bad[:5]]} oracle {o[bad[:5]]}")
+    grown, wait = oracle_wait(ow)
+    np.testing.assert_array_equal(gw.grass("grown").cpu().numpy(), grown, err_msg=f"{where} grown")
+    np.testing.assert_array_equal(gw.grass("wait").cpu().numpy(), wait, err_msg=f"{where} wait")
+    gc, oc = gw.counters(), ow.counters()
+    for k in ("n_active", "next_id", "hw", "overflow", "step"):
+        assert gc[k] == oc[k], (where, k, gc[k], oc[k])
+
+
+def compare_stats(gst, ost, energy=True):
+    keys = ["n_start", "parents", "births", "starved", "eaten", "grass_eaten", "n_end", "hw", "overflow"]
+    if energy:
+        keys.append("energy")
+    for k in keys:
+        assert gst[k] == ost[k], (k, gst[k], ost[k])
+
+
+def make(eng, c, seed=None):
+    seed = c["seed"] if seed is None else seed
+    gw = eng.World(c["side"], seed, c["model"], c["params"], c["cap"], c["n0"])
+    ow = oracle.World(c["side"], seed, c["model"], c["params"], c["cap"], c["n0"])
+    return gw, ow
+
+
+def test_small_config_every_step(eng):
+    """40x40, 100 sheep / 25 wolves, capacity 2048/1024, 200 steps, seed 0."""
+    c = workloads.PRED_SMALL
+    gw, ow = make(eng, c)
+    compare_state(gw, ow, "init")
+    stats = gw.new_stats(1)
+    for t in range(c["steps"]):
+        gw.step(1, stats, want_energy=True)
+        ost = ow.step()[0]
+        gst = eng.decode_stats(stats)[0]
+        compare_stats(gst, ost)
+        assert gst["step"] == t
+        compare_state(gw, ow, f"step {t}")
+    gw.check()
+    # and the stored trajectory
+    import os
+    traj = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "pred_small_trajectory.txt"),
+                      dtype=np.int64, comments="#")
+    assert traj[-1].tolist() == [c["steps"] - 1] + gw.counters()["n_active"]
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_random_small_worlds(eng, seed):
+    rng = np.random.default_rng(500 + seed)
+    side = int(rng.integers(1, 40))
+    cap = (int(rng.integers(1, 700)), int(rng.integers(1, 300)))
+    n0 = (int(rng.integers(0, cap[0] + 1)), int(rng.integers(0, cap[1] + 1)))
+    params = workloads.predation_params(
+        sheep_gain=int(rng.integers(0, 8)), wolf_gain=int(rng.integers(0, 30)),
+        sheep_repro=float(rng.choice([0.0, 0.04, 0.3, 0.9])), wolf_repro=float(rng.choice([0.0, 0.05, 0.5])),
+        regrowth=int(rng.integers(1, 40)), sheep_metab=int(rng.integers(0, 3)),
+        wolf_metab=int(rng.integers(0, 3)), grass_init=float(rng.choice([0.1, 0.5, 0.95])))
+    c = dict(side=side, n0=n0, cap=cap, seed=seed, model=int(rng.integers(0, 1000)), params=params)
+    gw, ow = make(eng, c)
+    stats = gw.new_stats(60)
+    gw.step(60, stats, want_energy=True)
+    ost = ow.step(60)
+    for g, o in zip(eng.decode_stats(stats), ost):
+        compare_stats(g, o)
+    compare_state(gw, ow, f"seed {seed}")
+    gw.check()
+
+
+def test_graph_replay_equals_eager(eng):
+    c = dict(workloads.PRED_SMALL)
+    a, _ = make(eng, c)
+    b, _ = make(eng, c)
+    sa = a.new_stats(25)
+    sb = b.new_stats(25)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for _ in range(4):
+            a.step(25, sa)
+        b.step_graph(25, 4, sb, stream=s)
+    s.synchronize()
+    assert torch.equal(sa, sb)
+    for sp in range(2):
+        for f in FIELDS:
+            assert torch.equal(a.agents(sp, f), b.agents(sp, f))
+    assert a.counters() == b.counters()
+
+
+def test_checkpoint_resume_bit_exact(eng):
+    c = dict(workloads.PRED_SMALL)
+    a, ow = make(eng, c)
+    a.step(50)
+    img = a.save()
+    a.step(70)
+    b, _ = make(eng, c)
+    b.load(img)
+    b.step(70)
+    for sp in range(2):
+        for f in FIELDS:
+            assert torch.equal(a.agents(sp, f), b.agents(sp, f))
+    assert torch.equal(a.grass("wait"), b.grass("wait"))
+    assert a.counters() == b.counters()
+    ow.step(120)
+    compare_state(b, ow, "resumed")
+
+
+def test_overflow_truncates_like_oracle(eng):
+    params = workloads.predation_params(sheep_repro=0.5, wolf_repro=0.5, sheep_gain=6)
+    c = dict(side=10, n0=(30, 10), cap=(40, 20), seed=3, model=0, params=params)
+    gw, ow = make(eng, c)
+    gw.step(60)
+    ow.step(60)
+    compare_state(gw, ow, "overflow")
+    assert max(gw.counters()["overflow"]) == 1
+
+
+def test_large_config_first_steps(eng):
+    """2048x2048, 1M sheep / 250k wolves, capacity 8Mi / 4Mi: 12 steps, full state."""
+    c = workloads.PRED_LARGE
+    gw, ow = make(eng, c)
+    compare_state(gw, ow, "init")
+    stats = gw.new_stats(12)
+    gw.step(12, stats, want_energy=True)
+    ost = ow.step(12)
+    for g, o in zip(eng.decode_stats(stats), ost):
+        compare_stats(g, o)
+    compare_state(gw, ow, "step 12")
+    gw.check()
+
+
+@pytest.mark.slow
+def test_large_config_full_run(eng):
+    """The full 1000-step large run: populations every step, full state at the end."""
+    c = workloads.PRED_LARGE
+    gw, ow = make(eng, c)
+    stats = gw.new_stats(c["steps"])
+    gw.step(c["steps"], stats)
+    ost = ow.step(c["steps"])
+    for g, o in zip(eng.decode_stats(stats), ost):
+        compare_stats(g, o, energy=False)
+    compare_state(gw, ow, "end")
+    gw.check()
+
+
+def test_create_argument_errors(eng):
+    from paper_2508_16508_gb300 import abm
+    import ctypes as C
+    cfg = abm.abm_config()
+    cfg.side = 0
+    h = C.c_void_p()
+    assert abm.lib().abm_create(C.byref(cfg), None, C.byref(h)) == abm.ERR_ARG
+    cfg.side, cfg.cap[0], cfg.cap[1], cfg.n0[0] = 10, 5, 5, 6
+    cfg.params[4] = 3
+    assert abm.lib().abm_create(C.byref(cfg), None, C.byref(h)) == abm.ERR_ARG
