@@ -180,10 +180,11 @@ void orc_c1_init(int32_t* active, int32_t* fields, int64_t n, int F, uint32_t se
   }
 }
 
-/* One microbenchmark call at step c with threshold T and k records. Each slot
- * takes one MASK draw per call: word 0 decides removal, word 1 the choice.
- *   1. remove live slots whose word 0 is below T;
- *   2. chosen = slots live after 1 whose word 1 is below T; the i-th
+/* One microbenchmark call at step c with threshold T and k records. Slots 2j
+ * and 2j+1 share the MASK draw with counter slot word j: slot 2j decides
+ * removal on word 0 and the choice on word 1, slot 2j+1 on words 2 and 3.
+ *   1. remove live slots whose removal word is below T;
+ *   2. chosen = slots live after 1 whose choice word is below T; the i-th
  *      chosen slot (i < min(k, #chosen)) gets DELTA record i added;
  *   3. NEWREC record j goes to the j-th slot free after 1, j < min(k, #free).
  * Steps 2 and 3 touch disjoint slots. out_counts = removed, added, updated. */
@@ -192,11 +193,11 @@ void orc_c1_call(int32_t* active, int32_t* fields, int64_t n, int F, uint32_t se
   int32_t* mask = (int32_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
   int32_t* rec = (int32_t*)calloc((size_t)(k > 0 ? k : 1) * (size_t)F, sizeof(int32_t));
   for (int64_t i = 0; i < n; i++)
-    mask[i] = draw(seed, model, step, (uint32_t)i, ORC_P_MASK, 0, 0) < T;
+    mask[i] = draw(seed, model, step, (uint32_t)(i >> 1), ORC_P_MASK, 0, 2 * (int)(i & 1)) < T;
   out_counts[0] = orc_remove(active, mask, n);
 
   for (int64_t i = 0; i < n; i++)
-    mask[i] = active[i] && draw(seed, model, step, (uint32_t)i, ORC_P_MASK, 0, 1) < T;
+    mask[i] = active[i] && draw(seed, model, step, (uint32_t)(i >> 1), ORC_P_MASK, 0, 2 * (int)(i & 1) + 1) < T;
   orc_c1_records(seed, model, step, ORC_P_DELTA0, ORC_P_DELTA1, k, F, rec);
   out_counts[2] = orc_update_distinct(fields, n, F, mask, rec, NULL, k, 0, NULL);
 

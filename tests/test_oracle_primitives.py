@@ -205,10 +205,14 @@ def c1_call_brute(active, fields, seed, step, T, k):
     """Microbenchmark call restated with numpy on Philox draws."""
     n, F = fields.shape[1], fields.shape[0]
     active = active.copy(); fields = fields.copy().astype(np.int64)
-    mask = oracle.philox_words(seed, 0, step, oracle.P_MASK, 0, 0, n) < T
+    # slots 2j and 2j+1 share draw j: words (0, 1) and (2, 3) = (remove, choose)
+    half = (n + 1) // 2
+    w = np.stack([oracle.philox_words(seed, 0, step, oracle.P_MASK, 0, 0, half, word=q) for q in range(4)])
+    slot = np.arange(n)
+    mask = w[2 * (slot & 1), slot >> 1] < T
     removed = int(np.sum(active.astype(bool) & mask))
     active[mask] = 0
-    choose = oracle.philox_words(seed, 0, step, oracle.P_MASK, 0, 0, n, word=1) < T
+    choose = w[2 * (slot & 1) + 1, slot >> 1] < T
     chosen = np.flatnonzero(active.astype(bool) & choose)
     free = np.flatnonzero(active == 0)
     d = oracle.c1_records(seed, 0, step, oracle.P_DELTA0, oracle.P_DELTA1, k, F)
