@@ -207,7 +207,9 @@ def selective_update_leg(torch, engine, abm, hbm_peak, steps=8, warmup=3):
     """Selective-update microbenchmark: 2^24 slots x 8 fields, fused remove/update/add call."""
     c = workloads.SELECTIVE
     n, F = c["n"], c["F"]
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    # L2 eviction between timed calls by READING 256 MiB (a written buffer would leave
+    # dirty lines whose write-back lands inside the next timed call)
+    flush = torch.ones(64 << 20, dtype=torch.int32, device="cuda")
     out = {}
     for p in c["p"]:
         T, k = workloads.threshold(p), workloads.k_for(p, n)
@@ -219,7 +221,8 @@ def selective_update_leg(torch, engine, abm, hbm_peak, steps=8, warmup=3):
         for it in range(warmup + steps):
             s.philox_records(it, abm.P_NEWREC0, abm.P_NEWREC1, k, out=rec)
             s.philox_records(it, abm.P_DELTA0, abm.P_DELTA1, k, out=dl)
-            flush.fill_(it & 0xFF)  # evict the slab's live flags from L2
+            flush.max()
+            torch.cuda._sleep(100000)  # device busy while the host enqueues the timed call
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             s.selective_update(it, T, rec, dl, out_counts=cnt)
@@ -244,7 +247,8 @@ def selective_update_leg(torch, engine, abm, hbm_peak, steps=8, warmup=3):
     isw = torch.empty(M, dtype=torch.uint8, device="cuda")
     times = []
     for it in range(warmup + steps):
-        flush.fill_(it & 0xFF)
+        flush.max()
+        torch.cuda._sleep(100000)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         rv(res, prio, isw)

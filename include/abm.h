@@ -163,6 +163,11 @@ abm_status abm_selective_update(abm_slab* s, uint32_t step, uint32_t threshold,
                                 const int32_t* records, const int32_t* deltas, int32_t k,
                                 int32_t* out_counts, void* stream);
 
+/* Launch shape of abm_selective_update's passes: `threads` per CTA (128, 256
+ * or 512) and `ctas_per_sm` CTAs per SM (threads * ctas_per_sm <= 2048).
+ * Results never depend on it; the autotuner picks it. Default 256, 8. */
+abm_status abm_slab_tune(abm_slab* s, int32_t threads, int32_t ctas_per_sm, void* stream);
+
 /* Fill out[k][F] (device int32) with record j field f = word f%4 of
  * draw(step, j, purpose0 + (f >= 4 ? purpose1 - purpose0 : 0), 0) under the
  * slab's key -- the Philox-generated records of the microbenchmark. */

@@ -90,6 +90,7 @@ def _sig(L):
         "abm_add": ([vp, vp, i32, i32, vp, vp, vp], st),
         "abm_update_distinct": ([vp, C.POINTER(abm_pred), vp, vp, i32, i32, vp, vp, vp], st),
         "abm_selective_update": ([vp, u32, u32, vp, vp, i32, vp, vp], st),
+        "abm_slab_tune": ([vp, i32, i32, vp], st),
         "abm_philox_records": ([vp, u32, u32, u32, i32, vp, vp], st),
         "abm_slab_counters_get": ([vp, C.POINTER(abm_slab_counters), vp], st),
         "abm_resolve_table_init": ([vp, i32, vp], st),

@@ -21,7 +21,7 @@ typedef unsigned long long u64;
 typedef unsigned int u32;
 
 constexpr u64 kNoKey = 0xFFFFFFFFFFFFFFFFull;
-constexpr int kMaxSpin = 1 << 21;  // bounded waits: ~1-2 s with the back-off below
+constexpr int kMaxSpin = 1 << 23;  // bounded waits: ~2 s with the back-off below
 
 // Device error codes written into a handle's error word.
 constexpr int kErrTimeout = 1;
@@ -159,8 +159,8 @@ __device__ __forceinline__ void tile_prefix(const ScanCtl& ctl, int tile, u32 ta
             timed_out = true;
             break;
           }
-          __nanosleep(backoff);
-          if (backoff < 1024) backoff <<= 1;
+          if (spins > 16) __nanosleep(backoff);  // short spins first: the wait is usually brief
+          if (spins > 64 && backoff < 256) backoff <<= 1;
         }
         if (timed_out) break;
         const u32 incl_mask = __ballot_sync(0xFFFFFFFFu, tile_incl(v) != 0u);
@@ -225,6 +225,26 @@ __device__ __forceinline__ void warp_add(int* dst, int v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
   if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, v);
+}
+
+// Programmatic dependent launch: a kernel launched with launch_pdl() may
+// start before its predecessor in the stream has finished; it must call
+// griddep_wait() before touching anything the predecessor writes.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
 }  // namespace abm

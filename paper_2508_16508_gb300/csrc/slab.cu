@@ -29,9 +29,8 @@ int num_sms() {
   return g_num_sms;
 }
 
-constexpr int kSlabThreads = 256;
-constexpr int kSlabItems = 8;  // 8 slots per thread: two 128-bit loads of live flags
-constexpr int kSlabTile = kSlabThreads * kSlabItems;
+constexpr int kSlabThreads = 256;    // default CTA size of the slab passes
+constexpr int kSlabTileMax = 16384;  // slab arrays are padded to a multiple of this
 constexpr int kMaxFields = 16;
 
 struct SlabDev {
@@ -39,7 +38,7 @@ struct SlabDev {
   int32_t* fields;   // cap x Fp, agent-major
   int32_t* counters; // [0] n_active [1] next_id [2] overflow [3] scratch count
   int32_t* rec_idx;  // [cap] compacted record indices (scratch)
-  int32_t* pending;  // [2] scan totals handed from the last tile to the last CTA out
+  int32_t* meta;     // [4] pass-2 results for pass 3: rank counts, first id
   int* err;
   int cap, F, Fp;
   u32 seed, model;
@@ -78,8 +77,14 @@ enum Op { OP_SELECT = 0, OP_REMOVE = 1, OP_ADD = 2, OP_UPDATE = 3, OP_FUSED = 4,
 struct ScanArgs {
   SlabDev s;
   PredDev pred;
-  ScanCtl ctl;
+  u32* ctrl;               // [1] CTAs finished, [2] epoch (last-CTA-out bookkeeping)
+  u32* planeA;             // n/32 words each: selected / free
+  u32* planeB;             // chosen (fused call)
+  u32* totals;             // [2 * G] per-CTA counts
+  u32* wtotals;            // [2 * G * warps] per-warp counts
   int n;                   // slots (or array entries for OP_ARRAY)
+  int chunk;               // slots per CTA (a multiple of the sub-tile)
+  int G;                   // CTAs = number of chunks
   const int32_t* src;      // OP_ARRAY: mask array
   const int32_t* rec;      // records [k][F]
   const int32_t* rec2;     // OP_FUSED: deltas [k][F]
@@ -88,7 +93,8 @@ struct ScanArgs {
   int id_field;            // OP_ADD
   int use_rec_idx;         // OP_UPDATE with a record mask
   u32 step, threshold;     // OP_FUSED
-  int32_t* out_idx;        // OP_SELECT / OP_ARRAY: compacted indices; OP_ADD/OP_UPDATE: slots
+  int32_t* list_a;         // slots by rank: selected / free (caller's out_idx or scratch)
+  int32_t* list_b;         // slots by rank: chosen (fused call)
   int32_t* out_count;      // device outputs (nullable)
 };
 
@@ -112,151 +118,254 @@ __device__ __forceinline__ void apply_record(int32_t* dst, const int32_t* src, i
   }
 }
 
-template <int OP>
-__global__ void __launch_bounds__(kSlabThreads) k_scan_op(ScanArgs a, int ntiles) {
-  __shared__ u64 s_warp[kSlabThreads / 32 + 1];
-  __shared__ u32 s_bcast[2];
-  __shared__ int s_tile;
-  const u32 tag = launch_tag(a.ctl.ctrl);
-  const SlabDev& s = a.s;
-
-  while (true) {
-    const int tile = next_tile(a.ctl.ctrl, &s_tile);
-    if (tile >= ntiles) break;
-    const int base = tile * kSlabTile + threadIdx.x * kSlabItems;
-
-    int live[kSlabItems];
-    u32 fa = 0, fb = 0, removed = 0;  // bit masks over the thread's items
-    const int32_t* flag_src = OP == OP_ARRAY ? a.src : s.active;
+template <int THREADS>
+__device__ __forceinline__ void block_sum2(u32& a, u32& b, u64* s_red) {
+  u64 v = ((u64)a << 32) | b;
 #pragma unroll
-    for (int v = 0; v < kSlabItems / 4; ++v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) s_red[warp] = v;
+  __syncthreads();
+  u64 t = 0;
+#pragma unroll
+  for (int w = 0; w < THREADS / 32; ++w) t += s_red[w];
+  a = (u32)(t >> 32);
+  b = (u32)t;
+}
+
+// Flags live in two bit-planes of one bit per slot: A = selected / free,
+// B = chosen (fused call); word w of a plane covers slots [32w, 32w + 32).
+//
+// Both passes use the same static partition: CTA b owns the slots
+// [b*chunk, (b+1)*chunk) and warp w of it the contiguous segment
+// [b*chunk + w*seg, ... + seg), seg a multiple of 512 slots. In each 512-slot
+// step, lane l handles the 16 consecutive slots [16l, 16l + 16).
+constexpr int kLaneSlots = 16;
+constexpr int kWarpStep = 32 * kLaneSlots;
+
+// Pass 1: flags from four 128-bit loads of live flags per lane; the lane's
+// 16-bit masks are paired with the neighbour lane's into plane words.
+template <int OP, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_count(ScanArgs a) {
+  constexpr int WARPS = THREADS / 32;
+  __shared__ u64 s_red[WARPS];
+  const SlabDev& s = a.s;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int seg = a.chunk / WARPS;
+  const int wlo = blockIdx.x * a.chunk + warp * seg;
+  const int whi = min(a.n, wlo + seg);
+  const int32_t* flag_src = OP == OP_ARRAY ? a.src : s.active;
+  u32 ca = 0, cb = 0;
+  for (int b0 = wlo; b0 < whi; b0 += kWarpStep) {
+    const int base = b0 + lane * kLaneSlots;
+    int live[kLaneSlots];
+#pragma unroll
+    for (int v = 0; v < kLaneSlots / 4; ++v) {
+      const int b = base + 4 * v;
       int4 q = make_int4(0, 0, 0, 0);
-      if (base + 4 * v + 3 < a.n) {
-        q = *reinterpret_cast<const int4*>(flag_src + base + 4 * v);
+      if (b + 3 < a.n) {
+        q = *reinterpret_cast<const int4*>(flag_src + b);
       } else {
-        if (base + 4 * v + 0 < a.n) q.x = flag_src[base + 4 * v + 0];
-        if (base + 4 * v + 1 < a.n) q.y = flag_src[base + 4 * v + 1];
-        if (base + 4 * v + 2 < a.n) q.z = flag_src[base + 4 * v + 2];
+        if (b + 0 < a.n) q.x = flag_src[b + 0];
+        if (b + 1 < a.n) q.y = flag_src[b + 1];
+        if (b + 2 < a.n) q.z = flag_src[b + 2];
       }
       live[4 * v + 0] = q.x; live[4 * v + 1] = q.y; live[4 * v + 2] = q.z; live[4 * v + 3] = q.w;
     }
+    u32 ma = 0, mb = 0, mr = 0;  // 16-bit masks over the lane's slots
+    if (OP == OP_FUSED) {
 #pragma unroll
-    for (int j = 0; j < kSlabItems; ++j) {
-      const int slot = base + j;
-      const bool valid = slot < a.n;
-      bool fA = false, fB = false;
-      if (OP == OP_ARRAY) {
-        fA = valid && live[j] != 0;
-      } else if (OP == OP_SELECT || OP == OP_REMOVE || OP == OP_UPDATE) {
-        fA = valid && eval_pred(a.pred, s, slot, live[j]);
-      } else if (OP == OP_ADD) {
-        fA = valid && live[j] == 0;
-      } else {  // OP_FUSED
-        if (valid) {
-          const uint4 u = draw4(s.seed, s.model, a.step, (u32)slot, ABM_P_MASK, 0u);
-          const bool rm = live[j] && u.x < a.threshold;
-          const bool alive = live[j] && !rm;
-          fA = !alive;
-          fB = alive && u.y < a.threshold;
-          if (rm) removed |= 1u << j;
-        }
+      for (int m = 0; m < kLaneSlots / 2; ++m) {
+        const int slot = base + 2 * m;
+        // slots 2j and 2j+1 share draw j: words (x, y) and (z, w) = (remove, choose)
+        const uint4 u = draw4(s.seed, s.model, a.step, (u32)slot >> 1, ABM_P_MASK, 0u);
+        const bool rm0 = live[2 * m] && u.x < a.threshold;
+        const bool rm1 = live[2 * m + 1] && u.z < a.threshold;
+        const bool al0 = live[2 * m] && !rm0, al1 = live[2 * m + 1] && !rm1;
+        ma |= ((u32)(slot < a.n && !al0) | ((u32)(slot + 1 < a.n && !al1) << 1)) << (2 * m);
+        mb |= ((u32)(al0 && u.y < a.threshold) | ((u32)(al1 && u.w < a.threshold) << 1)) << (2 * m);
+        mr |= ((u32)rm0 | ((u32)rm1 << 1)) << (2 * m);
       }
-      fa |= (u32)fA << j;
-      fb |= (u32)fB << j;
-    }
-    u32 ex_a, ex_b, tot_a, tot_b, pre_a, pre_b;
-    block_scan2<kSlabThreads>(__popc(fa), __popc(fb), ex_a, ex_b, tot_a, tot_b, s_warp);
-    tile_prefix<kSlabThreads>(a.ctl, tile, tag, tot_a, tot_b, pre_a, pre_b, s_bcast);
-    u32 ra = pre_a + ex_a, rb = pre_b + ex_b;
-
-    // the last tile knows the totals; the last CTA out applies them
-    if (tile == ntiles - 1 && threadIdx.x == 0) {
-      s.pending[0] = (int)(pre_a + tot_a);
-      s.pending[1] = (int)(pre_b + tot_b);
-    }
-
-    // scatter
-    const int next_id = (OP == OP_ADD && a.id_field >= 0) ? s.counters[1] : 0;
-    const int nrec = (OP == OP_UPDATE && a.use_rec_idx) ? s.counters[3] : a.k;
-    int newlive[kSlabItems];
-    bool dirty = false;
+    } else {
 #pragma unroll
-    for (int j = 0; j < kSlabItems; ++j) {
-      const int slot = base + j;
-      newlive[j] = live[j];
-      if (!((fa >> j) & 1u)) {
-        if (OP == OP_FUSED && ((removed >> j) & 1u)) { newlive[j] = 0; dirty = true; }
-        if (OP == OP_FUSED && ((fb >> j) & 1u)) {
-          if ((int)rb < a.k)
-            apply_record(s.fields + (size_t)slot * s.Fp, a.rec2 + (size_t)rb * s.F, s.F, true);
-          ++rb;
+      for (int j = 0; j < kLaneSlots; ++j) {
+        const int slot = base + j;
+        bool f = false;
+        if (slot < a.n) {
+          if (OP == OP_ARRAY) f = live[j] != 0;
+          else if (OP == OP_ADD) f = live[j] == 0;
+          else f = eval_pred(a.pred, s, slot, live[j]);
         }
-        continue;
+        ma |= (u32)f << j;
       }
-      const u32 rank = ra++;
-      if (OP == OP_SELECT || OP == OP_ARRAY) {
-        a.out_idx[rank] = slot;
-      } else if (OP == OP_REMOVE) {
-        newlive[j] = 0;
-        dirty = true;
-      } else if (OP == OP_ADD || OP == OP_FUSED) {
-        if ((int)rank < a.k) {
-          int32_t* dst = s.fields + (size_t)slot * s.Fp;
-          apply_record(dst, a.rec + (size_t)rank * s.F, s.F, false);
-          if (OP == OP_ADD && a.id_field >= 0) dst[a.id_field] = (int)((u32)next_id + rank);
-          if (OP == OP_ADD && a.out_idx) a.out_idx[rank] = slot;
-          newlive[j] = 1;
-          dirty = true;
-        } else if (OP == OP_FUSED && ((removed >> j) & 1u)) {
-          newlive[j] = 0;
-          dirty = true;
-        }
-      } else if (OP == OP_UPDATE) {
-        if ((int)rank < nrec) {
-          const int rj = a.use_rec_idx ? s.rec_idx[rank] : (int)rank;
-          apply_record(s.fields + (size_t)slot * s.Fp, a.rec + (size_t)rj * s.F, s.F,
-                       a.op_kind == ABM_OP_ADD);
-          if (a.out_idx) a.out_idx[rank] = slot;
+      if (OP == OP_REMOVE) mr = ma;
+    }
+    // removed slots become placeholders now (the fused call refills some of
+    // them in pass 2): rewrite only the 4-slot groups that changed
+    if (OP == OP_REMOVE || OP == OP_FUSED) {
+#pragma unroll
+      for (int v = 0; v < kLaneSlots / 4; ++v) {
+        const u32 g = (mr >> (4 * v)) & 0xFu;
+        if (!g) continue;
+        const int b = base + 4 * v;
+        const int4 q = make_int4((g & 1u) ? 0 : live[4 * v], (g & 2u) ? 0 : live[4 * v + 1],
+                                 (g & 4u) ? 0 : live[4 * v + 2], (g & 8u) ? 0 : live[4 * v + 3]);
+        if (b + 3 < a.n) {
+          *reinterpret_cast<int4*>(s.active + b) = q;
+        } else {
+          if (b + 0 < a.n) s.active[b + 0] = q.x;
+          if (b + 1 < a.n) s.active[b + 1] = q.y;
+          if (b + 2 < a.n) s.active[b + 2] = q.z;
         }
       }
     }
-    if (OP == OP_REMOVE || OP == OP_ADD || OP == OP_FUSED) {
-      if (dirty) {
-#pragma unroll
-        for (int v = 0; v < kSlabItems / 4; ++v) {
-          const int b0 = base + 4 * v;
-          if (b0 + 3 < a.n) {
-            *reinterpret_cast<int4*>(s.active + b0) =
-                make_int4(newlive[4 * v], newlive[4 * v + 1], newlive[4 * v + 2], newlive[4 * v + 3]);
-          } else {
-            for (int j = 0; j < 4; ++j)
-              if (b0 + j < a.n) s.active[b0 + j] = newlive[4 * v + j];
-          }
-        }
+    ca += __popc(ma);
+    cb += __popc(mb);
+    if (OP != OP_REMOVE) {
+      const u32 na = __shfl_down_sync(0xFFFFFFFFu, ma, 1);
+      const u32 nb = __shfl_down_sync(0xFFFFFFFFu, mb, 1);
+      if (!(lane & 1) && base < a.n) {
+        a.planeA[base >> 5] = ma | (na << 16);
+        if (OP == OP_FUSED) a.planeB[base >> 5] = mb | (nb << 16);
       }
     }
   }
-  if (last_cta_out(a.ctl.ctrl)) {
-    const int A = ntiles > 0 ? s.pending[0] : 0;
-    const int B = ntiles > 0 ? s.pending[1] : 0;
+  u64 v = ((u64)ca << 32) | cb;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  if (lane == 0) {
+    a.wtotals[2 * (blockIdx.x * WARPS + warp)] = (u32)(v >> 32);
+    a.wtotals[2 * (blockIdx.x * WARPS + warp) + 1] = (u32)v;
+  }
+  block_sum2<THREADS>(ca, cb, s_red);
+  if (threadIdx.x == 0) {
+    a.totals[2 * blockIdx.x] = ca;
+    a.totals[2 * blockIdx.x + 1] = cb;
+  }
+  if (OP == OP_REMOVE) {
+    if (last_cta_out(a.ctrl)) {
+      int A = 0;
+      for (int b = 0; b < a.G; ++b) A += (int)a.totals[2 * b];
+      s.counters[0] -= A;
+      if (a.out_count) *a.out_count = A;
+      __threadfence();
+    }
+  }
+}
+
+// Pass 2: ranks from the CTA prefix + warp prefix + a warp scan per step.
+// Plane A (possibly dense) is compacted word by word with the lanes
+// transposed onto the word's 32 slots, so flagged lanes write consecutive
+// ranks (coalesced); steps and words with no rank below the limit are
+// skipped. Plane B (sparse: chosen survivors) is walked per lane.
+template <int OP, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_scatter(ScanArgs a) {
+  constexpr int WARPS = THREADS / 32;
+  __shared__ u64 s_red[WARPS];
+  griddep_wait();
+  const SlabDev& s = a.s;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  u32 pa = 0, pb = 0, ta = 0, tb = 0;
+  for (int j = threadIdx.x; j < a.G; j += THREADS) {
+    const u32 x = a.totals[2 * j], y = a.totals[2 * j + 1];
+    if (j < (int)blockIdx.x) {
+      pa += x;
+      pb += y;
+    }
+    ta += x;
+    tb += y;
+  }
+  block_sum2<THREADS>(pa, pb, s_red);
+  block_sum2<THREADS>(ta, tb, s_red);
+  {
+    u32 x = 0, y = 0;
+    if (lane < warp) {
+      x = a.wtotals[2 * (blockIdx.x * WARPS + lane)];
+      y = a.wtotals[2 * (blockIdx.x * WARPS + lane) + 1];
+    }
+    u64 v = ((u64)x << 32) | y;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    pa += (u32)(v >> 32);
+    pb += (u32)v;
+  }
+  const int nrec = (OP == OP_UPDATE && a.use_rec_idx) ? s.counters[3] : a.k;
+  const u32 limit = (u32)(OP == OP_UPDATE ? nrec : (OP == OP_SELECT || OP == OP_ARRAY ? 0x7FFFFFFF : a.k));
+  const u32 limit_b = (u32)a.k;
+  const u32 half_lt = (1u << (lane & 15)) - 1u;
+  const int seg = a.chunk / WARPS;
+  const int wlo = blockIdx.x * a.chunk + warp * seg;
+  const int whi = min(a.n, wlo + seg);
+  for (int b0 = wlo; b0 < whi; b0 += kWarpStep) {
+    const int base = b0 + lane * kLaneSlots;
+    u32 ma = 0, mb = 0;
+    if (base < a.n) {
+      ma = (a.planeA[base >> 5] >> (16 * (lane & 1))) & 0xFFFFu;
+      if (OP == OP_FUSED) mb = (a.planeB[base >> 5] >> (16 * (lane & 1))) & 0xFFFFu;
+    }
+    const u32 c = (u32)__popc(ma) | ((u32)__popc(mb) << 16);
+    u32 inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const u32 t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+      if (lane >= o) inc += t;
+    }
+    const u32 tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
+    const u32 ex = inc - c;
+    const u32 ra = pa + (ex & 0xFFFFu);
+    u32 rb = pb + (ex >> 16);
+    pa += tot & 0xFFFFu;
+    pb += tot >> 16;
+    // plane A: lanes (2w, 2w+1) hold word w of this step
+    u32 todo = __ballot_sync(0xFFFFFFFFu, ma != 0 && ra < limit);
+    todo = (todo | (todo >> 1)) & 0x55555555u;  // one bit per word (its even lane)
+    while (todo) {
+      const int w = (__ffs(todo) - 1) >> 1;
+      todo &= todo - 1;
+      const int owner = 2 * w + (lane >> 4);
+      const u32 om = __shfl_sync(0xFFFFFFFFu, ma, owner);
+      const u32 orank = __shfl_sync(0xFFFFFFFFu, ra, owner);
+      const int slot = b0 + 32 * w + lane;
+      const u32 rank = orank + __popc(om & half_lt);
+      if (((om >> (lane & 15)) & 1u) && rank < limit) {
+        a.list_a[rank] = slot;
+        if (OP == OP_ADD || OP == OP_FUSED) s.active[slot] = 1;
+      }
+    }
+    // plane B: per lane, in slot order
+    if (OP == OP_FUSED) {
+      while (mb && rb < limit_b) {
+        const int j = __ffs(mb) - 1;
+        mb &= mb - 1;
+        a.list_b[rb++] = base + j;
+      }
+    }
+  }
+  if (last_cta_out(a.ctrl)) {
+    const int A = (int)ta, B = (int)tb;
     if (OP == OP_SELECT || OP == OP_ARRAY) {
       if (a.out_count) *a.out_count = A;
       if (OP == OP_ARRAY) s.counters[3] = A;
-    } else if (OP == OP_REMOVE) {
-      s.counters[0] -= A;
-      if (a.out_count) *a.out_count = A;
     } else if (OP == OP_ADD) {
       const int r = min(a.k, A);
+      s.meta[0] = r;
+      s.meta[1] = 0;
+      s.meta[2] = s.counters[1];  // first id of this batch
       s.counters[0] += r;
       if (a.id_field >= 0) s.counters[1] += r;
       if (a.k > A) s.counters[2] = 1;
       if (a.out_count) *a.out_count = r;
     } else if (OP == OP_UPDATE) {
-      const int nrec = a.use_rec_idx ? s.counters[3] : a.k;
-      if (a.out_count) *a.out_count = min(A, nrec);
-    } else {  // OP_FUSED: A = free after removal, B = chosen survivors
+      const int r = min(A, nrec);
+      s.meta[0] = r;
+      s.meta[1] = 0;
+      if (a.out_count) *a.out_count = r;
+    } else if (OP == OP_FUSED) {  // A = free after removal, B = chosen survivors
       const int n_before = s.counters[0];
       const int added = min(a.k, A);
+      s.meta[0] = added;
+      s.meta[1] = min(a.k, B);
       s.counters[0] = s.cap - A + added;
       if (a.k > A) s.counters[2] = 1;
       if (a.out_count) {
@@ -266,6 +375,92 @@ __global__ void __launch_bounds__(kSlabThreads) k_scan_op(ScanArgs a, int ntiles
       }
     }
     __threadfence();
+  }
+}
+
+// Pass 3: record j goes to (or is added to) the slot at rank j. Four records
+// per thread per round, all loads issued before the stores; coalesced record
+// reads, one 16/32-byte field run written per slot.
+template <int OP>
+__global__ void __launch_bounds__(256, 4) k_apply(ScanArgs a) {
+  griddep_wait();
+  const SlabDev& s = a.s;
+  const int ra = s.meta[0], rb = s.meta[1];
+  const int id0 = s.meta[2];
+  const int total = ra + rb;
+  const int stride = gridDim.x * blockDim.x;
+  const bool f8 = s.F == 8 && s.Fp == 8 && ((((uintptr_t)a.rec) | ((uintptr_t)a.rec2)) & 15) == 0;
+  for (int j0 = blockIdx.x * blockDim.x + threadIdx.x; j0 < total; j0 += 4 * stride) {
+    if (f8) {
+      int slot[4];
+      int4 r0[4], r1[4];
+      bool add[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int j = j0 + u * stride;
+        slot[u] = -1;
+        add[u] = false;
+        if (j < total) {
+          const int32_t* src;
+          if (j < ra) {
+            slot[u] = a.list_a[j];
+            const int rj = (OP == OP_UPDATE && a.use_rec_idx) ? s.rec_idx[j] : j;
+            src = a.rec + (size_t)rj * 8;
+            add[u] = OP == OP_UPDATE && a.op_kind == ABM_OP_ADD;
+          } else {
+            slot[u] = a.list_b[j - ra];
+            src = a.rec2 + (size_t)(j - ra) * 8;
+            add[u] = true;
+          }
+          r0[u] = __ldg(reinterpret_cast<const int4*>(src));
+          r1[u] = __ldg(reinterpret_cast<const int4*>(src) + 1);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (slot[u] < 0) continue;
+        int4* d = reinterpret_cast<int4*>(s.fields + (size_t)slot[u] * 8);
+        if (OP == OP_ADD && a.id_field >= 0) {  // stamp the id into the record before storing it
+          const int j = j0 + u * stride;
+          const int id = (int)((u32)id0 + (u32)j);
+          int4& r = a.id_field < 4 ? r0[u] : r1[u];
+          switch (a.id_field & 3) {
+            case 0: r.x = id; break;
+            case 1: r.y = id; break;
+            case 2: r.z = id; break;
+            default: r.w = id; break;
+          }
+        }
+        if (add[u]) {
+          const int4 o0 = d[0], o1 = d[1];
+          r0[u] = make_int4((int)((u32)o0.x + (u32)r0[u].x), (int)((u32)o0.y + (u32)r0[u].y),
+                            (int)((u32)o0.z + (u32)r0[u].z), (int)((u32)o0.w + (u32)r0[u].w));
+          r1[u] = make_int4((int)((u32)o1.x + (u32)r1[u].x), (int)((u32)o1.y + (u32)r1[u].y),
+                            (int)((u32)o1.z + (u32)r1[u].z), (int)((u32)o1.w + (u32)r1[u].w));
+        }
+        d[0] = r0[u];
+        d[1] = r1[u];
+      }
+      continue;
+    }
+    for (int u = 0; u < 4; ++u) {
+      const int j = j0 + u * stride;
+      if (j >= total) break;
+      if (j < ra) {
+        const int slot = a.list_a[j];
+        int32_t* dst = s.fields + (size_t)slot * s.Fp;
+        if (OP == OP_UPDATE) {
+          const int rj = a.use_rec_idx ? s.rec_idx[j] : j;
+          apply_record(dst, a.rec + (size_t)rj * s.F, s.F, a.op_kind == ABM_OP_ADD);
+        } else {
+          apply_record(dst, a.rec + (size_t)j * s.F, s.F, false);
+          if (OP == OP_ADD && a.id_field >= 0) dst[a.id_field] = (int)((u32)id0 + (u32)j);
+        }
+      } else {
+        const int i = j - ra;
+        apply_record(s.fields + (size_t)a.list_b[i] * s.Fp, a.rec2 + (size_t)i * s.F, s.F, true);
+      }
+    }
   }
 }
 
@@ -331,16 +526,20 @@ using namespace abm;
 
 struct abm_slab {
   SlabDev d;
-  u64* tiles;
-  u32* ctrl;      // [4] main scan, [4..8) array scan
-  u64* tiles2;
-  int ntiles_max;
+  u32* planes;    // 2 x n_pad / 32 words: bit-planes A, B of the slab passes
+  u32* planes2;   // n_pad / 32 words: plane A of record-mask compaction
+  u32* totals;    // [2 * max CTAs] per-CTA counts (slab passes)
+  u32* totals2;   // the same for record-mask compaction
+  u32* wtotals;   // [2 * max CTAs * 16 warps] per-warp counts
+  u32* wtotals2;
+  int32_t* lista;  // [cap] scratch slot lists when the caller wants none
+  int32_t* listb;
+  u32* ctrl;      // [0..4) slab passes, [4..8) record-mask compaction
   int n_pad;
-  int grid;
+  int max_ctas;
+  // shape of the fused selective-update pass (abm_slab_tune)
+  int fused_threads, fused_ctas_per_sm;
 };
-
-static ScanCtl ctl_main(abm_slab* s) { return ScanCtl{s->tiles, s->ctrl, s->d.err}; }
-static ScanCtl ctl_aux(abm_slab* s) { return ScanCtl{s->tiles2, s->ctrl + 4, s->d.err}; }
 
 extern "C" const char* abm_strerror(abm_status st) {
   switch (st) {
@@ -363,10 +562,16 @@ extern "C" abm_status abm_slab_destroy(abm_slab* s) {
   cudaFree(s->d.fields);
   cudaFree(s->d.counters);
   cudaFree(s->d.rec_idx);
-  cudaFree(s->d.pending);
   cudaFree(s->d.err);
-  cudaFree(s->tiles);
-  cudaFree(s->tiles2);
+  cudaFree(s->planes);
+  cudaFree(s->planes2);
+  cudaFree(s->totals);
+  cudaFree(s->totals2);
+  cudaFree(s->wtotals);
+  cudaFree(s->wtotals2);
+  cudaFree(s->lista);
+  cudaFree(s->listb);
+  cudaFree(s->d.meta);
   cudaFree(s->ctrl);
   delete s;
   return ABM_OK;
@@ -386,27 +591,32 @@ extern "C" abm_status abm_slab_create(int32_t capacity, int32_t n_fields, uint32
   s->d.Fp = (n_fields + 3) & ~3;
   s->d.seed = seed;
   s->d.model = model;
-  s->ntiles_max = (capacity + kSlabTile - 1) / kSlabTile;
-  s->n_pad = s->ntiles_max * kSlabTile;
+  s->n_pad = ((capacity + kSlabTileMax - 1) / kSlabTileMax) * kSlabTileMax;
+  s->max_ctas = num_sms() * 16;
+  s->fused_threads = 256;
+  s->fused_ctas_per_sm = 8;
   bool ok = cudaMalloc(&s->d.active, sizeof(int32_t) * (size_t)s->n_pad) == cudaSuccess &&
             cudaMalloc(&s->d.fields, sizeof(int32_t) * (size_t)s->n_pad * s->d.Fp) == cudaSuccess &&
             cudaMalloc(&s->d.counters, sizeof(int32_t) * 4) == cudaSuccess &&
             cudaMalloc(&s->d.rec_idx, sizeof(int32_t) * (size_t)capacity) == cudaSuccess &&
             cudaMalloc(&s->d.err, sizeof(int)) == cudaSuccess &&
-            cudaMalloc(&s->d.pending, sizeof(int32_t) * 2) == cudaSuccess &&
-            cudaMalloc(&s->tiles, sizeof(u64) * (size_t)s->ntiles_max) == cudaSuccess &&
-            cudaMalloc(&s->tiles2, sizeof(u64) * (size_t)s->ntiles_max) == cudaSuccess &&
+            cudaMalloc(&s->planes, sizeof(u32) * 2 * (size_t)(s->n_pad / 32)) == cudaSuccess &&
+            cudaMalloc(&s->planes2, sizeof(u32) * (size_t)(s->n_pad / 32)) == cudaSuccess &&
+            cudaMalloc(&s->totals, sizeof(u32) * 2 * (size_t)s->max_ctas) == cudaSuccess &&
+            cudaMalloc(&s->totals2, sizeof(u32) * 2 * (size_t)s->max_ctas) == cudaSuccess &&
+            cudaMalloc(&s->wtotals, sizeof(u32) * 32 * (size_t)s->max_ctas) == cudaSuccess &&
+            cudaMalloc(&s->wtotals2, sizeof(u32) * 32 * (size_t)s->max_ctas) == cudaSuccess &&
+            cudaMalloc(&s->lista, sizeof(int32_t) * (size_t)capacity) == cudaSuccess &&
+            cudaMalloc(&s->listb, sizeof(int32_t) * (size_t)capacity) == cudaSuccess &&
+            cudaMalloc(&s->d.meta, sizeof(int32_t) * 4) == cudaSuccess &&
             cudaMalloc(&s->ctrl, sizeof(u32) * 8) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     abm_slab_destroy(s);
     return ABM_ERR_OOM;
   }
-  s->grid = num_sms() * 8;
   if (cudaMemsetAsync(s->d.counters, 0, sizeof(int32_t) * 4, st) != cudaSuccess ||
       cudaMemsetAsync(s->d.err, 0, sizeof(int), st) != cudaSuccess ||
-      cudaMemsetAsync(s->tiles, 0, sizeof(u64) * (size_t)s->ntiles_max, st) != cudaSuccess ||
-      cudaMemsetAsync(s->tiles2, 0, sizeof(u64) * (size_t)s->ntiles_max, st) != cudaSuccess ||
       cudaMemsetAsync(s->ctrl, 0, sizeof(u32) * 8, st) != cudaSuccess) {
     abm_slab_destroy(s);
     return ABM_ERR_CUDA;
@@ -495,15 +705,47 @@ static PredDev to_dev(const abm_pred* p) {
   return d;
 }
 
-template <int OP>
-static abm_status launch_scan(abm_slab* s, const ScanArgs& a, const ScanCtl& ctl, cudaStream_t st) {
+// Up to three launches per operation: flags + per-warp / per-CTA counts, then
+// ranks + slot lists, then the record moves. Each warp owns one static
+// segment of slots in the first two passes; no CTA waits for another.
+template <int OP, int THREADS = kSlabThreads>
+static abm_status launch_scan(abm_slab* s, const ScanArgs& a, bool aux, cudaStream_t st,
+                              int ctas_per_sm = 8) {
   ScanArgs b = a;
-  b.ctl = ctl;
-  const int ntiles = (b.n + kSlabTile - 1) / kSlabTile;
-  const int grid = std::max(1, std::min(ntiles, s->grid));
-  k_scan_op<OP><<<grid, kSlabThreads, 0, st>>>(b, ntiles);
+  const size_t words = (size_t)(s->n_pad / 32);
+  b.planeA = aux ? s->planes2 : s->planes;
+  b.planeB = s->planes + words;
+  b.totals = aux ? s->totals2 : s->totals;
+  b.wtotals = aux ? s->wtotals2 : s->wtotals;
+  b.ctrl = aux ? s->ctrl + 4 : s->ctrl;
+  constexpr int SUB = (THREADS / 32) * kWarpStep;  // chunks are whole warp steps
+  if (b.n <= 0) {
+    if (b.out_count) ABM_CUDA_TRY(cudaMemsetAsync(b.out_count, 0, sizeof(int32_t), st));
+    if (OP == OP_ARRAY) ABM_CUDA_TRY(cudaMemsetAsync(s->d.counters + 3, 0, sizeof(int32_t), st));
+    return ABM_OK;
+  }
+  const int target = std::max(1, std::min(num_sms() * ctas_per_sm, s->max_ctas));
+  const long per = ((long)b.n + target - 1) / target;
+  b.chunk = (int)(((per + SUB - 1) / SUB) * SUB);
+  b.G = (int)(((long)b.n + b.chunk - 1) / b.chunk);
+  k_count<OP, THREADS><<<b.G, THREADS, 0, st>>>(b);
   ABM_LAUNCH_CHECK();
+  // the next passes may launch while the previous one drains; they wait on
+  // it (griddepcontrol) before reading its results
+  if (OP != OP_REMOVE) ABM_CUDA_TRY(launch_pdl(k_scatter<OP, THREADS>, b.G, THREADS, st, b));
+  if (OP == OP_ADD || OP == OP_UPDATE || OP == OP_FUSED)
+    ABM_CUDA_TRY(launch_pdl(k_apply<OP>, num_sms() * 8, 256, st, b));
   return ABM_OK;
+}
+
+static abm_status launch_fused(abm_slab* s, const ScanArgs& a, cudaStream_t st) {
+  const int c = s->fused_ctas_per_sm;
+  switch (s->fused_threads) {
+    case 128: return launch_scan<OP_FUSED, 128>(s, a, false, st, c);
+    case 256: return launch_scan<OP_FUSED, 256>(s, a, false, st, c);
+    case 512: return launch_scan<OP_FUSED, 512>(s, a, false, st, c);
+  }
+  return ABM_ERR_ARG;
 }
 
 static ScanArgs base_args(abm_slab* s) {
@@ -520,9 +762,9 @@ extern "C" abm_status abm_select(abm_slab* s, const abm_pred* pred, int32_t* out
   if (!s || !pred_ok(s, pred) || !out_idx || !out_count) return ABM_ERR_ARG;
   ScanArgs a = base_args(s);
   a.pred = to_dev(pred);
-  a.out_idx = out_idx;
+  a.list_a = out_idx;
   a.out_count = out_count;
-  return launch_scan<OP_SELECT>(s, a, ctl_main(s), (cudaStream_t)stream);
+  return launch_scan<OP_SELECT>(s, a, false, (cudaStream_t)stream);
 }
 
 extern "C" abm_status abm_remove(abm_slab* s, const abm_pred* pred, int32_t* out_removed, void* stream) {
@@ -530,7 +772,7 @@ extern "C" abm_status abm_remove(abm_slab* s, const abm_pred* pred, int32_t* out
   ScanArgs a = base_args(s);
   a.pred = to_dev(pred);
   a.out_count = out_removed;
-  return launch_scan<OP_REMOVE>(s, a, ctl_main(s), (cudaStream_t)stream);
+  return launch_scan<OP_REMOVE>(s, a, false, (cudaStream_t)stream);
 }
 
 extern "C" abm_status abm_add(abm_slab* s, const int32_t* records, int32_t k, int32_t id_field,
@@ -540,9 +782,9 @@ extern "C" abm_status abm_add(abm_slab* s, const int32_t* records, int32_t k, in
   a.rec = records;
   a.k = k;
   a.id_field = id_field;
-  a.out_idx = out_slots;
+  a.list_a = out_slots ? out_slots : s->lista;
   a.out_count = out_added;
-  return launch_scan<OP_ADD>(s, a, ctl_main(s), (cudaStream_t)stream);
+  return launch_scan<OP_ADD>(s, a, false, (cudaStream_t)stream);
 }
 
 extern "C" abm_status abm_update_distinct(abm_slab* s, const abm_pred* pred, const int32_t* records,
@@ -556,8 +798,8 @@ extern "C" abm_status abm_update_distinct(abm_slab* s, const abm_pred* pred, con
     ScanArgs r = base_args(s);
     r.n = k;
     r.src = record_mask;
-    r.out_idx = s->d.rec_idx;
-    abm_status e = launch_scan<OP_ARRAY>(s, r, ctl_aux(s), st);
+    r.list_a = s->d.rec_idx;
+    abm_status e = launch_scan<OP_ARRAY>(s, r, true, st);
     if (e != ABM_OK) return e;
   }
   ScanArgs a = base_args(s);
@@ -566,9 +808,9 @@ extern "C" abm_status abm_update_distinct(abm_slab* s, const abm_pred* pred, con
   a.k = k;
   a.op_kind = op;
   a.use_rec_idx = record_mask != nullptr;
-  a.out_idx = out_slots;
+  a.list_a = out_slots ? out_slots : s->lista;
   a.out_count = out_applied;
-  return launch_scan<OP_UPDATE>(s, a, ctl_main(s), st);
+  return launch_scan<OP_UPDATE>(s, a, false, st);
 }
 
 extern "C" abm_status abm_selective_update(abm_slab* s, uint32_t step, uint32_t threshold,
@@ -582,7 +824,19 @@ extern "C" abm_status abm_selective_update(abm_slab* s, uint32_t step, uint32_t 
   a.step = step;
   a.threshold = threshold;
   a.out_count = out_counts;
-  return launch_scan<OP_FUSED>(s, a, ctl_main(s), (cudaStream_t)stream);
+  a.list_a = s->lista;
+  a.list_b = s->listb;
+  return launch_fused(s, a, (cudaStream_t)stream);
+}
+
+extern "C" abm_status abm_slab_tune(abm_slab* s, int32_t threads, int32_t ctas_per_sm, void* stream) {
+  (void)stream;
+  if (!s || (threads != 128 && threads != 256 && threads != 512) || ctas_per_sm < 1 || ctas_per_sm > 16 ||
+      threads * ctas_per_sm > 2048)
+    return ABM_ERR_ARG;
+  s->fused_threads = threads;
+  s->fused_ctas_per_sm = ctas_per_sm;
+  return ABM_OK;
 }
 
 extern "C" abm_status abm_philox_records(abm_slab* s, uint32_t step, uint32_t purpose0, uint32_t purpose1,

@@ -102,6 +102,9 @@ class Slab:
              ptr(records), ptr(deltas), k, ptr(out), _stream(stream))
         return out
 
+    def tune(self, threads: int, ctas_per_sm: int, stream=None):
+        call("abm_slab_tune", self.h, threads, ctas_per_sm, _stream(stream))
+
     def philox_records(self, step: int, purpose0: int, purpose1: int, k: int, out=None,
                        stream=None) -> torch.Tensor:
         out = torch.empty((max(k, 1), self.F), **self._i32) if out is None else out

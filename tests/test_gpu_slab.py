@@ -82,10 +82,12 @@ def test_selective_update_equals_separate_calls(eng):
         a.selective_update(step, T, rec, dl)
         # the same call as remove -> distinct update -> add through the generic API,
         # with the two draws made into explicit masks
-        u0 = torch.from_numpy(oracle.philox_words(5, 0, step, oracle.P_MASK, 0, 0, n, 0).astype(np.int64))
-        u1 = torch.from_numpy(oracle.philox_words(5, 0, step, oracle.P_MASK, 0, 0, n, 1).astype(np.int64))
-        rm = (u0 < T).to(torch.int32).cuda()
-        ch = (u1 < T).to(torch.int32).cuda()
+        # slots 2j and 2j+1 share draw j: words (0, 1) and (2, 3) = (remove, choose)
+        w = np.stack([oracle.philox_words(5, 0, step, oracle.P_MASK, 0, 0, (n + 1) // 2, q)
+                      for q in range(4)]).astype(np.int64)
+        slot = np.arange(n)
+        rm = torch.from_numpy((w[2 * (slot & 1), slot >> 1] < T).astype(np.int32)).cuda()
+        ch = torch.from_numpy((w[2 * (slot & 1) + 1, slot >> 1] < T).astype(np.int32)).cuda()
         b.remove(abm.pred(abm.PRED_MASK, mask=rm))
         b.update_distinct(abm.pred(abm.PRED_MASK, mask=ch), dl, op=abm.OP_ADD)
         b.add(rec)
