@@ -289,6 +289,111 @@ abm_status abm_world_counters_get(abm_world* w, abm_world_counters* out, void* s
 abm_status abm_save(abm_world* w, void* buf, size_t* bytes, void* stream);
 abm_status abm_load(abm_world* w, const void* buf, size_t bytes, void* stream);
 
+/* ========================================================================== */
+/* Batched predation: many independent models in one persistent launch        */
+/* (ABMax vectorises models with vmap over Sets, Section 2, Table 2)          */
+/* ========================================================================== */
+/*
+ * Every model follows the rules of abm_step with its own side, key
+ * (seed, model), params, capacities and initial populations. One CTA runs one
+ * model at a time (largest models first); per-model slabs sit at offsets in
+ * shared device arrays. Limits per model as for abm_create.
+ */
+typedef struct abm_batch abm_batch;
+
+typedef struct abm_batch_model {
+  int32_t side;
+  uint32_t seed, model;
+  int32_t params[8];
+  int32_t cap[2];
+  int32_t n0[2];
+} abm_batch_model;
+
+typedef struct abm_batch_counters {
+  int32_t n_active[2], next_id[2], hw[2], overflow[2], extent[2], step, reserved;
+  int64_t agent_steps; /* sum over the steps run of the live agents at step start */
+} abm_batch_counters;
+
+/* Sweep of a model's slabs in every phase: the whole capacity (the paper's
+ * static shapes, placeholders included) or the extent (highest slot ever
+ * used + 1). Results are identical; only the work differs. */
+#define ABM_SWEEP_CAPACITY 0
+#define ABM_SWEEP_EXTENT 1
+
+/* models: host array of n. Allocates and initialises every model (synchronises `stream`). */
+abm_status abm_batch_create(const abm_batch_model* models, int32_t n, void* stream, abm_batch** out);
+abm_status abm_batch_destroy(abm_batch* b);
+/* Launch shape: CTA size (128..1024), CTAs per SM, and steps per launch
+ * (a run of nsteps is split into ceil(nsteps / steps_per_launch) launches,
+ * each replayable in a CUDA graph). Results never depend on it. */
+abm_status abm_batch_tune(abm_batch* b, int32_t threads, int32_t ctas_per_sm, int32_t steps_per_launch);
+/* Advance every model by nsteps (asynchronous on `stream`). */
+abm_status abm_batch_run(abm_batch* b, int32_t nsteps, int32_t sweep, void* stream);
+/* Host copy of every model's counters (out: host abm_batch_counters[n]; synchronises `stream`). */
+abm_status abm_batch_counters_get(abm_batch* b, abm_batch_counters* out, void* stream);
+/* State of model m, as abm_read_agents / abm_read_grass (dst: device int32[cap] / [side^2]). */
+abm_status abm_batch_read_agents(abm_batch* b, int32_t m, int32_t species, int32_t which, int32_t* dst,
+                                 void* stream);
+abm_status abm_batch_read_grass(abm_batch* b, int32_t m, int32_t which, int32_t* dst, void* stream);
+/* Device-side list of the models whose births were truncated by a full slab
+ * (list: device int32[n], count: device int32). */
+abm_status abm_batch_overflowed(abm_batch* b, int32_t* list, int32_t* count, void* stream);
+/* Per-model digest (device uint64[n]): an order-independent hash of the
+ * live agents (species, slot, cell, energy, id, age), the grass (steps
+ * until edible) and the counters. It does not depend on the capacity, so
+ * runs of the same models at different capacities compare equal iff their
+ * observable states are equal (up to hash collisions). */
+abm_status abm_batch_digest(abm_batch* b, uint64_t* out, void* stream);
+abm_status abm_batch_check(abm_batch* b, void* stream);
+/* Total slots per species and total cells allocated by the batch. */
+abm_status abm_batch_info(abm_batch* b, int64_t* slots_sheep, int64_t* slots_wolf, int64_t* cells);
+
+/* ========================================================================== */
+/* Learned capacity: an FP32 MLP predicting a high quantile of a model's peak */
+/* population, which sizes its slabs (no counterpart in the paper; Section 4 */
+/* requires the maximum number of agents in advance)                          */
+/* ========================================================================== */
+/*
+ * n_in -> `layers` hidden layers of `hidden` ReLU units -> n_out, row-major
+ * FP32. Parameters are one flat device array: for each linear map l,
+ * W_l[din][dout] then b_l[dout]. He-uniform initial weights from Philox
+ * (purpose 15, key (seed, 0x4D4C50)), zero biases. Inputs and outputs are
+ * device float[B][n_in] / [B][n_out]; B <= max_batch.
+ */
+typedef struct abm_mlp abm_mlp;
+abm_status abm_mlp_create(int32_t n_in, int32_t hidden, int32_t layers, int32_t n_out, uint32_t seed,
+                          int32_t max_batch, void* stream, abm_mlp** out);
+abm_status abm_mlp_destroy(abm_mlp* n);
+abm_status abm_mlp_forward(abm_mlp* n, const float* x, int32_t B, float* y, void* stream);
+/* Pinball (quantile tau) loss averaged over the B x n_out outputs and its
+ * gradient w.r.t. every parameter (readable via abm_mlp_params). Row r of
+ * the batch is row (perm_a * (perm_m0 + r) + perm_c) mod perm_rows of x and
+ * y when perm_rows > 0 (a cheap shuffle), else row r. loss_out: device
+ * float, nullable. */
+abm_status abm_mlp_gradients(abm_mlp* n, const float* x, const float* y, int32_t B, float tau,
+                             int64_t perm_rows, int64_t perm_a, int64_t perm_c, int64_t perm_m0,
+                             float* loss_out, void* stream);
+/* abm_mlp_gradients followed by one Adam step (beta 0.9 / 0.999, eps 1e-8). */
+abm_status abm_mlp_train_step(abm_mlp* n, const float* x, const float* y, int32_t B, float tau, float lr,
+                              int64_t perm_rows, int64_t perm_a, int64_t perm_c, int64_t perm_m0,
+                              float* loss_out, void* stream);
+/* Device pointers to the flat parameter and gradient arrays, and their length. */
+abm_status abm_mlp_params(abm_mlp* n, float** params, float** grads, int64_t* count);
+abm_status abm_mlp_reset_adam(abm_mlp* n, void* stream);
+/* Copy `count` (= the parameter count) floats between a device buffer and the parameters / gradients. */
+abm_status abm_mlp_set_params(abm_mlp* n, const float* src, int64_t count, void* stream);
+abm_status abm_mlp_get_params(abm_mlp* n, float* dst, int64_t count, void* stream);
+abm_status abm_mlp_get_grads(abm_mlp* n, float* dst, int64_t count, void* stream);
+/* Features of models: table = device int32[B][12] (side, n0 sheep, n0 wolves,
+ * the 8 params, horizon); x[b] = log1p(side), log1p(n0 sheep), log1p(n0
+ * wolves), params[j] / nominal[j] (as unsigned), horizon / 500.
+ * nominal: device int32[8]. */
+abm_status abm_capacity_features(const int32_t* table, int32_t B, const int32_t* nominal, float* x, void* stream);
+/* Capacities from predicted log peaks yhat[B][2]: cap = min(cap_max,
+ * roundup(ceil(exp(yhat) * (1 + margin)), round_to)), at least n0 and round_to. */
+abm_status abm_capacity_from_prediction(const float* yhat, int32_t B, float margin, int32_t round_to,
+                                        const int32_t* cap_max, const int32_t* n0, int32_t* cap, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

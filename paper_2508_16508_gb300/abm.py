@@ -67,6 +67,20 @@ class abm_world_counters(C.Structure):
                 ("reserved", C.c_int32)]
 
 
+class abm_batch_model(C.Structure):
+    _fields_ = [("side", C.c_int32), ("seed", C.c_uint32), ("model", C.c_uint32),
+                ("params", C.c_int32 * 8), ("cap", C.c_int32 * 2), ("n0", C.c_int32 * 2)]
+
+
+class abm_batch_counters(C.Structure):
+    _fields_ = [("n_active", C.c_int32 * 2), ("next_id", C.c_int32 * 2), ("hw", C.c_int32 * 2),
+                ("overflow", C.c_int32 * 2), ("extent", C.c_int32 * 2), ("step", C.c_int32),
+                ("reserved", C.c_int32), ("agent_steps", C.c_int64)]
+
+
+SWEEP_CAPACITY, SWEEP_EXTENT = 0, 1
+
+
 class abm_slab_counters(C.Structure):
     _fields_ = [("n_active", C.c_int32), ("next_id", C.c_int32), ("overflow", C.c_int32),
                 ("reserved", C.c_int32)]
@@ -106,6 +120,29 @@ def _sig(L):
         "abm_world_counters_get": ([vp, C.POINTER(abm_world_counters), vp], st),
         "abm_save": ([vp, vp, C.POINTER(C.c_size_t), vp], st),
         "abm_load": ([vp, vp, C.c_size_t, vp], st),
+        "abm_batch_create": ([C.POINTER(abm_batch_model), i32, vp, pp], st),
+        "abm_batch_destroy": ([vp], st),
+        "abm_batch_tune": ([vp, i32, i32, i32], st),
+        "abm_batch_run": ([vp, i32, i32, vp], st),
+        "abm_batch_counters_get": ([vp, C.POINTER(abm_batch_counters), vp], st),
+        "abm_batch_read_agents": ([vp, i32, i32, i32, vp, vp], st),
+        "abm_batch_read_grass": ([vp, i32, i32, vp, vp], st),
+        "abm_batch_overflowed": ([vp, vp, vp, vp], st),
+        "abm_batch_check": ([vp, vp], st),
+        "abm_batch_info": ([vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)], st),
+        "abm_mlp_create": ([i32, i32, i32, i32, u32, i32, vp, pp], st),
+        "abm_mlp_destroy": ([vp], st),
+        "abm_mlp_forward": ([vp, vp, i32, vp, vp], st),
+        "abm_mlp_gradients": ([vp, vp, vp, i32, C.c_float, i64, i64, i64, i64, vp, vp], st),
+        "abm_mlp_train_step": ([vp, vp, vp, i32, C.c_float, C.c_float, i64, i64, i64, i64, vp, vp], st),
+        "abm_mlp_params": ([vp, pp, pp, C.POINTER(i64)], st),
+        "abm_mlp_reset_adam": ([vp, vp], st),
+        "abm_mlp_set_params": ([vp, vp, i64, vp], st),
+        "abm_mlp_get_params": ([vp, vp, i64, vp], st),
+        "abm_mlp_get_grads": ([vp, vp, i64, vp], st),
+        "abm_batch_digest": ([vp, vp, vp], st),
+        "abm_capacity_features": ([vp, i32, vp, vp, vp], st),
+        "abm_capacity_from_prediction": ([vp, i32, C.c_float, i32, vp, vp, vp, vp], st),
     }
     for name, (args, res) in sigs.items():
         f = getattr(L, name)

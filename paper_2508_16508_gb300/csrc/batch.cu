@@ -1,0 +1,677 @@
+// Batched predation: thousands of independent wolf-sheep-grass models of
+// uneven size in one persistent launch (ABMax vectorises many models with
+// vmap over Sets, Section 2 and Table 2; here each model gets a CTA).
+//
+// A CTA takes the next model from a ticket (models ordered largest first),
+// runs the requested steps of it -- every phase separated by __syncthreads,
+// compaction by block scans -- and takes the next. Each model has its own
+// capacity slabs at offsets in shared arrays. The sweep over a model's slab is
+// either its full capacity (the static shapes of the paper: placeholders are
+// visited every step) or its extent (highest slot ever used + 1); both give
+// the same results, and the capacity sweep is what a tighter capacity speeds
+// up. A CTA never waits for another CTA.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "pred_rules.cuh"
+
+namespace abm {
+
+struct BModel {
+  int side, ncells;
+  u32 seed, model;
+  int prm[8];
+  int cap[2];       // slots per species (capacity)
+  int cap_pad[2];   // allocated slots (multiple of 16)
+  int n0[2];
+  long long oa[2];  // slot offset of each species' slab
+  long long oc;     // cell offset
+};
+
+struct BCtr {
+  int n_active[2], next_id[2], hw[2], overflow[2], extent[2], step, pad;
+  long long agent_steps;  // sum over steps run of the live agents at step start
+};
+
+struct BatchDev {
+  const BModel* models;
+  BCtr* ctr;
+  int nmodels;
+  int32_t* active[2];
+  int4* agent[2];
+  int32_t* plist[2];
+  int32_t* flist[2];
+  int32_t* regrow;
+  u64* gclaim;
+  u64* victim;
+  u64* wclaim;
+  const int32_t* order;
+  u32* ctrl;  // [0] model ticket, [1] CTAs finished, [2] epoch
+  int* err;
+};
+
+// the model a CTA is working on, in shared memory
+struct MCtx {
+  BModel m;
+  int n_active[2], next_id[2], hw[2], overflow[2], extent[2], step;
+  long long agent_steps;
+  int n_start[2], P[2], F[2], starved[2], eaten, grass;
+};
+
+template <int T>
+__device__ __forceinline__ void b_move(const BatchDev& b, MCtx& c, int S, int sweep, int t) {
+  const int32_t* act = b.active[S] + c.m.oa[S];
+  int4* ag = b.agent[S] + c.m.oa[S];
+  u64* victim = b.victim + c.m.oc;
+  const int L = c.m.side;
+  const int metab = c.m.prm[PRM_SHEEP_METAB + S];
+  const int nq = (sweep + 3) >> 2;
+  for (int q = threadIdx.x; q < nq; q += T) {
+    const int4 a4v = reinterpret_cast<const int4*>(act)[q];
+    const int a4[4] = {a4v.x, a4v.y, a4v.z, a4v.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (!a4[j]) continue;
+      const int slot = 4 * q + j;
+      int4 a = ag[slot];
+      if (S == 0) victim[a.x] = kNoKey;
+      const u32 dir = draw(c.m.seed, c.m.model, (u32)t, (u32)slot, ABM_P_MOVE, (u32)S) >> 29;
+      const int cell = step_cell(a.x, L, dir);
+      a.x = cell;
+      a.y -= metab;
+      a.w += 1;
+      ag[slot] = a;
+      if (S == 0) {
+        if (b.regrow[c.m.oc + cell] <= t)
+          atomicMin(&b.gclaim[c.m.oc + cell], claim_key(draw(c.m.seed, c.m.model, (u32)t, (u32)slot, ABM_P_PRIO, 0u), slot));
+      } else {
+        if (victim[cell] != kNoKey)
+          atomicMin(&b.wclaim[c.m.oc + cell], claim_key(draw(c.m.seed, c.m.model, (u32)t, (u32)slot, ABM_P_PRIO, 1u), slot));
+      }
+    }
+  }
+}
+
+// eat (claim winners), select parents, kill the starving, compact the free
+// slots and the parents (ranks by block scans, chunk by chunk)
+template <int T>
+__device__ __forceinline__ void b_scan(const BatchDev& b, MCtx& c, int S, int sweep, int t, u64* s_warp,
+                                       int* s_acc) {
+  int32_t* act = b.active[S] + c.m.oa[S];
+  int4* ag = b.agent[S] + c.m.oa[S];
+  int32_t* plist = b.plist[S] + c.m.oa[S];
+  int32_t* flist = b.flist[S] + c.m.oa[S];
+  u64* claim = (S == 0 ? b.gclaim : b.wclaim) + c.m.oc;
+  u64* victim = b.victim + c.m.oc;
+  const int gain = c.m.prm[S];
+  const u32 Tr = (u32)c.m.prm[PRM_SHEEP_T + S];
+  const int regrowth = c.m.prm[PRM_REGROWTH];
+  const int bound = c.n_active[S];
+  int starved = 0, won = 0;
+  u32 pf = 0, pp = 0;
+  for (int c0 = 0; c0 < sweep; c0 += 4 * T) {
+    const int base = c0 + 4 * threadIdx.x;
+    int a4[4] = {0, 0, 0, 0};
+    if (base < sweep) {
+      const int4 v = reinterpret_cast<const int4*>(act)[base >> 2];
+      a4[0] = v.x; a4[1] = v.y; a4[2] = v.z; a4[3] = v.w;
+    }
+    u32 fr = 0, par = 0;
+    bool died = false;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int slot = base + j;
+      if (slot >= sweep) continue;
+      if (!a4[j]) {
+        fr |= 1u << j;
+        continue;
+      }
+      int4 a = ag[slot];
+      const int cell = a.x;
+      const u64 cl = claim[cell];
+      if (cl != kNoKey && (u32)cl == (u32)slot) {
+        a.y += gain;
+        ag[slot].y = a.y;
+        claim[cell] = kNoKey;
+        ++won;
+        if (S == 0) {
+          b.regrow[c.m.oc + cell] = t + regrowth;
+        } else {
+          const u64 v = victim[cell];
+          b.active[0][c.m.oa[0] + (u32)v] = 0;
+          victim[cell] = kNoKey;
+        }
+      }
+      if (a.y < 0) {
+        a4[j] = 0;
+        died = true;
+        ++starved;
+      } else {
+        if (draw(c.m.seed, c.m.model, (u32)t, (u32)slot, ABM_P_REPRO, (u32)S) < Tr) par |= 1u << j;
+        if (S == 0)
+          atomicMin(&victim[cell], claim_key(draw(c.m.seed, c.m.model, (u32)t, (u32)slot, ABM_P_VICTIM, 0u), slot));
+      }
+    }
+    u32 ex_f, ex_p, tot_f, tot_p;
+    block_scan2<T>(__popc(fr), __popc(par), ex_f, ex_p, tot_f, tot_p, s_warp);
+    u32 rf = pf + ex_f, rp = pp + ex_p;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if ((fr >> j) & 1u) {
+        if ((int)rf < bound) flist[rf] = base + j;
+        ++rf;
+      }
+      if ((par >> j) & 1u) plist[rp++] = base + j;
+    }
+    if (died) reinterpret_cast<int4*>(act)[base >> 2] = make_int4(a4[0], a4[1], a4[2], a4[3]);
+    pf += tot_f;
+    pp += tot_p;
+  }
+  // per-CTA sums of the winners and the starved
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    starved += __shfl_xor_sync(0xFFFFFFFFu, starved, o);
+    won += __shfl_xor_sync(0xFFFFFFFFu, won, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (starved) atomicAdd(&s_acc[0], starved);
+    if (won) atomicAdd(&s_acc[1], won);
+  }
+  if (threadIdx.x == 0) {
+    c.P[S] = (int)pp;
+    c.F[S] = (int)pf;
+  }
+}
+
+// children: the i-th parent (ascending slot) fills the i-th free slot
+template <int T>
+__device__ __forceinline__ void b_births(const BatchDev& b, MCtx& c, int S, int r, int t) {
+  int32_t* act = b.active[S] + c.m.oa[S];
+  int4* ag = b.agent[S] + c.m.oa[S];
+  const int32_t* plist = b.plist[S] + c.m.oa[S];
+  const int32_t* flist = b.flist[S] + c.m.oa[S];
+  const int Fin = c.F[S], ext = c.extent[S];
+  const int id0 = c.next_id[S];
+  for (int i = threadIdx.x; i < r; i += T) {
+    const int p = plist[i];
+    const int slot = i < Fin ? flist[i] : ext + (i - Fin);
+    const int4 pa = ag[p];
+    const int half = pa.y >> 1;
+    ag[p].y = pa.y - half;
+    ag[slot] = make_int4(pa.x, half, (int)((u32)id0 + (u32)i), 0);
+    act[slot] = 1;
+    if (S == 0)
+      atomicMin(&b.victim[c.m.oc + pa.x], claim_key(draw(c.m.seed, c.m.model, (u32)t, (u32)slot, ABM_P_VICTIM, 0u), slot));
+  }
+}
+
+// after a species' births (thread 0): its counters. avail = free slots in
+// the whole capacity (both sweeps count them the same way).
+__device__ __forceinline__ void b_count_births(const BatchDev& b, MCtx& c, int S, int r, int starved, int avail) {
+  const int Fin = c.F[S], ext = c.extent[S];
+  const int n_after = c.n_start[S] + r;
+  if (n_after > c.hw[S]) c.hw[S] = n_after;
+  c.n_active[S] = n_after - starved;
+  c.next_id[S] += r;
+  if (r > Fin) {
+    c.extent[S] = ext + (r - Fin);
+  } else if (r > 0) {
+    const int last = b.flist[S][c.m.oa[S] + r - 1] + 1;  // children fill free slots below the extent
+    if (last > c.extent[S]) c.extent[S] = last;
+  }
+  if (c.P[S] > avail) c.overflow[S] = 1;
+}
+
+template <int T>
+__global__ void __launch_bounds__(T) k_batch_run(BatchDev b, int nsteps, int sweep_extent) {
+  __shared__ MCtx c;
+  __shared__ u64 s_warp[T / 32 + 1];
+  __shared__ int s_acc[4];
+  __shared__ int s_idx;
+  while (true) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_idx = (int)atomicAdd(&b.ctrl[0], 1u);
+    __syncthreads();
+    const int idx = s_idx;
+    if (idx >= b.nmodels) break;
+    const int mi = b.order[idx];
+    if (threadIdx.x == 0) {
+      c.m = b.models[mi];
+      const BCtr k = b.ctr[mi];
+      for (int s = 0; s < 2; ++s) {
+        c.n_active[s] = k.n_active[s];
+        c.next_id[s] = k.next_id[s];
+        c.hw[s] = k.hw[s];
+        c.overflow[s] = k.overflow[s];
+        c.extent[s] = k.extent[s];
+      }
+      c.step = k.step;
+      c.agent_steps = k.agent_steps;
+    }
+    __syncthreads();
+    for (int it = 0; it < nsteps; ++it) {
+      const int t = c.step;
+      if (threadIdx.x == 0) {
+        c.n_start[0] = c.n_active[0];
+        c.n_start[1] = c.n_active[1];
+        c.agent_steps += c.n_active[0] + c.n_active[1];
+        s_acc[0] = s_acc[1] = s_acc[2] = s_acc[3] = 0;
+      }
+      const int sw0 = sweep_extent ? c.extent[0] : c.m.cap[0];
+      __syncthreads();
+      // sheep: move + grass claims; eat, select, die, compact
+      b_move<T>(b, c, 0, sw0, t);
+      __syncthreads();
+      b_scan<T>(b, c, 0, sw0, t, s_warp, s_acc);
+      __syncthreads();
+      const int avail0 = c.F[0] + (sweep_extent ? c.m.cap[0] - c.extent[0] : 0);
+      const int r0 = min(c.P[0], avail0);
+      const int sw1 = sweep_extent ? c.extent[1] : c.m.cap[1];
+      // sheep births, concurrently the wolves' move + victim claims (a wolf's
+      // claim only needs the cell to hold a live sheep; every newborn lamb
+      // sits with its live parent)
+      b_births<T>(b, c, 0, r0, t);
+      b_move<T>(b, c, 1, sw1, t);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        b_count_births(b, c, 0, r0, s_acc[0], avail0);
+        c.starved[0] = s_acc[0];
+        c.grass = s_acc[1];
+        s_acc[0] = s_acc[1] = 0;
+      }
+      __syncthreads();
+      b_scan<T>(b, c, 1, sw1, t, s_warp, s_acc);
+      __syncthreads();
+      const int avail1 = c.F[1] + (sweep_extent ? c.m.cap[1] - c.extent[1] : 0);
+      const int r1 = min(c.P[1], avail1);
+      b_births<T>(b, c, 1, r1, t);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        b_count_births(b, c, 1, r1, s_acc[0], avail1);
+        c.starved[1] = s_acc[0];
+        c.eaten = s_acc[1];
+        c.n_active[0] -= s_acc[1];
+        c.step = t + 1;
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      BCtr k;
+      for (int s = 0; s < 2; ++s) {
+        k.n_active[s] = c.n_active[s];
+        k.next_id[s] = c.next_id[s];
+        k.hw[s] = c.hw[s];
+        k.overflow[s] = c.overflow[s];
+        k.extent[s] = c.extent[s];
+      }
+      k.step = c.step;
+      k.pad = 0;
+      k.agent_steps = c.agent_steps;
+      b.ctr[mi] = k;
+    }
+  }
+  last_cta_out(b.ctrl);
+}
+
+// one CTA per model: initial agents, grass, empty claim tables, counters
+__global__ void k_batch_init(BatchDev b) {
+  const int mi = blockIdx.x;
+  const BModel m = b.models[mi];
+  for (int s = 0; s < 2; ++s) {
+    const int gain = m.prm[s];
+    for (int k = threadIdx.x; k < m.cap_pad[s]; k += blockDim.x) {
+      const long long g = m.oa[s] + k;
+      if (k < m.n0[s]) {
+        const uint4 u = draw4(m.seed, m.model, ABM_INIT_STEP, (u32)k, ABM_P_INIT_AGENT, (u32)s);
+        b.agent[s][g] = make_int4(uniform_below(u.x, m.ncells), uniform_below(u.y, 2 * gain), k, 0);
+        b.active[s][g] = 1;
+      } else {
+        b.agent[s][g] = make_int4(0, 0, 0, 0);
+        b.active[s][g] = 0;
+      }
+    }
+  }
+  for (int cidx = threadIdx.x; cidx < m.ncells; cidx += blockDim.x) {
+    const uint4 u = draw4(m.seed, m.model, ABM_INIT_STEP, (u32)cidx, ABM_P_GRASS_INIT, 2u);
+    const bool grown = u.x < (u32)m.prm[PRM_GRASS_T];
+    const int wait = uniform_below(u.y, m.prm[PRM_REGROWTH]);
+    const long long g = m.oc + cidx;
+    b.regrow[g] = grown ? 0 : max(wait, 1);
+    b.gclaim[g] = kNoKey;
+    b.victim[g] = kNoKey;
+    b.wclaim[g] = kNoKey;
+  }
+  if (threadIdx.x == 0) {
+    BCtr k;
+    std::memset(&k, 0, sizeof(k));
+    for (int s = 0; s < 2; ++s) {
+      k.n_active[s] = m.n0[s];
+      k.next_id[s] = m.n0[s];
+      k.hw[s] = m.n0[s];
+      k.extent[s] = m.n0[s];
+    }
+    b.ctr[mi] = k;
+  }
+}
+
+__global__ void k_batch_grass(BatchDev b, int mi, int which, int32_t* dst) {
+  const BModel m = b.models[mi];
+  const int T = b.ctr[mi].step;
+  for (int cidx = blockIdx.x * blockDim.x + threadIdx.x; cidx < m.ncells; cidx += gridDim.x * blockDim.x) {
+    const int r = b.regrow[m.oc + cidx];
+    dst[cidx] = which == 0 ? (r <= T ? 1 : 0) : (r <= T ? 0 : r - T);
+  }
+}
+
+// list of the models whose births were ever truncated (device-side, one CTA)
+__global__ void k_batch_overflowed(BatchDev b, int32_t* list, int32_t* count) {
+  __shared__ int n;
+  if (threadIdx.x == 0) n = 0;
+  __syncthreads();
+  for (int base = 0; base < b.nmodels; base += blockDim.x) {
+    const int m = base + threadIdx.x;
+    const bool ov = m < b.nmodels && (b.ctr[m].overflow[0] | b.ctr[m].overflow[1]);
+    const u32 bal = __ballot_sync(0xFFFFFFFFu, ov);
+    __shared__ int warp_base[32];
+    if ((threadIdx.x & 31) == 0) warp_base[threadIdx.x >> 5] = __popc(bal);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int acc = n;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        const int x = warp_base[w];
+        warp_base[w] = acc;
+        acc += x;
+      }
+      n = acc;
+    }
+    __syncthreads();
+    if (ov) list[warp_base[threadIdx.x >> 5] + __popc(bal & ((1u << (threadIdx.x & 31)) - 1u))] = m;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *count = n;
+}
+
+// splitmix64 finaliser (Steele, Lea, Flood, "Fast splittable pseudorandom
+// number generators", OOPSLA 2014)
+__device__ __forceinline__ u64 mix64(u64 z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// order-independent digest of one model's observable state: live agents
+// (species, slot, cell, energy, id, age), grass (grown, wait) and counters
+__global__ void k_batch_digest(BatchDev b, u64* out) {
+  __shared__ u64 s[32];
+  const int mi = blockIdx.x;
+  const BModel m = b.models[mi];
+  const BCtr k = b.ctr[mi];
+  u64 h = 0;
+  for (int sp = 0; sp < 2; ++sp) {
+    for (int i = threadIdx.x; i < k.extent[sp]; i += blockDim.x) {
+      if (!b.active[sp][m.oa[sp] + i]) continue;
+      const int4 a = b.agent[sp][m.oa[sp] + i];
+      u64 z = mix64(((u64)sp << 40) ^ (u64)(u32)i);
+      z = mix64(z ^ (((u64)(u32)a.x << 32) | (u32)a.y));
+      z = mix64(z ^ (((u64)(u32)a.z << 32) | (u32)a.w));
+      h += z;
+    }
+  }
+  for (int c = threadIdx.x; c < m.ncells; c += blockDim.x) {
+    const int r = b.regrow[m.oc + c];
+    const u32 wait = r <= k.step ? 0u : (u32)(r - k.step);
+    h += mix64((2ull << 40) ^ ((u64)(u32)c << 8) ^ ((u64)wait << 40));
+  }
+  for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xFFFFFFFFu, h, o);
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = h;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    u64 t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s[w];
+    for (int sp = 0; sp < 2; ++sp) {
+      t += mix64(0xC0FFEEull + sp * 7 + ((u64)(u32)k.n_active[sp] << 20));
+      t += mix64(0xBADull + sp * 11 + ((u64)(u32)k.next_id[sp] << 20));
+      t += mix64(0xF00Dull + sp * 13 + ((u64)(u32)k.hw[sp] << 20));
+    }
+    out[mi] = t;
+  }
+}
+
+}  // namespace abm
+
+// ============================================================================
+using namespace abm;
+
+struct abm_batch {
+  BatchDev d;
+  BModel* models_dev;
+  std::vector<BModel> models;
+  long long slots[2], cells;
+  int threads, ctas_per_sm, steps_per_launch;
+};
+
+static void batch_free(abm_batch* b) {
+  for (int s = 0; s < 2; ++s) {
+    cudaFree(b->d.active[s]);
+    cudaFree(b->d.agent[s]);
+    cudaFree(b->d.plist[s]);
+    cudaFree(b->d.flist[s]);
+  }
+  cudaFree(b->d.regrow);
+  cudaFree(b->d.gclaim);
+  cudaFree(b->d.victim);
+  cudaFree(b->d.wclaim);
+  cudaFree(b->d.ctr);
+  cudaFree(b->models_dev);
+  cudaFree((void*)b->d.order);
+  cudaFree(b->d.ctrl);
+  cudaFree(b->d.err);
+  delete b;
+}
+
+extern "C" abm_status abm_batch_destroy(abm_batch* b) {
+  if (!b) return ABM_ERR_ARG;
+  batch_free(b);
+  return ABM_OK;
+}
+
+extern "C" abm_status abm_batch_create(const abm_batch_model* models, int32_t n, void* stream, abm_batch** out) {
+  if (!models || n < 1 || !out) return ABM_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  abm_batch* b = new (std::nothrow) abm_batch();
+  if (!b) return ABM_ERR_OOM;
+  b->models.resize((size_t)n);
+  long long oa[2] = {0, 0}, oc = 0;
+  for (int i = 0; i < n; ++i) {
+    const abm_batch_model& in = models[i];
+    if (in.side < 1 || in.side > 46340 || in.params[4] < 1) {
+      delete b;
+      return ABM_ERR_ARG;
+    }
+    BModel& m = b->models[(size_t)i];
+    std::memset(&m, 0, sizeof(m));
+    m.side = in.side;
+    m.ncells = in.side * in.side;
+    m.seed = in.seed;
+    m.model = in.model;
+    std::memcpy(m.prm, in.params, sizeof(m.prm));
+    for (int s = 0; s < 2; ++s) {
+      if (in.cap[s] < 1 || in.cap[s] > (1 << 28) - 1 || in.n0[s] < 0 || in.n0[s] > in.cap[s] || in.params[s] < 0 ||
+          in.params[5 + s] < 0) {
+        delete b;
+        return ABM_ERR_ARG;
+      }
+      m.cap[s] = in.cap[s];
+      m.cap_pad[s] = (in.cap[s] + 15) & ~15;
+      m.n0[s] = in.n0[s];
+      m.oa[s] = oa[s];
+      oa[s] += m.cap_pad[s];
+    }
+    m.oc = oc;
+    oc += m.ncells;
+  }
+  b->slots[0] = oa[0];
+  b->slots[1] = oa[1];
+  b->cells = oc;
+  BatchDev& d = b->d;
+  d.nmodels = n;
+  bool ok = true;
+  for (int s = 0; s < 2; ++s) {
+    ok = ok && cudaMalloc(&d.active[s], sizeof(int32_t) * (size_t)oa[s]) == cudaSuccess;
+    ok = ok && cudaMalloc(&d.agent[s], sizeof(int4) * (size_t)oa[s]) == cudaSuccess;
+    ok = ok && cudaMalloc(&d.plist[s], sizeof(int32_t) * (size_t)oa[s]) == cudaSuccess;
+    ok = ok && cudaMalloc(&d.flist[s], sizeof(int32_t) * (size_t)oa[s]) == cudaSuccess;
+  }
+  ok = ok && cudaMalloc(&d.regrow, sizeof(int32_t) * (size_t)oc) == cudaSuccess;
+  ok = ok && cudaMalloc(&d.gclaim, sizeof(u64) * (size_t)oc) == cudaSuccess;
+  ok = ok && cudaMalloc(&d.victim, sizeof(u64) * (size_t)oc) == cudaSuccess;
+  ok = ok && cudaMalloc(&d.wclaim, sizeof(u64) * (size_t)oc) == cudaSuccess;
+  ok = ok && cudaMalloc(&d.ctr, sizeof(BCtr) * (size_t)n) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->models_dev, sizeof(BModel) * (size_t)n) == cudaSuccess;
+  int32_t* order = nullptr;
+  ok = ok && cudaMalloc(&order, sizeof(int32_t) * (size_t)n) == cudaSuccess;
+  d.order = order;
+  ok = ok && cudaMalloc(&d.ctrl, sizeof(u32) * 4) == cudaSuccess;
+  ok = ok && cudaMalloc(&d.err, sizeof(int)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    batch_free(b);
+    return ABM_ERR_OOM;
+  }
+  d.models = b->models_dev;
+  // largest models first: they bound the tail of the persistent launch
+  std::vector<int32_t> ord((size_t)n);
+  std::iota(ord.begin(), ord.end(), 0);
+  std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
+    const BModel &a = b->models[(size_t)x], &c = b->models[(size_t)y];
+    return (long long)a.cap[0] + a.cap[1] + a.ncells > (long long)c.cap[0] + c.cap[1] + c.ncells;
+  });
+  if (cudaMemcpyAsync(b->models_dev, b->models.data(), sizeof(BModel) * (size_t)n, cudaMemcpyHostToDevice, st) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(order, ord.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemsetAsync(d.ctrl, 0, sizeof(u32) * 4, st) != cudaSuccess ||
+      cudaMemsetAsync(d.err, 0, sizeof(int), st) != cudaSuccess) {
+    batch_free(b);
+    return ABM_ERR_CUDA;
+  }
+  k_batch_init<<<n, 256, 0, st>>>(d);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
+    batch_free(b);
+    return ABM_ERR_CUDA;
+  }
+  b->threads = 256;
+  b->ctas_per_sm = 4;
+  b->steps_per_launch = 1 << 30;
+  *out = b;
+  return ABM_OK;
+}
+
+extern "C" abm_status abm_batch_tune(abm_batch* b, int32_t threads, int32_t ctas_per_sm, int32_t steps_per_launch) {
+  if (!b || (threads != 128 && threads != 256 && threads != 512 && threads != 1024) || ctas_per_sm < 1 ||
+      threads * ctas_per_sm > 2048 || steps_per_launch < 1)
+    return ABM_ERR_ARG;
+  b->threads = threads;
+  b->ctas_per_sm = ctas_per_sm;
+  b->steps_per_launch = steps_per_launch;
+  return ABM_OK;
+}
+
+extern "C" abm_status abm_batch_run(abm_batch* b, int32_t nsteps, int32_t sweep, void* stream) {
+  if (!b || nsteps < 0 || (sweep != ABM_SWEEP_CAPACITY && sweep != ABM_SWEEP_EXTENT)) return ABM_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int grid = std::max(1, std::min(b->d.nmodels, num_sms() * b->ctas_per_sm));
+  const int ext = sweep == ABM_SWEEP_EXTENT;
+  for (int done = 0; done < nsteps;) {
+    const int s = std::min(nsteps - done, b->steps_per_launch);
+    switch (b->threads) {
+      case 128: k_batch_run<128><<<grid, 128, 0, st>>>(b->d, s, ext); break;
+      case 256: k_batch_run<256><<<grid, 256, 0, st>>>(b->d, s, ext); break;
+      case 512: k_batch_run<512><<<grid, 512, 0, st>>>(b->d, s, ext); break;
+      default: k_batch_run<1024><<<grid, 1024, 0, st>>>(b->d, s, ext); break;
+    }
+    ABM_LAUNCH_CHECK();
+    done += s;
+  }
+  return ABM_OK;
+}
+
+extern "C" abm_status abm_batch_counters_get(abm_batch* b, abm_batch_counters* out, void* stream) {
+  if (!b || !out) return ABM_ERR_ARG;
+  std::vector<BCtr> h((size_t)b->d.nmodels);
+  cudaStream_t st = (cudaStream_t)stream;
+  ABM_CUDA_TRY(cudaMemcpyAsync(h.data(), b->d.ctr, sizeof(BCtr) * h.size(), cudaMemcpyDeviceToHost, st));
+  ABM_CUDA_TRY(cudaStreamSynchronize(st));
+  for (size_t i = 0; i < h.size(); ++i) {
+    abm_batch_counters& o = out[i];
+    for (int s = 0; s < 2; ++s) {
+      o.n_active[s] = h[i].n_active[s];
+      o.next_id[s] = h[i].next_id[s];
+      o.hw[s] = h[i].hw[s];
+      o.overflow[s] = h[i].overflow[s];
+      o.extent[s] = h[i].extent[s];
+    }
+    o.step = h[i].step;
+    o.reserved = 0;
+    o.agent_steps = h[i].agent_steps;
+  }
+  return ABM_OK;
+}
+
+extern "C" abm_status abm_batch_read_agents(abm_batch* b, int32_t m, int32_t species, int32_t which, int32_t* dst,
+                                            void* stream) {
+  if (!b || !dst || m < 0 || m >= b->d.nmodels || species < 0 || species > 1 || which < 0 || which > 4)
+    return ABM_ERR_ARG;
+  const BModel& mm = b->models[(size_t)m];
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t n = (size_t)mm.cap[species];
+  if (which == 0) {
+    ABM_CUDA_TRY(cudaMemcpyAsync(dst, b->d.active[species] + mm.oa[species], sizeof(int32_t) * n,
+                                 cudaMemcpyDeviceToDevice, st));
+  } else {
+    const int32_t* src = reinterpret_cast<const int32_t*>(b->d.agent[species] + mm.oa[species]) + (which - 1);
+    ABM_CUDA_TRY(cudaMemcpy2DAsync(dst, sizeof(int32_t), src, sizeof(int4), sizeof(int32_t), n,
+                                   cudaMemcpyDeviceToDevice, st));
+  }
+  return ABM_OK;
+}
+
+extern "C" abm_status abm_batch_read_grass(abm_batch* b, int32_t m, int32_t which, int32_t* dst, void* stream) {
+  if (!b || !dst || m < 0 || m >= b->d.nmodels || which < 0 || which > 1) return ABM_ERR_ARG;
+  k_batch_grass<<<std::max(1, std::min(num_sms() * 4, (b->models[(size_t)m].ncells + 255) / 256)), 256, 0,
+                  (cudaStream_t)stream>>>(b->d, m, which, dst);
+  ABM_LAUNCH_CHECK();
+  return ABM_OK;
+}
+
+extern "C" abm_status abm_batch_overflowed(abm_batch* b, int32_t* list, int32_t* count, void* stream) {
+  if (!b || !list || !count) return ABM_ERR_ARG;
+  k_batch_overflowed<<<1, 1024, 0, (cudaStream_t)stream>>>(b->d, list, count);
+  ABM_LAUNCH_CHECK();
+  return ABM_OK;
+}
+
+extern "C" abm_status abm_batch_digest(abm_batch* b, uint64_t* out, void* stream) {
+  if (!b || !out) return ABM_ERR_ARG;
+  k_batch_digest<<<b->d.nmodels, 256, 0, (cudaStream_t)stream>>>(b->d, (u64*)out);
+  ABM_LAUNCH_CHECK();
+  return ABM_OK;
+}
+
+extern "C" abm_status abm_batch_check(abm_batch* b, void* stream) {
+  if (!b) return ABM_ERR_ARG;
+  ABM_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  int err = 0;
+  ABM_CUDA_TRY(cudaMemcpy(&err, b->d.err, sizeof(int), cudaMemcpyDeviceToHost));
+  return err ? ABM_ERR_DEVICE_TIMEOUT : ABM_OK;
+}
+
+extern "C" abm_status abm_batch_info(abm_batch* b, int64_t* slots_sheep, int64_t* slots_wolf, int64_t* cells) {
+  if (!b) return ABM_ERR_ARG;
+  if (slots_sheep) *slots_sheep = b->slots[0];
+  if (slots_wolf) *slots_wolf = b->slots[1];
+  if (cells) *cells = b->cells;
+  return ABM_OK;
+}

@@ -27,7 +27,7 @@
 #include <new>
 #include <vector>
 
-#include "common.cuh"
+#include "pred_rules.cuh"
 
 namespace abm {
 
@@ -66,21 +66,6 @@ struct WorldDev {
   u32 seed, model;
   int params[8];
 };
-
-__device__ __forceinline__ int step_cell(int cell, int L, u32 dir) {
-  // neighbour table indexed by the top three bits of the MOVE draw, one nibble
-  // (offset + 1) per direction: (-1,-1) (0,-1) (1,-1) (-1,0) (1,0) (-1,1) (0,1) (1,1)
-  const int dx = (int)((0x21020210u >> (4u * dir)) & 0xFu) - 1;
-  const int dy = (int)((0x22211000u >> (4u * dir)) & 0xFu) - 1;
-  const int y = cell / L;
-  int x = cell - y * L + dx;
-  int yy = y + dy;
-  if (x < 0) x += L;
-  if (x >= L) x -= L;
-  if (yy < 0) yy += L;
-  if (yy >= L) yy -= L;
-  return yy * L + x;
-}
 
 template <int S>
 __global__ void __launch_bounds__(kPredThreads) k_move(WorldDev w, abm_step_stats* st) {

@@ -221,3 +221,82 @@ def decode_stats(t: torch.Tensor) -> list[dict]:
             d[name] = list(v) if hasattr(v, "__len__") else int(v)
         out.append(d)
     return out
+
+
+class Batch:
+    """Many independent predation models in one persistent launch."""
+
+    def __init__(self, models: list, stream=None):
+        arr = (abm.abm_batch_model * len(models))()
+        self.sides, self.caps = [], []
+        for i, m in enumerate(models):
+            arr[i].side, arr[i].seed, arr[i].model = int(m["side"]), m["seed"] & 0xFFFFFFFF, m["model"] & 0xFFFFFFFF
+            for j in range(8):
+                arr[i].params[j] = int(m["params"][j])
+            for s in range(2):
+                arr[i].cap[s], arr[i].n0[s] = int(m["cap"][s]), int(m["n0"][s])
+            self.sides.append(int(m["side"]))
+            self.caps.append([int(m["cap"][0]), int(m["cap"][1])])
+        h = C.c_void_p()
+        call("abm_batch_create", arr, len(models), _stream(stream), C.byref(h))
+        self.h = h
+        self.n = len(models)
+        self.dev = f"cuda:{torch.cuda.current_device()}"
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            abm.lib().abm_batch_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def tune(self, threads: int, ctas_per_sm: int, steps_per_launch: int = 1 << 30):
+        call("abm_batch_tune", self.h, threads, ctas_per_sm, steps_per_launch)
+
+    def run(self, nsteps: int, sweep: int = abm.SWEEP_CAPACITY, stream=None):
+        call("abm_batch_run", self.h, nsteps, sweep, _stream(stream))
+
+    def check(self, stream=None):
+        call("abm_batch_check", self.h, _stream(stream))
+
+    def counters(self, stream=None) -> list:
+        arr = (abm.abm_batch_counters * self.n)()
+        call("abm_batch_counters_get", self.h, arr, _stream(stream))
+        out = []
+        for c in arr:
+            out.append({"n_active": list(c.n_active), "next_id": list(c.next_id), "hw": list(c.hw),
+                        "overflow": list(c.overflow), "extent": list(c.extent), "step": c.step,
+                        "agent_steps": c.agent_steps})
+        return out
+
+    def agents(self, m: int, species: int, which: str, stream=None) -> torch.Tensor:
+        out = torch.empty(self.caps[m][species], dtype=torch.int32, device=self.dev)
+        call("abm_batch_read_agents", self.h, m, species, AGENT_FIELDS.index(which), ptr(out),
+             _stream(stream))
+        return out
+
+    def grass(self, m: int, which: str, stream=None) -> torch.Tensor:
+        out = torch.empty(self.sides[m] ** 2, dtype=torch.int32, device=self.dev)
+        call("abm_batch_read_grass", self.h, m, 0 if which == "grown" else 1, ptr(out), _stream(stream))
+        return out
+
+    def overflowed(self, stream=None) -> list:
+        lst = torch.empty(self.n, dtype=torch.int32, device=self.dev)
+        cnt = torch.zeros(1, dtype=torch.int32, device=self.dev)
+        call("abm_batch_overflowed", self.h, ptr(lst), ptr(cnt), _stream(stream))
+        c = int(cnt.item())
+        return lst[:c].cpu().tolist()
+
+    def digest(self, stream=None) -> torch.Tensor:
+        out = torch.empty(self.n, dtype=torch.int64, device=self.dev)
+        call("abm_batch_digest", self.h, ptr(out), _stream(stream))
+        return out
+
+    def info(self) -> dict:
+        a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+        call("abm_batch_info", self.h, C.byref(a), C.byref(b), C.byref(c))
+        return {"slots": [a.value, b.value], "cells": c.value}

@@ -1,0 +1,118 @@
+"""GPU parity: the batched many-model runner vs the oracle, model by model.
+
+Both sweeps (whole capacity, extent) must give the oracle's state bit for bit,
+for any split of the run into launches and any launch shape.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("active", "cell", "energy", "id", "age")
+
+
+@pytest.fixture(scope="module")
+def eng():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2508_16508_gb300 import abm, engine
+    abm.lib()
+    return engine
+
+
+def random_models(n, seed, max_side=40):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        side = int(rng.integers(1, max_side))
+        cap = (int(rng.integers(1, 500)), int(rng.integers(1, 300)))
+        n0 = (int(rng.integers(0, cap[0] + 1)), int(rng.integers(0, cap[1] + 1)))
+        params = workloads.predation_params(
+            sheep_gain=int(rng.integers(0, 8)), wolf_gain=int(rng.integers(0, 30)),
+            sheep_repro=float(rng.choice([0.0, 0.04, 0.3, 0.9])),
+            wolf_repro=float(rng.choice([0.0, 0.05, 0.5])), regrowth=int(rng.integers(1, 40)),
+            sheep_metab=int(rng.integers(0, 3)), wolf_metab=int(rng.integers(0, 3)),
+            grass_init=float(rng.choice([0.1, 0.5, 0.95])))
+        out.append(dict(side=side, seed=int(rng.integers(0, 2**32)), model=i, params=params,
+                        cap=cap, n0=n0))
+    return out
+
+
+def compare_model(b, m, ow, where):
+    for s in range(2):
+        for f in FIELDS:
+            g = b.agents(m, s, f).cpu().numpy()
+            o = ow.agents(s, f)
+            assert np.array_equal(g, o), (where, m, s, f, np.flatnonzero(g != o)[:5])
+    grown = ow.grass("grown")
+    wait = np.where(grown != 0, 0, np.maximum(ow.grass("countdown"), 1))
+    assert np.array_equal(b.grass(m, "grown").cpu().numpy(), grown), (where, m)
+    assert np.array_equal(b.grass(m, "wait").cpu().numpy(), wait), (where, m)
+
+
+@pytest.mark.parametrize("sweep", [0, 1])
+@pytest.mark.parametrize("threads,spl", [(256, 1 << 30), (128, 7), (512, 13)])
+def test_random_batch_vs_oracle(eng, sweep, threads, spl):
+    models = random_models(20, 100 + threads + sweep)
+    b = eng.Batch(models)
+    b.tune(threads, 2, spl)
+    b.run(45, sweep=sweep)
+    cnt = b.counters()
+    for m, md in enumerate(models):
+        ow = oracle.World(md["side"], md["seed"], md["model"], md["params"], md["cap"], md["n0"])
+        agents = 0
+        for st in ow.step(45):
+            agents += st["n_start"][0] + st["n_start"][1]
+        compare_model(b, m, ow, f"sweep {sweep}")
+        oc = ow.counters()
+        for k in ("n_active", "next_id", "hw", "overflow", "step"):
+            assert cnt[m][k] == oc[k], (m, k, cnt[m][k], oc[k])
+        assert cnt[m]["agent_steps"] == agents
+    b.check()
+
+
+def test_small_config_as_one_model_batch(eng):
+    c = workloads.PRED_SMALL
+    b = eng.Batch([dict(side=c["side"], seed=c["seed"], model=c["model"], params=c["params"],
+                        cap=c["cap"], n0=c["n0"])])
+    ow = oracle.World(c["side"], c["seed"], c["model"], c["params"], c["cap"], c["n0"])
+    for t in range(0, c["steps"], 20):
+        b.run(20)
+        ow.step(20)
+        compare_model(b, 0, ow, f"step {t + 20}")
+
+
+def test_batched_sampler_subset(eng):
+    """Models drawn by the batched workload's sampler, fixed capacity 4 side^2."""
+    tab = workloads.sample_models(4096, workloads.BATCH["sampler_seed"])
+    caps = workloads.fixed_caps(tab["side"])
+    rng = np.random.default_rng(0)
+    pick = sorted(rng.choice(4096, size=12, replace=False).tolist())
+    models = [dict(side=int(tab["side"][i]), seed=workloads.BATCH["philox_seed"], model=i,
+                   params=tab["params"][i], cap=caps[i], n0=tab["n0"][i]) for i in pick]
+    b = eng.Batch(models)
+    b.run(60, sweep=0)
+    for m, md in enumerate(models):
+        ow = oracle.World(md["side"], md["seed"], md["model"], md["params"], md["cap"], md["n0"])
+        ow.step(60)
+        compare_model(b, m, ow, "sampler")
+
+
+def test_overflow_list(eng):
+    params = workloads.predation_params(sheep_repro=0.5, wolf_repro=0.5, sheep_gain=6)
+    models = [dict(side=10, seed=3, model=i, params=params, cap=(40 if i % 2 else 4000, 2000), n0=(30, 10))
+              for i in range(6)]
+    b = eng.Batch(models)
+    b.run(40, sweep=1)
+    ov = b.overflowed()
+    want = []
+    for m, md in enumerate(models):
+        ow = oracle.World(md["side"], md["seed"], md["model"], md["params"], md["cap"], md["n0"])
+        ow.step(40)
+        if max(ow.counters()["overflow"]):
+            want.append(m)
+        compare_model(b, m, ow, "overflow")
+    assert ov == want and len(want) > 0
