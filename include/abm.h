@@ -46,6 +46,7 @@ typedef int32_t abm_status;
 #define ABM_ERR_DEVICE_TIMEOUT 4 /* a bounded device-side wait ran out */
 #define ABM_ERR_OVERFLOW 5       /* informational: more agents asked for a slot than were free */
 #define ABM_ERR_STATE 6          /* operation not valid for this handle */
+#define ABM_ERR_TOO_LARGE 7      /* size beyond a fixed, documented maximum */
 
 const char* abm_strerror(abm_status s);
 /* Library version: major * 10000 + minor * 100 + patch. */
@@ -196,6 +197,29 @@ abm_status abm_slab_counters_get(abm_slab* s, abm_slab_counters* out, void* stre
 abm_status abm_resolve_table_init(uint64_t* table, int32_t R, void* stream);
 abm_status abm_resolve(const int32_t* claim_res, const uint32_t* claim_prio, int32_t M, int32_t R,
                        uint64_t* table, int32_t* out_winner, uint8_t* out_is_winner, void* stream);
+
+/* abm_resolve for callers that cannot allocate device memory. (The paper has
+ * no counterpart; this is a deployment variant.) Some hosts of this library
+ * must not call cudaMalloc once they are running: an engine that owns a fixed
+ * device-memory budget and hands out every byte itself, a serving loop where
+ * an allocation's implicit synchronisation would stall other streams, or an
+ * embedding that forbids the CUDA allocator outright. This entry point
+ * allocates nothing -- no cudaMalloc, cudaFree or allocating library call --
+ * and takes no scratch argument: its per-resource table is a file-scope
+ * device array of ABM_RESOLVE_STATIC_MAX_R 64-bit entries (2 MiB), which
+ * every GPU that loads the library holds until the process exits. The caller
+ * still passes the inputs and outputs (same meaning as abm_resolve).
+ *  - R above ABM_RESOLVE_STATIC_MAX_R returns ABM_ERR_TOO_LARGE.
+ *  - The first call on a device looks the array's device address up
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - All calls share the one array. Each call empties the entries it uses
+ *    before claiming, so nothing carries over between calls, but calls that
+ *    overlap on the GPU (different streams, or different host threads on the
+ *    same device) race on it and give undefined results. */
+#define ABM_RESOLVE_STATIC_MAX_R (1 << 18)
+abm_status abm_resolve_static(const int32_t* claim_res, const uint32_t* claim_prio, int32_t M, int32_t R,
+                              int32_t* out_winner, uint8_t* out_is_winner, void* stream);
 
 /* ========================================================================== */
 /* Predation model (Section 5.1, Fig. 3)                                      */

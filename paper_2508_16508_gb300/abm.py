@@ -17,7 +17,8 @@ LIB_PATH = os.path.join(_HERE, "libabm.so")
 _lock = threading.Lock()
 _lib = None
 
-OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_DEVICE_TIMEOUT, ERR_OVERFLOW, ERR_STATE = range(7)
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_DEVICE_TIMEOUT, ERR_OVERFLOW, ERR_STATE, ERR_TOO_LARGE = range(8)
+RESOLVE_STATIC_MAX_R = 1 << 18
 
 P_MOVE, P_PRIO, P_REPRO, P_VICTIM = 1, 2, 3, 4
 P_INIT_AGENT, P_GRASS_INIT, P_MASK = 5, 6, 7
@@ -109,6 +110,7 @@ def _sig(L):
         "abm_slab_counters_get": ([vp, C.POINTER(abm_slab_counters), vp], st),
         "abm_resolve_table_init": ([vp, i32, vp], st),
         "abm_resolve": ([vp, vp, i32, i32, vp, vp, vp, vp], st),
+        "abm_resolve_static": ([vp, vp, i32, i32, vp, vp, vp], st),
         "abm_create": ([C.POINTER(abm_config), vp, pp], st),
         "abm_destroy": ([vp], st),
         "abm_step": ([vp, i32, vp, i32, vp], st),

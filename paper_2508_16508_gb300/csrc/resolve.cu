@@ -9,6 +9,7 @@
 // shared-memory hash table (open addressing, smem 64-bit atomicMin) and then
 // issues one global atomicMin per distinct resource it saw.
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -158,4 +159,47 @@ extern "C" abm_status abm_resolve(const int32_t* claim_res, const uint32_t* clai
                                   uint64_t* table, int32_t* out_winner, uint8_t* out_is_winner, void* stream) {
   if (M < 0 || R < 1 || !table || !out_winner || (M > 0 && (!claim_res || !claim_prio))) return ABM_ERR_ARG;
   return resolve_launch(claim_res, claim_prio, M, R, table, out_winner, out_is_winner, (cudaStream_t)stream);
+}
+
+// ----------------------------------------------------------------------------
+// Resolve without allocation: the scratch table lives in a fixed-size
+// file-scope device array instead of caller- or library-allocated memory.
+namespace abm {
+
+static __device__ __align__(256) unsigned long long g_resolve_scratch[ABM_RESOLVE_STATIC_MAX_R];
+
+constexpr int kMaxDevices = 64;
+static std::mutex g_scratch_mu;
+static u64* g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of this device's copy of the array, looked up once per
+// device (the array's name is only a host-side handle in host code).
+static abm_status static_scratch(u64** out) {
+  int dev = 0;
+  ABM_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return ABM_ERR_ARG;
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_resolve_scratch) != cudaSuccess || !p) return ABM_ERR_CUDA;
+    g_scratch_ptr[dev] = (u64*)p;
+  }
+  *out = g_scratch_ptr[dev];
+  return ABM_OK;
+}
+
+}  // namespace abm
+
+extern "C" abm_status abm_resolve_static(const int32_t* claim_res, const uint32_t* claim_prio, int32_t M, int32_t R,
+                                         int32_t* out_winner, uint8_t* out_is_winner, void* stream) {
+  if (M < 0 || R < 1 || !out_winner || (M > 0 && (!claim_res || !claim_prio))) return ABM_ERR_ARG;
+  if (R > ABM_RESOLVE_STATIC_MAX_R) return ABM_ERR_TOO_LARGE;
+  u64* table = nullptr;
+  abm_status e = static_scratch(&table);
+  if (e != ABM_OK) return e;
+  cudaStream_t st = (cudaStream_t)stream;
+  // the array keeps whatever the previous call left: empty the R entries used here
+  k_table_fill<<<std::max(1, std::min((R + 255) / 256, num_sms() * 8)), 256, 0, st>>>(table, R);
+  ABM_LAUNCH_CHECK();
+  return resolve_launch(claim_res, claim_prio, M, R, (uint64_t*)table, out_winner, out_is_winner, st);
 }

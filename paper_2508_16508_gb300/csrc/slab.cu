@@ -550,6 +550,7 @@ extern "C" const char* abm_strerror(abm_status st) {
     case ABM_ERR_DEVICE_TIMEOUT: return "device-side wait timed out";
     case ABM_ERR_OVERFLOW: return "more agents asked for a slot than were free";
     case ABM_ERR_STATE: return "operation not valid for this handle";
+    case ABM_ERR_TOO_LARGE: return "size beyond the fixed maximum of this entry point";
   }
   return "unknown status";
 }
