@@ -285,14 +285,25 @@ abm_status abm_step(abm_world* w, int32_t nsteps, abm_step_stats* stats, int32_t
  * (stats, if given, is device abm_step_stats[nsteps] and is overwritten by each replay). */
 abm_status abm_step_graph(abm_world* w, int32_t nsteps, int32_t reps, abm_step_stats* stats,
                           void* stream);
-/* abm_step that also times each kernel with CUDA events recorded on `stream`
- * between the launches. phase_ms (host float[8], required) receives the
- * milliseconds summed over the steps per kernel: [0] sheep move, [1] sheep
- * eat/select/compact, [2] sheep births, [3] wolf move, [4] wolf
- * eat/select/compact, [5] wolf births, [7] first to last event; [6] = 0.
+/* abm_step that also reports where the time goes; phase_ms (host float[8],
+ * required) receives milliseconds summed over the steps. Kernel engine: CUDA
+ * events between the launches, [0] sheep move, [1] sheep eat/select/compact,
+ * [2] sheep births, [3] wolf move, [4] wolf eat/select/compact, [5] wolf
+ * births. Persistent engine: block 0's global-timer laps between the grid
+ * barriers, [0] sheep move (+ previous wolf births), [1] sheep
+ * eat/select/flags, [2] sheep ranks, [3] sheep births + wolf move, [4] wolf
+ * eat/select/flags, [5] wolf ranks. Both: [7] whole call by events, [6] = 0.
  * Synchronises `stream`. */
 abm_status abm_step_profiled(abm_world* w, int32_t nsteps, abm_step_stats* stats, float* phase_ms,
                              void* stream);
+/* Execution engine of abm_step: ABM_ENGINE_PERSISTENT (default) runs all
+ * requested steps in one cooperative launch of `ctas_per_sm` CTAs per SM
+ * with bounded grid barriers between the phases; ABM_ENGINE_KERNELS runs six
+ * kernels per step (and is what abm_step_profiled, energy statistics and
+ * abm_step_graph use). Results are identical. */
+#define ABM_ENGINE_PERSISTENT 0
+#define ABM_ENGINE_KERNELS 1
+abm_status abm_world_tune(abm_world* w, int32_t engine, int32_t ctas_per_sm);
 /* Synchronises `stream`; reports a recorded device error (e.g. a timed-out wait). */
 abm_status abm_world_check(abm_world* w, void* stream);
 

@@ -80,6 +80,7 @@ class abm_batch_counters(C.Structure):
 
 
 SWEEP_CAPACITY, SWEEP_EXTENT = 0, 1
+ENGINE_PERSISTENT, ENGINE_KERNELS = 0, 1
 
 
 class abm_slab_counters(C.Structure):
@@ -117,6 +118,7 @@ def _sig(L):
         "abm_step_graph": ([vp, i32, i32, vp, vp], st),
         "abm_step_profiled": ([vp, i32, vp, C.POINTER(C.c_float), vp], st),
         "abm_world_check": ([vp, vp], st),
+        "abm_world_tune": ([vp, i32, i32], st),
         "abm_read_agents": ([vp, i32, i32, vp, vp], st),
         "abm_read_grass": ([vp, i32, vp, vp], st),
         "abm_world_counters_get": ([vp, C.POINTER(abm_world_counters), vp], st),

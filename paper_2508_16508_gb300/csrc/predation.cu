@@ -27,45 +27,9 @@
 #include <new>
 #include <vector>
 
-#include "pred_rules.cuh"
+#include "pred_world.cuh"
 
 namespace abm {
-
-constexpr int kPredThreads = 256;
-constexpr int kPredItems = 4;  // one 128-bit load of live flags per thread
-constexpr int kPredTile = kPredThreads * kPredItems;
-
-struct SpeciesDev {
-  int32_t* active;   // [cap_pad]
-  int4* agent;       // [cap_pad]: cell, energy, id, age
-  int32_t* parents;  // [cap] compacted parent slots
-  int32_t* freel;    // [cap] compacted free slots (only the first n_active are written)
-  u64* tiles;        // decoupled look-back states
-  u32* ctrl;         // [0..4) scan control, [4..8) births exit counter
-  int cap;
-};
-
-struct WorldCtr {
-  int n_active[2], next_id[2], hw[2], overflow[2], extent[2], step;
-  int parents[2], free_in[2];
-  int starved[2], eaten, grass_eaten;
-  int n_start[2];
-  u32 energy_exit[4];
-  long long energy[2];
-};
-
-struct WorldDev {
-  SpeciesDev sp[2];
-  int32_t* regrow;  // first step at which the cell's grass is edible
-  u64* gclaim;      // per-cell grass claims (sheep)
-  u64* victim;      // per-cell victim keys (sheep)
-  u64* wclaim;      // per-cell wolf claims
-  WorldCtr* ctr;
-  int* err;
-  int side, ncells;
-  u32 seed, model;
-  int params[8];
-};
 
 template <int S>
 __global__ void __launch_bounds__(kPredThreads) k_move(WorldDev w, abm_step_stats* st) {
@@ -319,6 +283,9 @@ struct abm_world {
   WorldDev d;
   int cap_pad[2];
   int grid;
+  int engine;       // ABM_ENGINE_PERSISTENT or ABM_ENGINE_KERNELS
+  int pgrid;        // CTAs of the persistent kernel
+  int pgrid_max;
   int64_t steps_host;
   // cached graph
   cudaGraphExec_t gexec;
@@ -341,6 +308,12 @@ static void world_free(abm_world* w) {
   cudaFree(w->d.wclaim);
   cudaFree(w->d.ctr);
   cudaFree(w->d.err);
+  for (int s = 0; s < 2; ++s)
+    for (int k = 0; k < 2; ++k) cudaFree(w->d.ps.plane[s][k]);
+  cudaFree(w->d.ps.totals);
+  cudaFree(w->d.ps.wtotals);
+  cudaFree(w->d.ps.bar);
+  cudaFree(w->d.ps.acc);
   if (w->gexec) cudaGraphExecDestroy(w->gexec);
   delete w;
 }
@@ -394,6 +367,18 @@ extern "C" abm_status abm_create(const abm_config* cfg, void* stream, abm_world*
   ok = ok && cudaMalloc(&d.wclaim, sizeof(u64) * (size_t)d.ncells) == cudaSuccess;
   ok = ok && cudaMalloc(&d.ctr, sizeof(WorldCtr)) == cudaSuccess;
   ok = ok && cudaMalloc(&d.err, sizeof(int)) == cudaSuccess;
+  w->pgrid_max = persistent_max_ctas();
+  if (w->pgrid_max < 1) ok = false;
+  const int pmax = std::max(1, w->pgrid_max);
+  for (int s = 0; s < 2 && ok; ++s)
+    for (int k = 0; k < 2 && ok; ++k)
+      ok = cudaMalloc(&d.ps.plane[s][k], sizeof(u32) * (size_t)(w->cap_pad[s] / 32)) == cudaSuccess;
+  ok = ok && cudaMalloc(&d.ps.totals, sizeof(u32) * 2 * (size_t)pmax) == cudaSuccess;
+  ok = ok && cudaMalloc(&d.ps.wtotals, sizeof(u32) * 2 * (size_t)pmax * persistent_warps()) == cudaSuccess;
+  ok = ok && cudaMalloc(&d.ps.bar, sizeof(u32) * 2) == cudaSuccess;
+  ok = ok && cudaMalloc(&d.ps.acc, sizeof(int) * 8) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(d.ps.bar, 0, sizeof(u32) * 2, st) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(d.ps.acc, 0, sizeof(int) * 8, st) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     world_free(w);
@@ -413,6 +398,8 @@ extern "C" abm_status abm_create(const abm_config* cfg, void* stream, abm_world*
     return ABM_ERR_CUDA;
   }
   w->grid = num_sms() * 8;
+  w->engine = ABM_ENGINE_PERSISTENT;
+  w->pgrid = std::min(w->pgrid_max, num_sms() * 2);
   k_world_init<<<num_sms() * 4, 256, 0, st>>>(d, cfg->n0[0], cfg->n0[1]);
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
     world_free(w);
@@ -448,6 +435,34 @@ extern "C" abm_status abm_step_profiled(abm_world* w, int32_t nsteps, abm_step_s
                                         void* stream) {
   if (!w || nsteps < 0 || !phase_ms) return ABM_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
+  if (w->engine == ABM_ENGINE_PERSISTENT) {
+    // one launch; block 0 times its phases with the global timer, the whole
+    // launch is timed with events
+    unsigned long long* ns = nullptr;
+    ABM_CUDA_TRY(cudaMallocAsync((void**)&ns, sizeof(unsigned long long) * 8, st));
+    ABM_CUDA_TRY(cudaMemsetAsync(ns, 0, sizeof(unsigned long long) * 8, st));
+    cudaEvent_t e0, e1;
+    ABM_CUDA_TRY(cudaEventCreate(&e0));
+    ABM_CUDA_TRY(cudaEventCreate(&e1));
+    cudaEventRecord(e0, st);
+    abm_status rc = nsteps > 0 ? launch_persistent(w->d, w->pgrid, nsteps, stats, st, ns) : ABM_OK;
+    cudaEventRecord(e1, st);
+    unsigned long long h[8] = {0};
+    if (rc == ABM_OK) {
+      w->steps_host += nsteps;
+      if (cudaMemcpyAsync(h, ns, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess)
+        rc = ABM_ERR_CUDA;
+    }
+    float total = 0.f;
+    if (rc == ABM_OK && cudaEventElapsedTime(&total, e0, e1) != cudaSuccess) rc = ABM_ERR_CUDA;
+    for (int k = 0; k < 8; ++k) phase_ms[k] = k < 6 ? (float)(h[k] * 1e-6) : 0.f;
+    phase_ms[7] = total;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFreeAsync(ns, st);
+    return rc;
+  }
   std::vector<cudaEvent_t> ev((size_t)nsteps * 7);
   for (auto& e : ev) ABM_CUDA_TRY(cudaEventCreate(&e));
   abm_status rc = ABM_OK;
@@ -479,6 +494,12 @@ extern "C" abm_status abm_step_profiled(abm_world* w, int32_t nsteps, abm_step_s
 extern "C" abm_status abm_step(abm_world* w, int32_t nsteps, abm_step_stats* stats, int32_t want_energy,
                                void* stream) {
   if (!w || nsteps < 0) return ABM_ERR_ARG;
+  if (w->engine == ABM_ENGINE_PERSISTENT && !want_energy) {
+    if (nsteps == 0) return ABM_OK;
+    abm_status e = launch_persistent(w->d, w->pgrid, nsteps, stats, (cudaStream_t)stream);
+    if (e == ABM_OK) w->steps_host += nsteps;
+    return e;
+  }
   for (int i = 0; i < nsteps; ++i) {
     abm_status e = enqueue_step(w, stats ? stats + i : nullptr, want_energy, (cudaStream_t)stream);
     if (e != ABM_OK) return e;
@@ -514,6 +535,15 @@ extern "C" abm_status abm_step_graph(abm_world* w, int32_t nsteps, int32_t reps,
   }
   for (int r = 0; r < reps; ++r) ABM_CUDA_TRY(cudaGraphLaunch(w->gexec, st));
   w->steps_host += (int64_t)nsteps * reps;
+  return ABM_OK;
+}
+
+extern "C" abm_status abm_world_tune(abm_world* w, int32_t engine, int32_t ctas_per_sm) {
+  if (!w || (engine != ABM_ENGINE_PERSISTENT && engine != ABM_ENGINE_KERNELS) || ctas_per_sm < 1) return ABM_ERR_ARG;
+  const int g = num_sms() * ctas_per_sm;
+  if (engine == ABM_ENGINE_PERSISTENT && g > w->pgrid_max) return ABM_ERR_ARG;
+  w->engine = engine;
+  if (engine == ABM_ENGINE_PERSISTENT) w->pgrid = g;
   return ABM_OK;
 }
 
@@ -626,6 +656,7 @@ extern "C" abm_status abm_load(abm_world* w, const void* buf, size_t bytes, void
   ABM_CUDA_TRY(cudaMemcpyAsync(w->d.regrow, p, (size_t)w->d.ncells * sizeof(int32_t), cudaMemcpyHostToDevice, st));
   k_reset_tables<<<num_sms() * 4, 256, 0, st>>>(w->d);
   ABM_LAUNCH_CHECK();
+  ABM_CUDA_TRY(cudaMemsetAsync(w->d.ps.acc, 0, sizeof(int) * 8, st));
   ABM_CUDA_TRY(cudaStreamSynchronize(st));
   w->steps_host = h.step;
   return ABM_OK;

@@ -165,6 +165,9 @@ class World:
              stream=None):
         call("abm_step", self.h, nsteps, ptr(stats), 1 if want_energy else 0, _stream(stream))
 
+    def tune(self, engine: int = abm.ENGINE_PERSISTENT, ctas_per_sm: int = 2):
+        call("abm_world_tune", self.h, engine, ctas_per_sm)
+
     def step_graph(self, nsteps: int, reps: int = 1, stats: torch.Tensor | None = None,
                    stream=None):
         call("abm_step_graph", self.h, nsteps, reps, ptr(stats), _stream(stream))

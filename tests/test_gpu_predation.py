@@ -57,24 +57,39 @@ def compare_stats(gst, ost, energy=True):
         assert gst[k] == ost[k], (k, gst[k], ost[k])
 
 
-def make(eng, c, seed=None):
+def make(eng, c, seed=None, engine=0):
     seed = c["seed"] if seed is None else seed
     gw = eng.World(c["side"], seed, c["model"], c["params"], c["cap"], c["n0"])
+    gw.tune(engine)
     ow = oracle.World(c["side"], seed, c["model"], c["params"], c["cap"], c["n0"])
     return gw, ow
 
 
-def test_small_config_every_step(eng):
+ENGINES = [0, 1]  # persistent cooperative kernel, six kernels per step
+
+
+def energies(gw):
+    e = []
+    for s in range(2):
+        a = gw.agents(s, "active").cpu().numpy().astype(bool)
+        e.append(int(gw.agents(s, "energy").cpu().numpy()[a].astype(np.int64).sum()))
+    return e
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_small_config_every_step(eng, engine):
     """40x40, 100 sheep / 25 wolves, capacity 2048/1024, 200 steps, seed 0."""
     c = workloads.PRED_SMALL
-    gw, ow = make(eng, c)
+    gw, ow = make(eng, c, engine=engine)
     compare_state(gw, ow, "init")
     stats = gw.new_stats(1)
     for t in range(c["steps"]):
-        gw.step(1, stats, want_energy=True)
+        gw.step(1, stats, want_energy=engine == 1)
         ost = ow.step()[0]
         gst = eng.decode_stats(stats)[0]
-        compare_stats(gst, ost)
+        compare_stats(gst, ost, energy=engine == 1)
+        if engine == 0:
+            assert energies(gw) == ost["energy"]
         assert gst["step"] == t
         compare_state(gw, ow, f"step {t}")
     gw.check()
@@ -85,8 +100,9 @@ def test_small_config_every_step(eng):
     assert traj[-1].tolist() == [c["steps"] - 1] + gw.counters()["n_active"]
 
 
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("seed", range(24))
-def test_random_small_worlds(eng, seed):
+def test_random_small_worlds(eng, seed, engine):
     rng = np.random.default_rng(500 + seed)
     side = int(rng.integers(1, 40))
     cap = (int(rng.integers(1, 700)), int(rng.integers(1, 300)))
@@ -97,20 +113,20 @@ def test_random_small_worlds(eng, seed):
         regrowth=int(rng.integers(1, 40)), sheep_metab=int(rng.integers(0, 3)),
         wolf_metab=int(rng.integers(0, 3)), grass_init=float(rng.choice([0.1, 0.5, 0.95])))
     c = dict(side=side, n0=n0, cap=cap, seed=seed, model=int(rng.integers(0, 1000)), params=params)
-    gw, ow = make(eng, c)
+    gw, ow = make(eng, c, engine=engine)
     stats = gw.new_stats(60)
-    gw.step(60, stats, want_energy=True)
+    gw.step(60, stats, want_energy=engine == 1)
     ost = ow.step(60)
     for g, o in zip(eng.decode_stats(stats), ost):
-        compare_stats(g, o)
+        compare_stats(g, o, energy=engine == 1)
     compare_state(gw, ow, f"seed {seed}")
     gw.check()
 
 
 def test_graph_replay_equals_eager(eng):
     c = dict(workloads.PRED_SMALL)
-    a, _ = make(eng, c)
-    b, _ = make(eng, c)
+    a, _ = make(eng, c, engine=0)
+    b, _ = make(eng, c, engine=1)
     sa = a.new_stats(25)
     sb = b.new_stats(25)
     s = torch.cuda.Stream()
@@ -154,25 +170,48 @@ def test_overflow_truncates_like_oracle(eng):
     assert max(gw.counters()["overflow"]) == 1
 
 
-def test_large_config_first_steps(eng):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_large_config_first_steps(eng, engine):
     """2048x2048, 1M sheep / 250k wolves, capacity 8Mi / 4Mi: 12 steps, full state."""
     c = workloads.PRED_LARGE
-    gw, ow = make(eng, c)
+    gw, ow = make(eng, c, engine=engine)
     compare_state(gw, ow, "init")
     stats = gw.new_stats(12)
-    gw.step(12, stats, want_energy=True)
+    gw.step(12, stats, want_energy=engine == 1)
     ost = ow.step(12)
     for g, o in zip(eng.decode_stats(stats), ost):
-        compare_stats(g, o)
+        compare_stats(g, o, energy=engine == 1)
     compare_state(gw, ow, "step 12")
     gw.check()
+
+
+def test_large_config_engines_agree_over_300_steps(eng):
+    """Both engines over 300 steps of the large run (through the population
+    crash and recovery), whole state compared."""
+    c = workloads.PRED_LARGE
+    a, _ = make(eng, c, engine=0)
+    b, _ = make(eng, c, engine=1)
+    sa, sb = a.new_stats(300), b.new_stats(300)
+    a.step(300, sa)
+    b.step(300, sb)
+    torch.cuda.synchronize()
+    ra, rb = eng.decode_stats(sa), eng.decode_stats(sb)
+    for x, y in zip(ra, rb):
+        for k in ("n_start", "parents", "births", "starved", "eaten", "grass_eaten", "n_end", "hw", "overflow"):
+            assert x[k] == y[k], (k, x["step"])
+    for s in range(2):
+        for f in FIELDS:
+            assert torch.equal(a.agents(s, f), b.agents(s, f)), (s, f)
+    assert torch.equal(a.grass("wait"), b.grass("wait"))
+    assert a.counters() == b.counters()
+    a.check()
 
 
 @pytest.mark.slow
 def test_large_config_full_run(eng):
     """The full 1000-step large run: populations every step, full state at the end."""
     c = workloads.PRED_LARGE
-    gw, ow = make(eng, c)
+    gw, ow = make(eng, c, engine=0)
     stats = gw.new_stats(c["steps"])
     gw.step(c["steps"], stats)
     ost = ow.step(c["steps"])
@@ -192,3 +231,34 @@ def test_create_argument_errors(eng):
     cfg.side, cfg.cap[0], cfg.cap[1], cfg.n0[0] = 10, 5, 5, 6
     cfg.params[4] = 3
     assert abm.lib().abm_create(C.byref(cfg), None, C.byref(h)) == abm.ERR_ARG
+
+
+def test_large_config_full_run_vs_stored_oracle(eng):
+    """All 1000 steps of the large run on the persistent engine: every step's
+    counts against the oracle's stored trajectory, and the SHA-256 of the final
+    state against the oracle's (tests/golden/make_golden.py large)."""
+    import os
+    import sys
+    path = os.path.join(os.path.dirname(__file__), "golden", "pred_large_trajectory.txt")
+    if not os.path.exists(path):
+        pytest.skip("stored large trajectory not written")
+    sys.path.insert(0, os.path.join(os.path.dirname(__file__), "golden"))
+    from make_golden import state_sha256
+    with open(path) as f:
+        want_sha = [ln.split()[2] for ln in f if ln.startswith("# final_state_sha256")][0]
+    want = np.loadtxt(path, dtype=np.int64, comments="#")
+    c = workloads.PRED_LARGE
+    gw = eng.World(c["side"], c["seed"], c["model"], c["params"], c["cap"], c["n0"])
+    stats = gw.new_stats(c["steps"])
+    gw.step(c["steps"], stats)
+    got = np.array([[r["step"], *r["n_start"], *r["parents"], *r["births"], *r["starved"], r["eaten"],
+                     r["grass_eaten"], *r["n_end"], *r["hw"]] for r in eng.decode_stats(stats)])
+    np.testing.assert_array_equal(got, want)
+    st = {}
+    for s, name in ((0, "sheep"), (1, "wolf")):
+        for f in FIELDS:
+            st[f"{name}.{f}"] = gw.agents(s, f).cpu().numpy()
+    st["grass.grown"] = gw.grass("grown").cpu().numpy()
+    st["grass.wait"] = gw.grass("wait").cpu().numpy()
+    assert state_sha256(st) == want_sha
+    gw.check()
