@@ -69,27 +69,38 @@ __device__ __forceinline__ void b_move(const BatchDev& b, MCtx& c, int S, int sw
   const int L = c.m.side;
   const int metab = c.m.prm[PRM_SHEEP_METAB + S];
   const int nq = (sweep + 3) >> 2;
-  for (int q = threadIdx.x; q < nq; q += T) {
-    const int4 a4v = reinterpret_cast<const int4*>(act)[q];
-    const int a4[4] = {a4v.x, a4v.y, a4v.z, a4v.w};
+  // four 128-bit loads of live flags in flight per thread, then the work
+  for (int q0 = threadIdx.x; q0 < nq; q0 += 4 * T) {
+    int4 a4v[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (!a4[j]) continue;
-      const int slot = 4 * q + j;
-      int4 a = ag[slot];
-      if (S == 0) victim[a.x] = kNoKey;
-      const u32 dir = draw(c.m.seed, c.m.model, (u32)t, (u32)slot, ABM_P_MOVE, (u32)S) >> 29;
-      const int cell = step_cell(a.x, L, dir);
-      a.x = cell;
-      a.y -= metab;
-      a.w += 1;
-      ag[slot] = a;
-      if (S == 0) {
-        if (b.regrow[c.m.oc + cell] <= t)
-          atomicMin(&b.gclaim[c.m.oc + cell], claim_key(draw(c.m.seed, c.m.model, (u32)t, (u32)slot, ABM_P_PRIO, 0u), slot));
-      } else {
-        if (victim[cell] != kNoKey)
-          atomicMin(&b.wclaim[c.m.oc + cell], claim_key(draw(c.m.seed, c.m.model, (u32)t, (u32)slot, ABM_P_PRIO, 1u), slot));
+    for (int u = 0; u < 4; ++u) {
+      const int q = q0 + u * T;
+      a4v[u] = q < nq ? reinterpret_cast<const int4*>(act)[q] : make_int4(0, 0, 0, 0);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int a4[4] = {a4v[u].x, a4v[u].y, a4v[u].z, a4v[u].w};
+      if (!(a4[0] | a4[1] | a4[2] | a4[3])) continue;
+      const int q = q0 + u * T;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (!a4[j]) continue;
+        const int slot = 4 * q + j;
+        int4 a = ag[slot];
+        if (S == 0) victim[a.x] = kNoKey;
+        const u32 dir = draw(c.m.seed, c.m.model, (u32)t, (u32)slot, ABM_P_MOVE, (u32)S) >> 29;
+        const int cell = step_cell(a.x, L, dir);
+        a.x = cell;
+        a.y -= metab;
+        a.w += 1;
+        ag[slot] = a;
+        if (S == 0) {
+          if (b.regrow[c.m.oc + cell] <= t)
+            atomicMin(&b.gclaim[c.m.oc + cell], claim_key(draw(c.m.seed, c.m.model, (u32)t, (u32)slot, ABM_P_PRIO, 0u), slot));
+        } else {
+          if (victim[cell] != kNoKey)
+            atomicMin(&b.wclaim[c.m.oc + cell], claim_key(draw(c.m.seed, c.m.model, (u32)t, (u32)slot, ABM_P_PRIO, 1u), slot));
+        }
       }
     }
   }
@@ -112,20 +123,21 @@ __device__ __forceinline__ void b_scan(const BatchDev& b, MCtx& c, int S, int sw
   const int bound = c.n_active[S];
   int starved = 0, won = 0;
   u32 pf = 0, pp = 0;
-  for (int c0 = 0; c0 < sweep; c0 += 4 * T) {
-    const int base = c0 + 4 * threadIdx.x;
-    int a4[4] = {0, 0, 0, 0};
-    if (base < sweep) {
-      const int4 v = reinterpret_cast<const int4*>(act)[base >> 2];
-      a4[0] = v.x; a4[1] = v.y; a4[2] = v.z; a4[3] = v.w;
-    }
-    u32 fr = 0, par = 0;
-    bool died = false;
+  for (int c0 = 0; c0 < sweep; c0 += 16 * T) {
+    const int base = c0 + 16 * threadIdx.x;
+    int a16[16];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int v = 0; v < 4; ++v) {
+      int4 q = make_int4(0, 0, 0, 0);
+      if (base + 4 * v < sweep) q = reinterpret_cast<const int4*>(act)[(base >> 2) + v];
+      a16[4 * v] = q.x; a16[4 * v + 1] = q.y; a16[4 * v + 2] = q.z; a16[4 * v + 3] = q.w;
+    }
+    u32 fr = 0, par = 0, died = 0;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
       const int slot = base + j;
       if (slot >= sweep) continue;
-      if (!a4[j]) {
+      if (!a16[j]) {
         fr |= 1u << j;
         continue;
       }
@@ -146,8 +158,8 @@ __device__ __forceinline__ void b_scan(const BatchDev& b, MCtx& c, int S, int sw
         }
       }
       if (a.y < 0) {
-        a4[j] = 0;
-        died = true;
+        a16[j] = 0;
+        died |= 1u << j;
         ++starved;
       } else {
         if (draw(c.m.seed, c.m.model, (u32)t, (u32)slot, ABM_P_REPRO, (u32)S) < Tr) par |= 1u << j;
@@ -158,15 +170,24 @@ __device__ __forceinline__ void b_scan(const BatchDev& b, MCtx& c, int S, int sw
     u32 ex_f, ex_p, tot_f, tot_p;
     block_scan2<T>(__popc(fr), __popc(par), ex_f, ex_p, tot_f, tot_p, s_warp);
     u32 rf = pf + ex_f, rp = pp + ex_p;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if ((fr >> j) & 1u) {
-        if ((int)rf < bound) flist[rf] = base + j;
-        ++rf;
-      }
-      if ((par >> j) & 1u) plist[rp++] = base + j;
+    while (fr) {
+      const int j = __ffs(fr) - 1;
+      fr &= fr - 1;
+      if ((int)rf < bound) flist[rf] = base + j;
+      ++rf;
     }
-    if (died) reinterpret_cast<int4*>(act)[base >> 2] = make_int4(a4[0], a4[1], a4[2], a4[3]);
+    while (par) {
+      const int j = __ffs(par) - 1;
+      par &= par - 1;
+      plist[rp++] = base + j;
+    }
+    if (died) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v)
+        if ((died >> (4 * v)) & 0xFu)
+          reinterpret_cast<int4*>(act)[(base >> 2) + v] =
+              make_int4(a16[4 * v], a16[4 * v + 1], a16[4 * v + 2], a16[4 * v + 3]);
+    }
     pf += tot_f;
     pp += tot_p;
   }
