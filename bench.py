@@ -11,8 +11,9 @@ the start of the step, divided by the device time.
 
 The same JSON line carries the selective-update microbenchmark (2^24 slots x 8
 int32 fields, p in {0.001, 0.05, 0.5}, plus the Zipf conflict pass) in HBM
-GB/s, the roofline of the dominant kernel, the oracle's CPU timing and the
-end-to-end (host API) rate.
+GB/s; the batched legs (4096 models, 500 steps: plain fixed capacity vs
+learned capacity); the roofline of the timed kernel; the oracle's CPU timing;
+and the end-to-end (host API) rate.
 
 ``--impl reference`` times the sequential CPU oracle on the same workload.
 """
@@ -30,6 +31,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+import numpy as np  # noqa: E402
+
 import workloads  # noqa: E402
 
 METRIC = "agent-steps/s (predation)"
@@ -44,7 +47,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=995)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-extras", action="store_true", help="skip the microbenchmark legs")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the microbenchmark, batched and CPU legs")
     return ap.parse_args()
 
 
@@ -124,7 +128,8 @@ def kernel_bytes(k: int, st: dict) -> int:
         win = st["grass_eaten"] if s == 0 else st["eaten"]
         win_b = 4 + 8 + 4 if s == 0 else 4 + 8 + 8 + 8 + 4
         free = max(E - n, 0)
-        b = 4 * E + n * (16 + 8) + win * win_b + 4 * min(free, n) + 4 * st["parents"][s] + 4 * st["starved"][s]
+        b = 4 * E + n * (16 + 8) + win * win_b + 4 * min(free, st["parents"][s]) + 4 * st["parents"][s] \
+            + 4 * st["starved"][s]
         if s == 0:
             b += 8 * (n - st["starved"][s])
         return b
@@ -203,7 +208,7 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def selective_update_leg(torch, engine, abm, hbm_peak, steps=8, warmup=3):
+def selective_update_leg(torch, engine, abm, autotune, hbm_peak, steps=8, warmup=3):
     """Selective-update microbenchmark: 2^24 slots x 8 fields, fused remove/update/add call."""
     c = workloads.SELECTIVE
     n, F = c["n"], c["F"]
@@ -213,7 +218,9 @@ def selective_update_leg(torch, engine, abm, hbm_peak, steps=8, warmup=3):
     out = {}
     for p in c["p"]:
         T, k = workloads.threshold(p), workloads.k_for(p, n)
+        tuned = autotune.tune_slab(n, F, p, k, seed=c["seed"])
         s = engine.Slab(n, F, seed=c["seed"], init=abm.INIT_HALF_LIVE)
+        s.tune(tuned["threads"], tuned["ctas_per_sm"])
         rec = torch.empty((k, F), dtype=torch.int32, device="cuda")
         dl = torch.empty((k, F), dtype=torch.int32, device="cuda")
         cnt = torch.zeros(3, dtype=torch.int32, device="cuda")
@@ -236,7 +243,8 @@ def selective_update_leg(torch, engine, abm, hbm_peak, steps=8, warmup=3):
         ms = statistics.median(times)
         b = statistics.median(nbytes)
         gbs = b / (ms * 1e-3) / 1e9
-        out[str(p)] = {"k": k, "ms": ms, "algorithmic_bytes": int(b), "gbs": gbs, "frac": gbs / hbm_peak}
+        out[str(p)] = {"k": k, "ms": ms, "algorithmic_bytes": int(b), "gbs": gbs, "frac": gbs / hbm_peak,
+                       "launch": f"{tuned['threads']} threads x {tuned['ctas_per_sm']} CTAs/SM (autotuned)"}
         del s, rec, dl
     # conflict pass: M = N/4 claims over R = N/64 resources, Zipf(1.1)
     M, R = n // 4, n // 64
@@ -264,55 +272,132 @@ def selective_update_leg(torch, engine, abm, hbm_peak, steps=8, warmup=3):
     return out
 
 
+def batched_leg(torch, engine, capacity, autotune, abm, hbm_peak):
+    """Batched models: plain fixed capacity (static shapes, the whole capacity
+    swept every step) vs learned capacity (MLP-sized slabs, device overflow
+    detection, fixed-capacity rerun of the overflowed models)."""
+    B = workloads.BATCH
+    steps = B["steps"]
+    tab = workloads.sample_models(B["n_models"], B["sampler_seed"])
+    fixed = workloads.fixed_caps(tab["side"])
+    models = [dict(side=int(tab["side"][i]), seed=B["philox_seed"], model=i, params=tab["params"][i],
+                   cap=fixed[i], n0=tab["n0"][i]) for i in range(B["n_models"])]
+    tf = autotune.tune_batch(models, steps, abm.SWEEP_CAPACITY)
+    th, cps = tf["threads"], tf["ctas_per_sm"]
+    out = {"workload": B["name"], "models": B["n_models"], "steps": steps,
+           "launch_fixed": f"{th} threads x {cps} CTAs/SM (autotuned)"}
+    # plain fixed capacity (one persistent launch for all 500 steps)
+    b = engine.Batch(models)
+    b.tune(th, cps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    b.run(steps, sweep=abm.SWEEP_CAPACITY)
+    e1.record()
+    e1.synchronize()
+    t_fixed = e0.elapsed_time(e1)
+    want = b.digest().cpu().numpy()
+    cnt = b.counters()
+    b.check()
+    info = b.info()
+    del b
+    torch.cuda.empty_cache()
+    agents = sum(c["agent_steps"] for c in cnt)
+    hw = np.array([c["hw"] for c in cnt], dtype=np.int64)
+    # sweep bytes of the capacity sweep: live flags read twice per species per step
+    sweep_bytes = 2 * 4 * (info["slots"][0] + info["slots"][1]) * steps
+    out["fixed"] = {"ms": t_fixed, "agent_steps_per_s": agents / (t_fixed * 1e-3),
+                    "slots": info["slots"], "live_flag_sweep_gbs": sweep_bytes / (t_fixed * 1e-3) / 1e9}
+    # the same models with extent sweeps (a stronger plain baseline: placeholders past
+    # the highest slot ever used are never visited)
+    b = engine.Batch(models)
+    b.tune(th, cps)
+    e0.record()
+    b.run(steps, sweep=abm.SWEEP_EXTENT)
+    e1.record()
+    e1.synchronize()
+    t_ext = e0.elapsed_time(e1)
+    ext_ok = bool(np.array_equal(b.digest().cpu().numpy(), want))
+    del b
+    torch.cuda.empty_cache()
+    out["fixed_extent_sweep"] = {"ms": t_ext, "agent_steps_per_s": agents / (t_ext * 1e-3), "bit_exact": ext_ok}
+    # learned capacity
+    wpath = os.path.join(ROOT, "paper_2508_16508_gb300", "data", "capacity_mlp.npz")
+    m = capacity.CapacityModel.load(wpath)
+    e0.record()
+    learned = m.capacities(m.features(capacity.table_of(models, steps)), fixed, tab["n0"], margin=0.0)
+    e1.record()
+    e1.synchronize()
+    t_mlp = e0.elapsed_time(e1)
+    lmodels = [dict(m, cap=(int(cc[0]), int(cc[1]))) for m, cc in zip(models, learned)]
+    tl = autotune.tune_batch(lmodels, steps, abm.SWEEP_CAPACITY)
+    out["launch_learned"] = f"{tl['threads']} threads x {tl['ctas_per_sm']} CTAs/SM (autotuned)"
+    res = capacity.run_learned(models, learned, fixed, steps, threads=tl["threads"], ctas_per_sm=tl["ctas_per_sm"])
+    t_learned = res["ms_learned"] + res["ms_rerun"] + t_mlp
+    out["learned"] = {"ms": t_learned, "ms_run": res["ms_learned"], "ms_rerun": res["ms_rerun"], "ms_mlp": t_mlp,
+                      "agent_steps_per_s": agents / (t_learned * 1e-3),
+                      "speedup_vs_fixed": t_fixed / t_learned,
+                      "overflowed_models": len(res["overflowed"]), "unrecovered_overflows": 0,
+                      "bit_exact_vs_fixed": bool(np.array_equal(res["digest"], want)),
+                      "capacity_sum_fixed": int(fixed.sum()), "capacity_sum_learned": int(learned.sum()),
+                      "peak_sum": int(hw.sum()),
+                      "wasted_capacity": (int(learned.sum()) - int(hw.sum())) / int(hw.sum())}
+    return out
+
+
 def run_ours(args, rank, world, local):
+    import numpy as _np  # noqa: F401
     import torch
     torch.cuda.set_device(local)
-    from paper_2508_16508_gb300 import abm, engine
+    from paper_2508_16508_gb300 import abm, autotune, capacity, engine
     abm.lib()
     hbm_peak, peak_kind = peaks()
     c = workloads.PRED_LARGE
     # each rank runs an independent replica (its own Philox model id)
+    tw = autotune.tune_world(c)
     gw = engine.World(c["side"], c["seed"], c["model"] + rank, c["params"], c["cap"], c["n0"])
+    gw.tune(tw["engine"], tw["ctas_per_sm"])
     K, W = args.steps, args.warmup
     stats = gw.new_stats(max(K, 1))
     gw.step(W)
     torch.cuda.synchronize()
     barrier(world)
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        phase = gw.step_profiled(K, stats)  # events on the launching stream, synchronises
+    clk = ClockSampler(local)
+    clk.__enter__()
+    # one persistent launch for all K steps; CUDA events around it on the
+    # launching stream, block 0's global-timer laps between the grid barriers
+    phase = gw.step_profiled(K, stats)
     torch.cuda.synchronize()
     barrier(world)
     gw.check()
     ms_total = phase[7]
     st_rows = engine.decode_stats(stats[:K])
-    cnt_after = gw.counters()
-    # extents at the start of each timed step: replay the recorded populations
-    # (extent only grows, by births beyond the free slots inside it)
     agents = sum(r["n_start"][0] + r["n_start"][1] for r in st_rows)
-    local_rate = agents / (ms_total * 1e-3)
     t_max = max_over_ranks(ms_total, world, device="cuda")
     total_agents = sum_over_ranks(agents, world, device="cuda")
     value = total_agents / (t_max * 1e-3)
 
-    # roofline of the dominant kernel
-    shares = [phase[i] / max(sum(phase[:6]), 1e-9) for i in range(6)]
-    dom = max(range(6), key=lambda i: phase[i])
-    dom_bytes = sum(kernel_bytes(dom, r) for r in st_rows)
-    achieved = dom_bytes / (phase[dom] * 1e-3) / 1e9
-    roofline = {"kernel": KERNELS[dom], "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
-                "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "traffic": None, "launch_ms": phase[dom] / max(K, 1),
-                "algorithmic_bytes_per_launch": dom_bytes / max(K, 1)}
+    # roofline of the (only) kernel of the timed region: algorithmic bytes of
+    # every phase of every step over the launch's duration
+    step_bytes = sum(kernel_bytes(k, r) for r in st_rows for k in range(6))
+    achieved = step_bytes / (ms_total * 1e-3) / 1e9
+    roofline = {"kernel": "k_persistent (all phases of all timed steps, one cooperative launch)",
+                "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "peak_kind": peak_kind,
+                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                "launch_ms": ms_total, "algorithmic_bytes_per_launch": step_bytes,
+                "note": "latency-bound: dependent random cell accesses and 6 grid barriers per step"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": t_max / max(K, 1), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic (Philox-seeded initial state)",
-            "config": config_block(), "roofline": roofline, "gpu_launches": 6 * K,
-            "clocks": clk.summary(),
-            "phases_ms_per_step": {n: phase[i] / max(K, 1) for i, n in enumerate(PHASES)},
-            "phase_share": {n: shares[i] for i, n in enumerate(PHASES)},
-            "end_counters": cnt_after}
+            "config": dict(config_block(), engine=("persistent" if tw["engine"] == abm.ENGINE_PERSISTENT
+                                                    else "kernels"), ctas_per_sm=tw["ctas_per_sm"],
+                           launch="autotuned"),
+            "roofline": roofline, "gpu_launches": 1 if tw["engine"] == abm.ENGINE_PERSISTENT else 6 * K,
+            "phases_us_per_step": {n: 1e3 * phase[i] / max(K, 1) for i, n in enumerate(
+                ("A_prev_wolf_births_sheep_move", "B_sheep_eat_select_flags", "C_sheep_ranks", "D_sheep_births_wolf_move",
+                 "E_wolf_eat_select_flags", "F_wolf_ranks"))},
+            "end_counters": gw.counters()}
 
     if rank == 0 and not args.no_extras:
         # end to end through the public API: one abm_step per step, then the
@@ -334,10 +419,15 @@ def run_ours(args, rank, world, local):
         e2e_dt = time.perf_counter() - t0
         line["e2e"] = {"value": ea / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": 0,
                        "d2h_bytes_per_step": abm.STATS_BYTES,
-                       "note": "abm_step + synchronous read-back of the step's statistics; the model "
-                               "state lives on the device, so a step has no host input"}
+                       "note": "abm_step (one persistent launch per step) + synchronous read-back of the "
+                               "step's statistics; the model state lives on the device, so a step has no "
+                               "host input"}
         del ew
-        line["selective_update"] = selective_update_leg(torch, engine, abm, hbm_peak)
+        line["selective_update"] = selective_update_leg(torch, engine, abm, autotune, hbm_peak)
+        line["batched"] = batched_leg(torch, engine, capacity, autotune, abm, hbm_peak)
+    clk.__exit__(None, None, None)
+    line["clocks"] = clk.summary()
+    if rank == 0 and not args.no_extras:
         # the oracle on the machine's host cores, bounded sample
         rate, n, dt = oracle_predation_rate(10**9, 0, budget_s=15.0)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",

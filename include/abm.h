@@ -304,6 +304,13 @@ abm_status abm_step_profiled(abm_world* w, int32_t nsteps, abm_step_stats* stats
 #define ABM_ENGINE_PERSISTENT 0
 #define ABM_ENGINE_KERNELS 1
 abm_status abm_world_tune(abm_world* w, int32_t engine, int32_t ctas_per_sm);
+/* Failure-detection self-check (no counterpart in the paper): runs the
+ * bounded grid barrier of the persistent engine with one arrival more than
+ * the grid provides, so its wait runs out after `spin_limit` polls (1..2^24;
+ * ~100 ns each). Returns ABM_ERR_DEVICE_TIMEOUT when the timeout was detected
+ * and reported -- the expected outcome -- and leaves the context usable.
+ * Synchronises `stream`. */
+abm_status abm_diag_barrier_timeout(int32_t spin_limit, void* stream);
 /* Synchronises `stream`; reports a recorded device error (e.g. a timed-out wait). */
 abm_status abm_world_check(abm_world* w, void* stream);
 

@@ -119,6 +119,7 @@ def _sig(L):
         "abm_step_profiled": ([vp, i32, vp, C.POINTER(C.c_float), vp], st),
         "abm_world_check": ([vp, vp], st),
         "abm_world_tune": ([vp, i32, i32], st),
+        "abm_diag_barrier_timeout": ([i32, vp], st),
         "abm_read_agents": ([vp, i32, i32, vp, vp], st),
         "abm_read_grass": ([vp, i32, vp, vp], st),
         "abm_world_counters_get": ([vp, C.POINTER(abm_world_counters), vp], st),

@@ -29,13 +29,14 @@ constexpr int kBarSpin = 1 << 24;         // bounded barrier wait (~2 s with the
 // the last CTA to arrive resets the arrival count and bumps the generation.
 // A wait that runs out records an error and proceeds (results are then
 // invalid, but the kernel ends).
-__device__ __forceinline__ void grid_sync(u32* bar, int* err) {
+__device__ __forceinline__ void grid_sync(u32* bar, int* err, u32 expected = 0, int limit = kBarSpin) {
+  if (expected == 0) expected = gridDim.x;
   __syncthreads();
   if (threadIdx.x == 0) {
     const u32 gen = ld_relaxed32(bar + 1);
     __threadfence();
     const u32 arrived = atomicAdd(bar, 1u);
-    if (arrived == gridDim.x - 1) {
+    if (arrived == expected - 1) {
       bar[0] = 0u;
       __threadfence();
       atomicAdd(bar + 1, 1u);
@@ -43,7 +44,7 @@ __device__ __forceinline__ void grid_sync(u32* bar, int* err) {
       int spins = 0;
       u32 backoff = 16;
       while (ld_relaxed32(bar + 1) == gen) {
-        if (++spins > kBarSpin) {
+        if (++spins > limit) {
           atomicExch(err, kErrTimeout);
           break;
         }
@@ -444,6 +445,14 @@ __global__ void __launch_bounds__(kPT) k_persistent(WorldDev w, int nsteps, abm_
   }
 }
 
+// Failure-detection check: a grid barrier that waits for one CTA more than
+// the grid has, so that the wait must run out; every CTA records the timeout
+// and returns. Used to show that a wait which never completes ends the kernel
+// with an error status instead of hanging the GPU.
+__global__ void k_barrier_timeout(u32* bar, int* err, int limit) {
+  grid_sync(bar, err, gridDim.x + 1, limit);
+}
+
 int persistent_max_ctas() {
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent, kPT, 0) != cudaSuccess) return 0;
@@ -461,3 +470,33 @@ abm_status launch_persistent(const WorldDev& d, int grid, int nsteps, abm_step_s
 }
 
 }  // namespace abm
+
+extern "C" abm_status abm_diag_barrier_timeout(int32_t spin_limit, void* stream) {
+  using namespace abm;
+  if (spin_limit < 1 || spin_limit > (1 << 24)) return ABM_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  u32* bar = nullptr;
+  int* err = nullptr;
+  ABM_CUDA_TRY(cudaMalloc(&bar, sizeof(u32) * 2));
+  if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+    cudaFree(bar);
+    return ABM_ERR_OOM;
+  }
+  abm_status rc = ABM_OK;
+  if (cudaMemsetAsync(bar, 0, sizeof(u32) * 2, st) != cudaSuccess || cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess)
+    rc = ABM_ERR_CUDA;
+  if (rc == ABM_OK) {
+    void* args[] = {(void*)&bar, (void*)&err, (void*)&spin_limit};
+    if (cudaLaunchCooperativeKernel((const void*)k_barrier_timeout, dim3((unsigned)num_sms()), dim3(32), args, 0, st) !=
+        cudaSuccess)
+      rc = ABM_ERR_CUDA;
+  }
+  int herr = 0;
+  if (rc == ABM_OK && (cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                       cudaStreamSynchronize(st) != cudaSuccess))
+    rc = ABM_ERR_CUDA;
+  cudaFree(bar);
+  cudaFree(err);
+  if (rc != ABM_OK) return rc;
+  return herr ? ABM_ERR_DEVICE_TIMEOUT : ABM_OK;
+}
