@@ -49,7 +49,17 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the microbenchmark, batched and CPU legs")
-    return ap.parse_args()
+    ap.add_argument("--leg", default="all", choices=["all", "predation", "selective", "batched"],
+                    help="run one leg alone (profiling); 'all' prints the benchmark line")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="default launch shapes instead of the autotuner (fixed launch sequence for ncu)")
+    ap.add_argument("--p", type=float, action="append", help="selective leg: only these p")
+    ap.add_argument("--batch-models", type=int, default=None)
+    ap.add_argument("--batch-steps", type=int, default=None)
+    a = ap.parse_args()
+    if a.leg == "predation":
+        a.no_extras = True
+    return a
 
 
 def peaks():
@@ -137,6 +147,36 @@ def kernel_bytes(k: int, st: dict) -> int:
     return births * (4 + 4 + 16 + 4 + 16 + 4 + (8 if s == 0 else 0))
 
 
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_persistent_large_predation_traffic.txt")
+TRAFFIC_SOURCES = ("pred_persistent.cu", "pred_world.cuh", "pred_rules.cuh", "common.cuh")
+
+
+def persistent_sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2508_16508_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def persistent_traffic(K: int, W: int, ctas_per_sm: int):
+    """DRAM bytes (read + write) of the timed k_persistent launch from the
+    stored ncu capture, or None when the capture covers another step range or
+    the kernel's sources changed since it was taken."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            kv = dict(ln.split("=", 1) for ln in (x.strip() for x in f) if "=" in ln and not ln.startswith("#"))
+        kv = {k.strip(): v.strip() for k, v in kv.items()}
+        if kv.get("sources_sha256") != persistent_sources_sha256():
+            return None
+        if int(kv["steps"]) != K or int(kv["warmup"]) != W or int(kv["ctas_per_sm"]) != ctas_per_sm:
+            return None
+        return int(kv["dram_bytes_read"]) + int(kv["dram_bytes_write"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 # ----------------------------------------------------------------------------
 
 def dist_init(args):
@@ -208,7 +248,7 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def selective_update_leg(torch, engine, abm, autotune, hbm_peak, steps=8, warmup=3):
+def selective_update_leg(torch, engine, abm, autotune, hbm_peak, steps=8, warmup=3, tune=True, ps=None):
     """Selective-update microbenchmark: 2^24 slots x 8 fields, fused remove/update/add call."""
     c = workloads.SELECTIVE
     n, F = c["n"], c["F"]
@@ -216,11 +256,14 @@ def selective_update_leg(torch, engine, abm, autotune, hbm_peak, steps=8, warmup
     # dirty lines whose write-back lands inside the next timed call)
     flush = torch.ones(64 << 20, dtype=torch.int32, device="cuda")
     out = {}
-    for p in c["p"]:
+    for p in (ps or c["p"]):
         T, k = workloads.threshold(p), workloads.k_for(p, n)
-        tuned = autotune.tune_slab(n, F, p, k, seed=c["seed"])
+        tuned = autotune.tune_slab(n, F, p, k, seed=c["seed"]) if tune else None
         s = engine.Slab(n, F, seed=c["seed"], init=abm.INIT_HALF_LIVE)
-        s.tune(tuned["threads"], tuned["ctas_per_sm"])
+        if tuned:
+            s.tune(tuned["threads"], tuned["ctas_per_sm"])
+        else:
+            tuned = {"threads": "default", "ctas_per_sm": "default"}
         rec = torch.empty((k, F), dtype=torch.int32, device="cuda")
         dl = torch.empty((k, F), dtype=torch.int32, device="cuda")
         cnt = torch.zeros(3, dtype=torch.int32, device="cuda")
@@ -244,7 +287,8 @@ def selective_update_leg(torch, engine, abm, autotune, hbm_peak, steps=8, warmup
         b = statistics.median(nbytes)
         gbs = b / (ms * 1e-3) / 1e9
         out[str(p)] = {"k": k, "ms": ms, "algorithmic_bytes": int(b), "gbs": gbs, "frac": gbs / hbm_peak,
-                       "launch": f"{tuned['threads']} threads x {tuned['ctas_per_sm']} CTAs/SM (autotuned)"}
+                       "launch": f"{tuned['threads']} threads x {tuned['ctas_per_sm']} CTAs/SM"
+                                 + (" (autotuned)" if tune else "")}
         del s, rec, dl
     # conflict pass: M = N/4 claims over R = N/64 resources, Zipf(1.1)
     M, R = n // 4, n // 64
@@ -272,20 +316,24 @@ def selective_update_leg(torch, engine, abm, autotune, hbm_peak, steps=8, warmup
     return out
 
 
-def batched_leg(torch, engine, capacity, autotune, abm, hbm_peak):
+def batched_leg(torch, engine, capacity, autotune, abm, hbm_peak, n_models=None, steps=None, tune=True):
     """Batched models: plain fixed capacity (static shapes, the whole capacity
     swept every step) vs learned capacity (MLP-sized slabs, device overflow
     detection, fixed-capacity rerun of the overflowed models)."""
     B = workloads.BATCH
-    steps = B["steps"]
+    steps = steps or B["steps"]
+    n_models = n_models or B["n_models"]
     tab = workloads.sample_models(B["n_models"], B["sampler_seed"])
-    fixed = workloads.fixed_caps(tab["side"])
+    fixed = workloads.fixed_caps(tab["side"])[:n_models]
     models = [dict(side=int(tab["side"][i]), seed=B["philox_seed"], model=i, params=tab["params"][i],
-                   cap=fixed[i], n0=tab["n0"][i]) for i in range(B["n_models"])]
-    tf = autotune.tune_batch(models, steps, abm.SWEEP_CAPACITY)
+                   cap=fixed[i], n0=tab["n0"][i]) for i in range(n_models)]
+    default = {"threads": 512, "ctas_per_sm": 2}
+    tf = autotune.tune_batch(models, steps, abm.SWEEP_CAPACITY) if tune else default
     th, cps = tf["threads"], tf["ctas_per_sm"]
-    out = {"workload": B["name"], "models": B["n_models"], "steps": steps,
-           "launch_fixed": f"{th} threads x {cps} CTAs/SM (autotuned)"}
+    out = {"workload": B["name"] if n_models == B["n_models"] and steps == B["steps"]
+           else f"{n_models} models of {B['name']}, {steps} steps",
+           "models": n_models, "steps": steps,
+           "launch_fixed": f"{th} threads x {cps} CTAs/SM" + (" (autotuned)" if tune else "")}
     # plain fixed capacity (one persistent launch for all 500 steps)
     b = engine.Batch(models)
     b.tune(th, cps)
@@ -324,13 +372,13 @@ def batched_leg(torch, engine, capacity, autotune, abm, hbm_peak):
     wpath = os.path.join(ROOT, "paper_2508_16508_gb300", "data", "capacity_mlp.npz")
     m = capacity.CapacityModel.load(wpath)
     e0.record()
-    learned = m.capacities(m.features(capacity.table_of(models, steps)), fixed, tab["n0"], margin=0.0)
+    learned = m.capacities(m.features(capacity.table_of(models, steps)), fixed, tab["n0"][:n_models], margin=0.0)
     e1.record()
     e1.synchronize()
     t_mlp = e0.elapsed_time(e1)
     lmodels = [dict(m, cap=(int(cc[0]), int(cc[1]))) for m, cc in zip(models, learned)]
-    tl = autotune.tune_batch(lmodels, steps, abm.SWEEP_CAPACITY)
-    out["launch_learned"] = f"{tl['threads']} threads x {tl['ctas_per_sm']} CTAs/SM (autotuned)"
+    tl = autotune.tune_batch(lmodels, steps, abm.SWEEP_CAPACITY) if tune else default
+    out["launch_learned"] = f"{tl['threads']} threads x {tl['ctas_per_sm']} CTAs/SM" + (" (autotuned)" if tune else "")
     res = capacity.run_learned(models, learned, fixed, steps, threads=tl["threads"], ctas_per_sm=tl["ctas_per_sm"])
     t_learned = res["ms_learned"] + res["ms_rerun"] + t_mlp
     out["learned"] = {"ms": t_learned, "ms_run": res["ms_learned"], "ms_rerun": res["ms_rerun"], "ms_mlp": t_mlp,
@@ -351,9 +399,20 @@ def run_ours(args, rank, world, local):
     from paper_2508_16508_gb300 import abm, autotune, capacity, engine
     abm.lib()
     hbm_peak, peak_kind = peaks()
+    if args.leg in ("selective", "batched"):
+        if rank == 0:
+            with ClockSampler(local) as clk:
+                if args.leg == "selective":
+                    out = selective_update_leg(torch, engine, abm, autotune, hbm_peak, tune=not args.no_tune,
+                                               ps=args.p)
+                else:
+                    out = batched_leg(torch, engine, capacity, autotune, abm, hbm_peak, n_models=args.batch_models,
+                                      steps=args.batch_steps, tune=not args.no_tune)
+            print(json.dumps({"leg": args.leg, "result": out, "clocks": clk.summary()}), flush=True)
+        return
     c = workloads.PRED_LARGE
     # each rank runs an independent replica (its own Philox model id)
-    tw = autotune.tune_world(c)
+    tw = autotune.tune_world(c) if not args.no_tune else {"engine": abm.ENGINE_PERSISTENT, "ctas_per_sm": 2}
     gw = engine.World(c["side"], c["seed"], c["model"] + rank, c["params"], c["cap"], c["n0"])
     gw.tune(tw["engine"], tw["ctas_per_sm"])
     K, W = args.steps, args.warmup
@@ -383,7 +442,8 @@ def run_ours(args, rank, world, local):
     achieved = step_bytes / (ms_total * 1e-3) / 1e9
     roofline = {"kernel": "k_persistent (all phases of all timed steps, one cooperative launch)",
                 "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "peak_kind": peak_kind,
-                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": persistent_traffic(K, W, tw["ctas_per_sm"])
+                if tw["engine"] == abm.ENGINE_PERSISTENT else None,
                 "launch_ms": ms_total, "algorithmic_bytes_per_launch": step_bytes,
                 "note": "latency-bound: dependent random cell accesses and 6 grid barriers per step"}
 
@@ -392,7 +452,9 @@ def run_ours(args, rank, world, local):
             "vs_baseline": None, "dtype": "int32", "data": "synthetic (Philox-seeded initial state)",
             "config": dict(config_block(), engine=("persistent" if tw["engine"] == abm.ENGINE_PERSISTENT
                                                     else "kernels"), ctas_per_sm=tw["ctas_per_sm"],
-                           launch="autotuned"),
+                           launch="default" if args.no_tune else "autotuned",
+                           tune_trials_ms=[[("persistent" if x["engine"] == abm.ENGINE_PERSISTENT else "kernels"),
+                                            x["ctas_per_sm"], round(x["ms"], 3)] for x in tw.get("trials", [])]),
             "roofline": roofline, "gpu_launches": 1 if tw["engine"] == abm.ENGINE_PERSISTENT else 6 * K,
             "phases_us_per_step": {n: 1e3 * phase[i] / max(K, 1) for i, n in enumerate(
                 ("A_prev_wolf_births_sheep_move", "B_sheep_eat_select_flags", "C_sheep_ranks", "D_sheep_births_wolf_move",
@@ -402,13 +464,19 @@ def run_ours(args, rank, world, local):
     if rank == 0 and not args.no_extras:
         # end to end through the public API: one abm_step per step, then the
         # step's statistics read back to pinned host memory
-        ew = engine.World(c["side"], c["seed"], c["model"], c["params"], c["cap"], c["n0"])
-        ne = min(K, 300)
+        ew = engine.World(c["side"], c["seed"], c["model"] + rank, c["params"], c["cap"], c["n0"])
+        ew.tune(tw["engine"], tw["ctas_per_sm"])
+        ne = K
         sdev = ew.new_stats(1)
         shost = torch.empty_like(sdev, device="cpu").pin_memory()
         ew.step(W)
+        nb = ew.image_bytes()
+        img_in = torch.empty(nb, dtype=torch.uint8).pin_memory()
+        img_out = torch.empty(nb, dtype=torch.uint8).pin_memory()
+        ew.save_into(img_in)  # the state after the warm-up steps, as a host checkpoint
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        ew.load_from(img_in)  # the run's input: the whole state, host -> device
         ea = 0
         for _ in range(ne):
             ew.step(1, sdev)
@@ -416,13 +484,16 @@ def run_ours(args, rank, world, local):
             torch.cuda.current_stream().synchronize()
             r = engine.decode_stats(shost)[0]
             ea += r["n_start"][0] + r["n_start"][1]
+        ew.save_into(img_out)  # the run's output: the whole state, device -> host
         e2e_dt = time.perf_counter() - t0
-        line["e2e"] = {"value": ea / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": 0,
-                       "d2h_bytes_per_step": abm.STATS_BYTES,
-                       "note": "abm_step (one persistent launch per step) + synchronous read-back of the "
-                               "step's statistics; the model state lives on the device, so a step has no "
-                               "host input"}
-        del ew
+        line["e2e"] = {"value": ea / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": nb / max(ne, 1),
+                       "d2h_bytes_per_step": abm.STATS_BYTES + nb / max(ne, 1),
+                       "steps": ne, "state_bytes": nb,
+                       "same_trajectory_as_timed_run": ew.counters() == gw.counters(),
+                       "note": "abm_load of the state from pinned host memory, then per step one abm_step "
+                               "call and a synchronous read-back of the step's statistics, then abm_save "
+                               "of the final state to pinned host memory; wall clock"}
+        del ew, img_in, img_out
         line["selective_update"] = selective_update_leg(torch, engine, abm, autotune, hbm_peak)
         line["batched"] = batched_leg(torch, engine, capacity, autotune, abm, hbm_peak)
     clk.__exit__(None, None, None)

@@ -10,8 +10,10 @@
 //   5. wolves eat / select / die, flags, counts
 //   6. wolves ranks -> lists; counters and statistics of the step
 //   (7. wolf births run together with phase 1 of the next step)
-// Every CTA owns one static chunk of [0, extent) in phases 2/3 and 5/6, so a
-// rank is a prefix over per-CTA totals plus a warp scan: no look-back chains.
+// Phases 1/2 and 4/5 deal 128-slot units to warps round-robin over the CTAs
+// (the live agents crowd the low slots); phases 3/6 give CTA b a contiguous
+// run of units, so a rank is a prefix over per-run sums, a block scan of the
+// unit counts and a warp scan: no look-back chains.
 // Every thread keeps the world counters in registers and updates them from
 // the same totals, so no counter needs a broadcast.
 #include <algorithm>
@@ -22,169 +24,243 @@ namespace abm {
 
 constexpr int kPT = 512;                  // threads per CTA
 constexpr int kPWarps = kPT / 32;
-constexpr int kPCStep = kPWarps * 128;    // chunks are multiples of 128 slots per warp
-constexpr int kBarSpin = 1 << 24;         // bounded barrier wait (~2 s with the back-off)
+constexpr int kBarSpin = 1 << 24;
+constexpr int kPhases = 6;                // grid barriers per step         // bounded barrier wait (~2 s with the back-off)
 
-// Grid barrier (all CTAs co-resident: cooperative launch). Generation-based:
-// the last CTA to arrive resets the arrival count and bumps the generation.
-// A wait that runs out records an error and proceeds (results are then
-// invalid, but the kernel ends).
-__device__ __forceinline__ void grid_sync(u32* bar, int* err, u32 expected = 0, int limit = kBarSpin) {
-  if (expected == 0) expected = gridDim.x;
+// Grid barrier (all CTAs co-resident: cooperative launch) over a monotonic
+// arrival counter: the k-th barrier of a launch is passed once the counter
+// reaches base + k * G, base = the arrivals of all earlier launches (kept by
+// the host, which knows that each step has kPhases barriers). Each CTA arrives with
+// a release add after its threads meet at __syncthreads and waits with
+// acquire loads, so everything written before the barrier anywhere in the
+// grid is visible after it. A wait that runs out records an error and
+// proceeds (results are then invalid, but the kernel ends).
+__device__ __forceinline__ u32 ld_acquire32(const u32* p) {
+  u32 v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void red_release_add(u32* p, u32 v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void grid_sync(u32* bar, int* err, u32& target, u32 expected = 0, int limit = kBarSpin) {
+  target += expected == 0 ? gridDim.x : expected;
   __syncthreads();
   if (threadIdx.x == 0) {
-    const u32 gen = ld_relaxed32(bar + 1);
-    __threadfence();
-    const u32 arrived = atomicAdd(bar, 1u);
-    if (arrived == expected - 1) {
-      bar[0] = 0u;
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      int spins = 0;
-      u32 backoff = 16;
-      while (ld_relaxed32(bar + 1) == gen) {
-        if (++spins > limit) {
-          atomicExch(err, kErrTimeout);
-          break;
-        }
-        if (ld_relaxed32(reinterpret_cast<const u32*>(err)) != 0u) break;  // another CTA gave up
-        __nanosleep(backoff);
-        if (backoff < 128) backoff <<= 1;
+    red_release_add(bar, 1u);
+    int spins = 0;
+    u32 backoff = 16;
+    while ((int)(ld_acquire32(bar) - target) < 0) {
+      if (++spins > limit) {
+        atomicExch(err, kErrTimeout);
+        break;
       }
+      if (ld_relaxed32(reinterpret_cast<const u32*>(err)) != 0u) break;  // another CTA gave up
+      __nanosleep(backoff);
+      if (backoff < 128) backoff <<= 1;
     }
-    __threadfence();
   }
   __syncthreads();
 }
 
+// Work compaction over a CTA: in one pass every warp loads the live flags of
+// one 128-slot unit (lane l: slots 4l..4l+3, live mask m); the live slots of
+// the CTA's 16 units go into one shared list, entry = warp << 7 | offset, so
+// that all 512 threads then work on whole live agents instead of the warps of
+// dense units working while the others idle on placeholders.
+struct CtaList {
+  unsigned short* list;  // [kPWarps * 128]
+  int* wcnt;             // [kPWarps]
+};
+
+__device__ __forceinline__ int cta_list_live(u32 m, const CtaList& cl) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const u32 lt = (1u << lane) - 1u;
+  const u32 b0 = __ballot_sync(0xFFFFFFFFu, m & 1u), b1 = __ballot_sync(0xFFFFFFFFu, m & 2u);
+  const u32 b2 = __ballot_sync(0xFFFFFFFFu, m & 4u), b3 = __ballot_sync(0xFFFFFFFFu, m & 8u);
+  int pre = __popc(b0 & lt) + __popc(b1 & lt) + __popc(b2 & lt) + __popc(b3 & lt);
+  if (lane == 0) cl.wcnt[warp] = __popc(b0) + __popc(b1) + __popc(b2) + __popc(b3);
+  __syncthreads();
+  int tot = 0;
+#pragma unroll
+  for (int k = 0; k < kPWarps; ++k) {
+    const int c = cl.wcnt[k];
+    if (k < warp) pre += c;
+    tot += c;
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if (m & (1u << j)) cl.list[pre++] = (unsigned short)((warp << 7) | (4 * lane + j));
+  __syncthreads();
+  return tot;
+}
+
+__device__ __forceinline__ u32 live_mask(int4 a) {
+  return (u32)(a.x != 0) | ((u32)(a.y != 0) << 1) | ((u32)(a.z != 0) << 2) | ((u32)(a.w != 0) << 3);
+}
+
+// unit of warp k in pass p of this CTA: units are dealt round-robin over the
+// CTAs (unit i -> CTA i mod G), so the crowded low slots spread over all SMs
+__device__ __forceinline__ int unit_of(int k, int pass) {
+  return (int)blockIdx.x + (int)gridDim.x * (k + kPWarps * pass);
+}
+
 template <int S>
-__device__ __forceinline__ void p_move(const WorldDev& w, int t, int ext) {
+__device__ __forceinline__ void move_one(const WorldDev& w, int t, int slot, int4 ag, int L, int metab) {
+  const SpeciesDev& sp = w.sp[S];
+  if (S == 0) w.victim[ag.x] = kNoKey;  // last step's victim entry for this cell
+  const u32 dir = draw(w.seed, w.model, (u32)t, (u32)slot, ABM_P_MOVE, (u32)S) >> 29;
+  const int cell = step_cell(ag.x, L, dir);
+  ag.x = cell;
+  ag.y -= metab;
+  ag.w += 1;
+  sp.agent[slot] = ag;
+  if (S == 0) {
+    if (w.regrow[cell] <= t)
+      atomicMin(&w.gclaim[cell], claim_key(draw(w.seed, w.model, (u32)t, (u32)slot, ABM_P_PRIO, 0u), slot));
+  } else {
+    if (w.victim[cell] != kNoKey)
+      atomicMin(&w.wclaim[cell], claim_key(draw(w.seed, w.model, (u32)t, (u32)slot, ABM_P_PRIO, 1u), slot));
+  }
+}
+
+// phase 1/4: move every live agent; claims for the cell's grass (sheep) or
+// the cell's victim (wolves)
+template <int S>
+__device__ __forceinline__ void p_move(const WorldDev& w, int t, int ext, const CtaList& cl) {
   const SpeciesDev& sp = w.sp[S];
   const int L = w.side;
   const int metab = w.params[PRM_SHEEP_METAB + S];
-  const int nq = (ext + 3) >> 2;
-  for (int q = blockIdx.x * kPT + threadIdx.x; q < nq; q += gridDim.x * kPT) {
-    const int4 act = reinterpret_cast<const int4*>(sp.active)[q];
-    const int a4[4] = {act.x, act.y, act.z, act.w};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (!a4[j]) continue;
-      const int slot = 4 * q + j;
-      int4 ag = sp.agent[slot];
-      if (S == 0) w.victim[ag.x] = kNoKey;  // last step's victim entry for this cell
-      const u32 dir = draw(w.seed, w.model, (u32)t, (u32)slot, ABM_P_MOVE, (u32)S) >> 29;
-      const int cell = step_cell(ag.x, L, dir);
-      ag.x = cell;
-      ag.y -= metab;
-      ag.w += 1;
-      sp.agent[slot] = ag;
-      if (S == 0) {
-        if (w.regrow[cell] <= t)
-          atomicMin(&w.gclaim[cell], claim_key(draw(w.seed, w.model, (u32)t, (u32)slot, ABM_P_PRIO, 0u), slot));
-      } else {
-        if (w.victim[cell] != kNoKey)
-          atomicMin(&w.wclaim[cell], claim_key(draw(w.seed, w.model, (u32)t, (u32)slot, ABM_P_PRIO, 1u), slot));
-      }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nblk = (ext + 127) >> 7;
+  for (int pass = 0; unit_of(0, pass) < nblk; ++pass) {
+    const int i = unit_of(warp, pass);
+    const int base = (i << 7) + 4 * lane;
+    int4 act = make_int4(0, 0, 0, 0);
+    if (i < nblk && base < ext) act = reinterpret_cast<const int4*>(sp.active)[base >> 2];
+    const int tot = cta_list_live(live_mask(act), cl);
+    for (int e = threadIdx.x; e < tot; e += 2 * kPT) {
+      const u32 ea = cl.list[e];
+      const int eb = e + kPT < tot ? (int)cl.list[e + kPT] : -1;
+      const int sa = (unit_of((int)(ea >> 7), pass) << 7) + (int)(ea & 127u);
+      const int sb = eb >= 0 ? (unit_of(eb >> 7, pass) << 7) + (eb & 127) : -1;
+      const int4 aa = sp.agent[sa];
+      int4 ab = make_int4(0, 0, 0, 0);
+      if (sb >= 0) ab = sp.agent[sb];
+      move_one<S>(w, t, sa, aa, L, metab);
+      if (sb >= 0) move_one<S>(w, t, sb, ab, L, metab);
     }
+    __syncthreads();  // the list is rewritten by the next pass
   }
 }
 
-__device__ __forceinline__ int chunk_of(int ext) {
-  const int per = (ext + (int)gridDim.x - 1) / (int)gridDim.x;
-  const int c = ((per + kPCStep - 1) / kPCStep) * kPCStep;
-  return c > kPCStep ? c : kPCStep;
+// one live agent of phase 2/5: eat if it won its cell, then die (energy
+// below zero) or be drawn as a parent. Returns bit 0 = parent, bit 1 = died,
+// bit 2 = ate.
+template <int S>
+__device__ __forceinline__ u32 count_one(const WorldDev& w, int t, int slot, int4 ag, u64 cl, int gain, u32 Tr,
+                                         int regrowth) {
+  const SpeciesDev& sp = w.sp[S];
+  const int cell = ag.x;
+  u32 r = 0;
+  if (cl != kNoKey && (u32)cl == (u32)slot) {
+    ag.y += gain;
+    sp.agent[slot].y = ag.y;
+    r |= 4u;
+    if (S == 0) {
+      w.gclaim[cell] = kNoKey;
+      w.regrow[cell] = t + regrowth;
+    } else {
+      w.wclaim[cell] = kNoKey;
+      const u64 v = w.victim[cell];
+      w.sp[0].active[(u32)v] = 0;
+      w.victim[cell] = kNoKey;
+    }
+  }
+  if (ag.y < 0) {
+    sp.active[slot] = 0;
+    r |= 2u;
+  } else {
+    if (draw(w.seed, w.model, (u32)t, (u32)slot, ABM_P_REPRO, (u32)S) < Tr) r |= 1u;
+    if (S == 0)
+      atomicMin(&w.victim[cell], claim_key(draw(w.seed, w.model, (u32)t, (u32)slot, ABM_P_VICTIM, 0u), slot));
+  }
+  return r;
 }
 
-// phase 2/5: eat, select parents, kill the starving; free / parent flags into
-// bit-planes (word = 32 slots = 8 lanes x 4 slots), per-warp and per-CTA counts
+// phase 2/5: eat, select parents, kill the starving. Units are dealt and
+// their live agents listed as for the moves. Each unit then writes its free /
+// parent bits into the bit-planes (word = 32 slots = 8 lanes x 4 slots) and
+// its two counts, which are also summed per run of kseg units (the CTA
+// segments of the rank phase).
 template <int S>
-__device__ __forceinline__ void p_count(const WorldDev& w, int t, int ext, int* acc, u64* s_red) {
+__device__ __forceinline__ void p_count(const WorldDev& w, int t, int ext, int kseg, int* acc, const CtaList& cl,
+                                        u32* s_upar /* [kPWarps][4], zero on entry and exit */) {
   const SpeciesDev& sp = w.sp[S];
   const PersistDev& ps = w.ps;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int chunk = chunk_of(ext);
-  const int seg = chunk / kPWarps;
-  const int wlo = blockIdx.x * chunk + warp * seg;
-  const int whi = min(ext, wlo + seg);
+  const int nblk = (ext + 127) >> 7;
   const int gain = w.params[S];
   const u32 Tr = (u32)w.params[PRM_SHEEP_T + S];
   const int regrowth = w.params[PRM_REGROWTH];
-  u64* claim = S == 0 ? w.gclaim : w.wclaim;
-  u32 cf = 0, cp = 0;
+  const u64* claim = S == 0 ? w.gclaim : w.wclaim;
   int starved = 0, won = 0;
-  for (int b0 = wlo; b0 < whi; b0 += 128) {
-    const int base = b0 + 4 * lane;
+  for (int pass = 0; unit_of(0, pass) < nblk; ++pass) {
+    const int i = unit_of(warp, pass);
+    const int base = (i << 7) + 4 * lane;
     int4 act = make_int4(0, 0, 0, 0);
-    if (base < ext) act = reinterpret_cast<const int4*>(sp.active)[base >> 2];
-    int a4[4] = {act.x, act.y, act.z, act.w};
-    u32 fr = 0, par = 0;
-    bool died = false;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int slot = base + j;
-      if (slot >= ext) continue;
-      if (!a4[j]) {
-        fr |= 1u << j;
-        continue;
-      }
-      int4 ag = sp.agent[slot];
-      const int cell = ag.x;
-      const u64 cl = claim[cell];
-      if (cl != kNoKey && (u32)cl == (u32)slot) {
-        ag.y += gain;
-        sp.agent[slot].y = ag.y;
-        claim[cell] = kNoKey;
-        ++won;
-        if (S == 0) {
-          w.regrow[cell] = t + regrowth;
-        } else {
-          const u64 v = w.victim[cell];
-          w.sp[0].active[(u32)v] = 0;
-          w.victim[cell] = kNoKey;
-        }
-      }
-      if (ag.y < 0) {
-        a4[j] = 0;
-        died = true;
-        ++starved;
-      } else {
-        if (draw(w.seed, w.model, (u32)t, (u32)slot, ABM_P_REPRO, (u32)S) < Tr) par |= 1u << j;
-        if (S == 0)
-          atomicMin(&w.victim[cell], claim_key(draw(w.seed, w.model, (u32)t, (u32)slot, ABM_P_VICTIM, 0u), slot));
+    if (i < nblk && base < ext) act = reinterpret_cast<const int4*>(sp.active)[base >> 2];
+    const u32 m = live_mask(act);
+    const u32 valid = (i >= nblk || base >= ext) ? 0u : (ext - base >= 4 ? 0xFu : (1u << (ext - base)) - 1u);
+    const u32 fr = ~m & valid;
+    const int tot = cta_list_live(m, cl);
+    for (int e = threadIdx.x; e < tot; e += 2 * kPT) {
+      const u32 ea = cl.list[e];
+      const int eb = e + kPT < tot ? (int)cl.list[e + kPT] : -1;
+      const int sa = (unit_of((int)(ea >> 7), pass) << 7) + (int)(ea & 127u);
+      const int sb = eb >= 0 ? (unit_of(eb >> 7, pass) << 7) + (eb & 127) : -1;
+      const int4 aa = sp.agent[sa];
+      int4 ab = make_int4(0, 0, 0, 0);
+      if (sb >= 0) ab = sp.agent[sb];
+      const u64 ca = claim[aa.x];
+      const u64 cb = sb >= 0 ? claim[ab.x] : kNoKey;
+      u32 r = count_one<S>(w, t, sa, aa, ca, gain, Tr, regrowth);
+      if (r & 1u) atomicOr(&s_upar[4 * (ea >> 7) + ((ea & 127u) >> 5)], 1u << (ea & 31u));
+      starved += (r >> 1) & 1u;
+      won += (r >> 2) & 1u;
+      if (sb >= 0) {
+        r = count_one<S>(w, t, sb, ab, cb, gain, Tr, regrowth);
+        if (r & 1u) atomicOr(&s_upar[4 * (eb >> 7) + ((eb & 127) >> 5)], 1u << (eb & 31));
+        starved += (r >> 1) & 1u;
+        won += (r >> 2) & 1u;
       }
     }
-    if (died) reinterpret_cast<int4*>(sp.active)[base >> 2] = make_int4(a4[0], a4[1], a4[2], a4[3]);
-    cf += __popc(fr);
-    cp += __popc(par);
-    // 8 lanes x 4 bits -> one plane word
-    u32 vf = fr << (4 * (lane & 7)), vp = par << (4 * (lane & 7));
+    __syncthreads();
+    if (i < nblk) {
+      const u32 pw = s_upar[4 * warp + (lane >> 3)];
+      const u32 par = (pw >> (4 * (lane & 7))) & 0xFu;
+      // 8 lanes x 4 bits -> one plane word
+      u32 vf = fr << (4 * (lane & 7));
 #pragma unroll
-    for (int o = 1; o < 8; o <<= 1) {
-      vf |= __shfl_xor_sync(0xFFFFFFFFu, vf, o);
-      vp |= __shfl_xor_sync(0xFFFFFFFFu, vp, o);
-    }
-    if ((lane & 7) == 0 && base < ext) {
-      ps.plane[S][0][base >> 5] = vf;
-      ps.plane[S][1][base >> 5] = vp;
-    }
-  }
-  u64 v = ((u64)cf << 32) | cp;
+      for (int o = 1; o < 8; o <<= 1) vf |= __shfl_xor_sync(0xFFFFFFFFu, vf, o);
+      if ((lane & 7) == 0 && base < ext) {
+        ps.plane[S][0][base >> 5] = vf;
+        ps.plane[S][1][base >> 5] = pw;
+      }
+      u32 cu = ((u32)__popc(fr) << 16) | (u32)__popc(par);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-  if (lane == 0) {
-    ps.wtotals[2 * (blockIdx.x * kPWarps + warp)] = (u32)(v >> 32);
-    ps.wtotals[2 * (blockIdx.x * kPWarps + warp) + 1] = (u32)v;
-  }
-  // per-CTA totals
-  __syncthreads();
-  if (lane == 0) s_red[warp] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    u64 tt = 0;
-    for (int i = 0; i < kPWarps; ++i) tt += s_red[i];
-    ps.totals[2 * blockIdx.x] = (u32)(tt >> 32);
-    ps.totals[2 * blockIdx.x + 1] = (u32)tt;
+      for (int o = 16; o > 0; o >>= 1) cu += __shfl_xor_sync(0xFFFFFFFFu, cu, o);
+      if (lane == 0) {
+        const u64 v = ((u64)(cu >> 16) << 32) | (cu & 0xFFFFu);
+        ps.blk[S][i] = v;
+        atomicAdd(reinterpret_cast<unsigned long long*>(&ps.seg[S][i / kseg]), (unsigned long long)v);
+      }
+      __syncwarp();
+      if (lane < 4) s_upar[4 * warp + lane] = 0u;
+    }
+    __syncthreads();  // the list and the unit words are rewritten by the next pass
   }
   // accumulators (warp-aggregated)
 #pragma unroll
@@ -198,12 +274,14 @@ __device__ __forceinline__ void p_count(const WorldDev& w, int t, int ext, int* 
   }
 }
 
-// grand totals of the per-CTA counts: (free, parents), in every thread
+// grand totals of the per-segment counts: (free, parents) over all segments
+// and over the segments before this CTA's, in every thread
+template <int S>
 __device__ __forceinline__ void grand_totals(const PersistDev& ps, u32& F, u32& P, u32& preF, u32& preP,
                                              u64* s_red) {
   u64 tot = 0, pre = 0;
   for (int j = threadIdx.x; j < (int)gridDim.x; j += kPT) {
-    const u64 x = ((u64)ps.totals[2 * j] << 32) | ps.totals[2 * j + 1];
+    const u64 x = ps.seg[S][j];
     tot += x;
     if (j < (int)blockIdx.x) pre += x;
   }
@@ -227,70 +305,70 @@ __device__ __forceinline__ void grand_totals(const PersistDev& ps, u32& F, u32& 
   P = (u32)tot;
   preF = (u32)(pre >> 32);
   preP = (u32)pre;
+  __syncthreads();  // s_red is reused by the caller
 }
 
-// phase 3/6: ranks -> parent list (all) and free list (ranks below P only)
+// phase 3/6: ranks -> parent list (all) and free list (ranks below P only).
+// CTA b owns units [b*kseg, (b+1)*kseg); the unit ranks are the segment's
+// prefix plus a block scan of the unit counts; inside a unit, a warp scan.
 template <int S>
-__device__ __forceinline__ void p_scatter(const WorldDev& w, int ext, u32 P, u32 preF, u32 preP) {
+__device__ __forceinline__ void p_ranks(const WorldDev& w, int ext, int kseg, u32 P, u32 preF, u32 preP,
+                                        u64* s_red, u64* s_pre) {
   const SpeciesDev& sp = w.sp[S];
   const PersistDev& ps = w.ps;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  u32 pf = preF, pp = preP;
-  {
-    u32 x = 0, y = 0;
-    if (lane < warp) {
-      x = ps.wtotals[2 * (blockIdx.x * kPWarps + lane)];
-      y = ps.wtotals[2 * (blockIdx.x * kPWarps + lane) + 1];
-    }
+  const int nblk = (ext + 127) >> 7;
+  const int j0 = blockIdx.x * kseg, j1 = min(nblk, j0 + kseg);
+  u32 cf = preF, cp = preP;
+  for (int c0 = j0; c0 < j1; c0 += kPT) {
+    const int j = c0 + threadIdx.x;
+    const u64 v = j < j1 ? ps.blk[S][j] : 0ull;
+    u32 exf, exp_, tf, tp;
+    block_scan2<kPT>((u32)(v >> 32), (u32)v, exf, exp_, tf, tp, s_red);
+    s_pre[threadIdx.x] = ((u64)(cf + exf) << 32) | (u64)(cp + exp_);
+    __syncthreads();
+    const int cn = min(kPT, j1 - c0);
+    for (int q = warp; q < cn; q += kPWarps) {
+      const u64 pre = s_pre[q];
+      u32 pf = (u32)(pre >> 32), pp = (u32)pre;
+      const int base = ((c0 + q) << 7) + 4 * lane;
+      u32 fr = 0, par = 0;
+      if (base < ext) {
+        const int sh = 4 * (lane & 7);
+        fr = (ps.plane[S][0][base >> 5] >> sh) & 0xFu;
+        par = (ps.plane[S][1][base >> 5] >> sh) & 0xFu;
+      }
+      const u32 c = (u32)__popc(fr) | ((u32)__popc(par) << 16);
+      u32 inc = c;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
-      y += __shfl_xor_sync(0xFFFFFFFFu, y, o);
+      for (int o = 1; o < 32; o <<= 1) {
+        const u32 x = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+        if (lane >= o) inc += x;
+      }
+      const u32 ex = inc - c;
+      u32 rf = pf + (ex & 0xFFFFu), rp = pp + (ex >> 16);
+      while (fr && rf < P) {  // only the first P free slots can receive a child
+        const int jj = __ffs(fr) - 1;
+        fr &= fr - 1;
+        sp.freel[rf++] = base + jj;
+      }
+      while (par) {
+        const int jj = __ffs(par) - 1;
+        par &= par - 1;
+        sp.parents[rp++] = base + jj;
+      }
     }
-    pf += x;
-    pp += y;
-  }
-  const int chunk = chunk_of(ext);
-  const int seg = chunk / kPWarps;
-  const int wlo = blockIdx.x * chunk + warp * seg;
-  const int whi = min(ext, wlo + seg);
-  for (int b0 = wlo; b0 < whi; b0 += 128) {
-    const int base = b0 + 4 * lane;
-    u32 fr = 0, par = 0;
-    if (base < ext) {
-      const int sh = 4 * (lane & 7);
-      fr = (ps.plane[S][0][base >> 5] >> sh) & 0xFu;
-      par = (ps.plane[S][1][base >> 5] >> sh) & 0xFu;
-    }
-    const u32 c = (u32)__popc(fr) | ((u32)__popc(par) << 16);
-    u32 inc = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const u32 x = __shfl_up_sync(0xFFFFFFFFu, inc, o);
-      if (lane >= o) inc += x;
-    }
-    const u32 tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
-    const u32 ex = inc - c;
-    u32 rf = pf + (ex & 0xFFFFu), rp = pp + (ex >> 16);
-    pf += tot & 0xFFFFu;
-    pp += tot >> 16;
-    while (fr && rf < P) {  // only the first P free slots can receive a child
-      const int j = __ffs(fr) - 1;
-      fr &= fr - 1;
-      sp.freel[rf++] = base + j;
-    }
-    while (par) {
-      const int j = __ffs(par) - 1;
-      par &= par - 1;
-      sp.parents[rp++] = base + j;
-    }
+    cf += tf;
+    cp += tp;
+    __syncthreads();  // s_pre and s_red are rewritten by the next pass
   }
 }
 
 template <int S>
 __device__ __forceinline__ void p_births(const WorldDev& w, int t, int r, int F, int ext, int id0) {
   const SpeciesDev& sp = w.sp[S];
-  for (int i = blockIdx.x * kPT + threadIdx.x; i < r; i += gridDim.x * kPT) {
+  // birth i -> CTA i mod G: the births spread over all SMs
+  for (int i = blockIdx.x + gridDim.x * threadIdx.x; i < r; i += gridDim.x * kPT) {
     const int p = sp.parents[i];
     const int slot = i < F ? sp.freel[i] : ext + (i - F);
     const int4 pa = sp.agent[p];
@@ -329,11 +407,21 @@ struct PhaseClock {
   }
 };
 
-__global__ void __launch_bounds__(kPT) k_persistent(WorldDev w, int nsteps, abm_step_stats* stats,
+// MINB = resident CTAs per SM the register budget is cut for (1: up to 128
+// registers a thread, 2: 64).
+template <int MINB>
+__global__ void __launch_bounds__(kPT, MINB) k_persistent(WorldDev w, int nsteps, abm_step_stats* stats,
                                                      unsigned long long* phase_ns) {
   __shared__ u64 s_red[2 * kPWarps];
+  __shared__ u64 s_pre[kPT];
+  __shared__ unsigned short s_clist[kPWarps * 128];
+  __shared__ int s_wcnt[kPWarps];
+  __shared__ u32 s_upar[kPWarps * 4];
+  const CtaList cl{s_clist, s_wcnt};
+  if (threadIdx.x < kPWarps * 4) s_upar[threadIdx.x] = 0u;
   PhaseClock clk{phase_ns, 0};
   clk.start();
+  u32 bar_target = w.bar_base;  // arrival count that completes the next barrier
   WorldCtr* c = w.ctr;
   const PersistDev& ps = w.ps;
   // counters: one copy per thread, all updated identically
@@ -352,33 +440,38 @@ __global__ void __launch_bounds__(kPT) k_persistent(WorldDev w, int nsteps, abm_
     // ---- phase 1: sheep move (+ wolf births of the previous step)
     if (it > 0) p_births<1>(w, t - 1, wb.r, wb.F, wb.ext, wb.id0);
     if (blockIdx.x == 0 && threadIdx.x == 0) acc[0] = acc[1] = acc[2] = acc[3] = 0;  // unused since step t-2
-    p_move<0>(w, t, ext[0]);
+    if (blockIdx.x == 0)  // wolf segment sums: last read in phase 6 of the previous step
+      for (int j = threadIdx.x; j < (int)gridDim.x; j += kPT) ps.seg[1][j] = 0ull;
+    p_move<0>(w, t, ext[0], cl);
     if (blockIdx.x == 0 && threadIdx.x == 0 && st) {
       st->n_start[0] = nstart0;
       st->n_start[1] = nstart1;
       st->extent[0] = ext[0];
       st->extent[1] = ext[1];
     }
-    grid_sync(ps.bar, w.err);
+    grid_sync(ps.bar, w.err, bar_target);
     clk.lap(0);
     if (*(volatile int*)w.err) return;
     // ---- phase 2: sheep eat / select / die / flags
-    p_count<0>(w, t, ext[0], acc, s_red);
-    grid_sync(ps.bar, w.err);
+    const int kseg0 = (((ext[0] + 127) >> 7) + (int)gridDim.x - 1) / (int)gridDim.x;
+    p_count<0>(w, t, ext[0], kseg0, acc, cl, s_upar);
+    grid_sync(ps.bar, w.err, bar_target);
     clk.lap(1);
     // ---- phase 3: sheep ranks and lists; sheep counters
     u32 F0, P0, preF, preP;
-    grand_totals(ps, F0, P0, preF, preP, s_red);
-    p_scatter<0>(w, ext[0], P0, preF, preP);
+    grand_totals<0>(ps, F0, P0, preF, preP, s_red);
+    p_ranks<0>(w, ext[0], kseg0, P0, preF, preP, s_red, s_pre);
     const int avail0 = (int)F0 + (cap[0] - ext[0]);
     const int r0 = min((int)P0, avail0);
     const Births sb = {r0, (int)F0, ext[0], nid[0]};
-    grid_sync(ps.bar, w.err);
+    grid_sync(ps.bar, w.err, bar_target);
     clk.lap(2);
     // ---- phase 4: sheep births, wolves move + claims (a wolf only needs a live
     // sheep on its cell; every newborn lamb sits with its live parent)
     p_births<0>(w, t, sb.r, sb.F, sb.ext, sb.id0);
-    p_move<1>(w, t, ext[1]);
+    if (blockIdx.x == 0)  // sheep segment sums: last read in phase 3
+      for (int j = threadIdx.x; j < (int)gridDim.x; j += kPT) ps.seg[0][j] = 0ull;
+    p_move<1>(w, t, ext[1], cl);
     const int starved0 = acc[0], grass = acc[3];
     {
       const int n_after = nstart0 + r0;
@@ -388,16 +481,17 @@ __global__ void __launch_bounds__(kPT) k_persistent(WorldDev w, int nsteps, abm_
       if (r0 > (int)F0) ext[0] += r0 - (int)F0;
       if ((int)P0 > avail0) ovf[0] = 1;
     }
-    grid_sync(ps.bar, w.err);
+    grid_sync(ps.bar, w.err, bar_target);
     clk.lap(3);
     // ---- phase 5: wolves eat / kill / select / die / flags
-    p_count<1>(w, t, ext[1], acc, s_red);
-    grid_sync(ps.bar, w.err);
+    const int kseg1 = (((ext[1] + 127) >> 7) + (int)gridDim.x - 1) / (int)gridDim.x;
+    p_count<1>(w, t, ext[1], kseg1, acc, cl, s_upar);
+    grid_sync(ps.bar, w.err, bar_target);
     clk.lap(4);
     // ---- phase 6: wolf ranks and lists; counters; statistics
     u32 F1, P1, preF1, preP1;
-    grand_totals(ps, F1, P1, preF1, preP1, s_red);
-    p_scatter<1>(w, ext[1], P1, preF1, preP1);
+    grand_totals<1>(ps, F1, P1, preF1, preP1, s_red);
+    p_ranks<1>(w, ext[1], kseg1, P1, preF1, preP1, s_red, s_pre);
     const int starved1 = acc[1], eaten = acc[2];
     const int avail1 = (int)F1 + (cap[1] - ext[1]);
     const int r1 = min((int)P1, avail1);
@@ -428,7 +522,7 @@ __global__ void __launch_bounds__(kPT) k_persistent(WorldDev w, int nsteps, abm_
       st->step = t;
     }
     ++t;
-    grid_sync(ps.bar, w.err);
+    grid_sync(ps.bar, w.err, bar_target);
     clk.lap(5);
   }
   // the last step's wolf births
@@ -450,22 +544,27 @@ __global__ void __launch_bounds__(kPT) k_persistent(WorldDev w, int nsteps, abm_
 // and returns. Used to show that a wait which never completes ends the kernel
 // with an error status instead of hanging the GPU.
 __global__ void k_barrier_timeout(u32* bar, int* err, int limit) {
-  grid_sync(bar, err, gridDim.x + 1, limit);
+  u32 target = 0;
+  grid_sync(bar, err, target, gridDim.x + 1, limit);
 }
 
 int persistent_max_ctas() {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent, kPT, 0) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent<2>, kPT, 0) != cudaSuccess) return 0;
   return nb * num_sms();
 }
 
 int persistent_warps() { return kPWarps; }
 
-abm_status launch_persistent(const WorldDev& d, int grid, int nsteps, abm_step_stats* stats, cudaStream_t st,
-                             unsigned long long* phase_ns) {
+abm_status launch_persistent(const WorldDev& d, u32* bar_next, int grid, int nsteps, abm_step_stats* stats,
+                             cudaStream_t st, unsigned long long* phase_ns) {
   WorldDev dd = d;
+  dd.bar_base = *bar_next;
   void* args[] = {(void*)&dd, (void*)&nsteps, (void*)&stats, (void*)&phase_ns};
-  ABM_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_persistent, dim3((unsigned)grid), dim3(kPT), args, 0, st));
+  // one CTA per SM: the variant with the larger register budget
+  const void* fn = grid <= num_sms() ? (const void*)k_persistent<1> : (const void*)k_persistent<2>;
+  ABM_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), dim3(kPT), args, 0, st));
+  *bar_next += (u32)kPhases * (u32)nsteps * (u32)grid;  // arrivals this launch adds to the counter
   return ABM_OK;
 }
 

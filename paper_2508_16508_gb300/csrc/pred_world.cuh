@@ -32,9 +32,9 @@ struct WorldCtr {
 // scratch of the persistent step kernel
 struct PersistDev {
   u32* plane[2][2];   // per species: [0] free, [1] parent bit-planes (cap/32 words)
-  u32* totals;        // [2 * max CTAs] per-CTA (free, parent) counts
-  u32* wtotals;       // [2 * max CTAs * warps] per-warp counts
-  u32* bar;           // [0] arrivals, [1] generation
+  u64* blk[2];        // per species: (free << 32 | parents) of each 128-slot unit (cap/128)
+  u64* seg[2];        // per species: the same summed over each CTA's run of units (max CTAs)
+  u32* bar;           // [0] grid-barrier arrivals (monotonic, wraps)
   int* acc;           // [2][4] per-step accumulators by step parity: starved0, starved1, eaten, grass
 };
 
@@ -49,13 +49,15 @@ struct WorldDev {
   int* err;
   int side, ncells;
   u32 seed, model;
+  u32 bar_base;     // barrier arrivals before this launch (persistent kernel)
   int params[8];
 };
 
 // persistent step kernel (pred_persistent.cu)
 int persistent_max_ctas();
 int persistent_warps();
-abm_status launch_persistent(const WorldDev& d, int grid, int nsteps, abm_step_stats* stats, cudaStream_t st,
+abm_status launch_persistent(const WorldDev& d, u32* bar_next, int grid, int nsteps, abm_step_stats* stats,
+                             cudaStream_t st,
                              unsigned long long* phase_ns = nullptr);
 
 }  // namespace abm

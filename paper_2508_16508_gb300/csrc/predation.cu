@@ -285,6 +285,7 @@ struct abm_world {
   int grid;
   int engine;       // ABM_ENGINE_PERSISTENT or ABM_ENGINE_KERNELS
   int pgrid;        // CTAs of the persistent kernel
+  u32 bar_next;     // value of the persistent kernel's barrier counter after the launches so far
   int pgrid_max;
   int64_t steps_host;
   // cached graph
@@ -310,8 +311,10 @@ static void world_free(abm_world* w) {
   cudaFree(w->d.err);
   for (int s = 0; s < 2; ++s)
     for (int k = 0; k < 2; ++k) cudaFree(w->d.ps.plane[s][k]);
-  cudaFree(w->d.ps.totals);
-  cudaFree(w->d.ps.wtotals);
+  for (int s = 0; s < 2; ++s) {
+    cudaFree(w->d.ps.blk[s]);
+    cudaFree(w->d.ps.seg[s]);
+  }
   cudaFree(w->d.ps.bar);
   cudaFree(w->d.ps.acc);
   if (w->gexec) cudaGraphExecDestroy(w->gexec);
@@ -373,8 +376,11 @@ extern "C" abm_status abm_create(const abm_config* cfg, void* stream, abm_world*
   for (int s = 0; s < 2 && ok; ++s)
     for (int k = 0; k < 2 && ok; ++k)
       ok = cudaMalloc(&d.ps.plane[s][k], sizeof(u32) * (size_t)(w->cap_pad[s] / 32)) == cudaSuccess;
-  ok = ok && cudaMalloc(&d.ps.totals, sizeof(u32) * 2 * (size_t)pmax) == cudaSuccess;
-  ok = ok && cudaMalloc(&d.ps.wtotals, sizeof(u32) * 2 * (size_t)pmax * persistent_warps()) == cudaSuccess;
+  for (int s = 0; s < 2 && ok; ++s) {
+    ok = cudaMalloc(&d.ps.blk[s], sizeof(u64) * (size_t)(w->cap_pad[s] / 128)) == cudaSuccess &&
+         cudaMalloc(&d.ps.seg[s], sizeof(u64) * (size_t)pmax) == cudaSuccess &&
+         cudaMemsetAsync(d.ps.seg[s], 0, sizeof(u64) * (size_t)pmax, st) == cudaSuccess;
+  }
   ok = ok && cudaMalloc(&d.ps.bar, sizeof(u32) * 2) == cudaSuccess;
   ok = ok && cudaMalloc(&d.ps.acc, sizeof(int) * 8) == cudaSuccess;
   ok = ok && cudaMemsetAsync(d.ps.bar, 0, sizeof(u32) * 2, st) == cudaSuccess;
@@ -445,7 +451,7 @@ extern "C" abm_status abm_step_profiled(abm_world* w, int32_t nsteps, abm_step_s
     ABM_CUDA_TRY(cudaEventCreate(&e0));
     ABM_CUDA_TRY(cudaEventCreate(&e1));
     cudaEventRecord(e0, st);
-    abm_status rc = nsteps > 0 ? launch_persistent(w->d, w->pgrid, nsteps, stats, st, ns) : ABM_OK;
+    abm_status rc = nsteps > 0 ? launch_persistent(w->d, &w->bar_next, w->pgrid, nsteps, stats, st, ns) : ABM_OK;
     cudaEventRecord(e1, st);
     unsigned long long h[8] = {0};
     if (rc == ABM_OK) {
@@ -496,7 +502,7 @@ extern "C" abm_status abm_step(abm_world* w, int32_t nsteps, abm_step_stats* sta
   if (!w || nsteps < 0) return ABM_ERR_ARG;
   if (w->engine == ABM_ENGINE_PERSISTENT && !want_energy) {
     if (nsteps == 0) return ABM_OK;
-    abm_status e = launch_persistent(w->d, w->pgrid, nsteps, stats, (cudaStream_t)stream);
+    abm_status e = launch_persistent(w->d, &w->bar_next, w->pgrid, nsteps, stats, (cudaStream_t)stream);
     if (e == ABM_OK) w->steps_host += nsteps;
     return e;
   }
@@ -657,6 +663,10 @@ extern "C" abm_status abm_load(abm_world* w, const void* buf, size_t bytes, void
   k_reset_tables<<<num_sms() * 4, 256, 0, st>>>(w->d);
   ABM_LAUNCH_CHECK();
   ABM_CUDA_TRY(cudaMemsetAsync(w->d.ps.acc, 0, sizeof(int) * 8, st));
+  for (int s = 0; s < 2; ++s)
+    ABM_CUDA_TRY(cudaMemsetAsync(w->d.ps.seg[s], 0, sizeof(u64) * (size_t)std::max(1, w->pgrid_max), st));
+  ABM_CUDA_TRY(cudaMemsetAsync(w->d.ps.bar, 0, sizeof(u32) * 2, st));
+  w->bar_next = 0;
   ABM_CUDA_TRY(cudaStreamSynchronize(st));
   w->steps_host = h.step;
   return ABM_OK;

@@ -211,6 +211,20 @@ class World:
         buf = C.create_string_buffer(image, len(image))
         call("abm_load", self.h, buf, len(image), _stream(stream))
 
+    def image_bytes(self) -> int:
+        n = C.c_size_t(0)
+        call("abm_save", self.h, None, C.byref(n), None)
+        return n.value
+
+    def save_into(self, host: torch.Tensor, stream=None):
+        """Checkpoint into a host uint8 tensor (pinned for full copy speed)."""
+        n = C.c_size_t(host.numel())
+        call("abm_save", self.h, ptr(host), C.byref(n), _stream(stream))
+
+    def load_from(self, host: torch.Tensor, stream=None):
+        """Restore from a host uint8 tensor written by save / save_into."""
+        call("abm_load", self.h, ptr(host), host.numel(), _stream(stream))
+
 
 def decode_stats(t: torch.Tensor) -> list[dict]:
     """Device stats rows (int32 words) -> list of dicts."""
