@@ -65,34 +65,52 @@ __device__ __forceinline__ void grid_sync(u32* bar, int* err, u32& target, u32 e
   __syncthreads();
 }
 
-// Work compaction over a CTA: in one pass every warp loads the live flags of
-// one 128-slot unit (lane l: slots 4l..4l+3, live mask m); the live slots of
-// the CTA's 16 units go into one shared list, entry = warp << 7 | offset, so
-// that all 512 threads then work on whole live agents instead of the warps of
-// dense units working while the others idle on placeholders.
+// Work compaction over a CTA: in one round every warp loads the live flags of
+// kQ 128-slot units (lane l: slots 4l..4l+3 of each, live mask m[q]); the live
+// slots of the CTA's kQ * 16 units go into one shared list, entry = v << 7 |
+// offset with v = q * 16 + warp the unit's place in the round, so that all 512
+// threads then work on whole live agents instead of the warps of dense units
+// working while the others idle on placeholders.
+constexpr int kQ = 2;                  // units per warp per round
+constexpr int kRoundUnits = kQ * kPWarps;
+
 struct CtaList {
-  unsigned short* list;  // [kPWarps * 128]
-  int* wcnt;             // [kPWarps]
+  unsigned short* list;  // [kRoundUnits * 128]
+  int* wcnt;             // [kRoundUnits]
+  // carried from a move phase to the count phase of the same species when
+  // all its units fit in one round: the live words of the round's units and,
+  // per list entry, the moved agent's cell and energy
+  u32* live;             // [kRoundUnits * 4]
+  int* cell;             // [kRoundUnits * 128]
+  int* energy;           // [kRoundUnits * 128]
 };
 
-__device__ __forceinline__ int cta_list_live(u32 m, const CtaList& cl) {
+__device__ __forceinline__ int cta_list_live(const u32 (&m)[kQ], const CtaList& cl) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const u32 lt = (1u << lane) - 1u;
-  const u32 b0 = __ballot_sync(0xFFFFFFFFu, m & 1u), b1 = __ballot_sync(0xFFFFFFFFu, m & 2u);
-  const u32 b2 = __ballot_sync(0xFFFFFFFFu, m & 4u), b3 = __ballot_sync(0xFFFFFFFFu, m & 8u);
-  int pre = __popc(b0 & lt) + __popc(b1 & lt) + __popc(b2 & lt) + __popc(b3 & lt);
-  if (lane == 0) cl.wcnt[warp] = __popc(b0) + __popc(b1) + __popc(b2) + __popc(b3);
+  int pre[kQ];
+#pragma unroll
+  for (int q = 0; q < kQ; ++q) {
+    const u32 b0 = __ballot_sync(0xFFFFFFFFu, m[q] & 1u), b1 = __ballot_sync(0xFFFFFFFFu, m[q] & 2u);
+    const u32 b2 = __ballot_sync(0xFFFFFFFFu, m[q] & 4u), b3 = __ballot_sync(0xFFFFFFFFu, m[q] & 8u);
+    pre[q] = __popc(b0 & lt) + __popc(b1 & lt) + __popc(b2 & lt) + __popc(b3 & lt);
+    if (lane == 0) cl.wcnt[q * kPWarps + warp] = __popc(b0) + __popc(b1) + __popc(b2) + __popc(b3);
+  }
   __syncthreads();
   int tot = 0;
 #pragma unroll
-  for (int k = 0; k < kPWarps; ++k) {
+  for (int k = 0; k < kRoundUnits; ++k) {
     const int c = cl.wcnt[k];
-    if (k < warp) pre += c;
+#pragma unroll
+    for (int q = 0; q < kQ; ++q)
+      if (k < q * kPWarps + warp) pre[q] += c;
     tot += c;
   }
 #pragma unroll
-  for (int j = 0; j < 4; ++j)
-    if (m & (1u << j)) cl.list[pre++] = (unsigned short)((warp << 7) | (4 * lane + j));
+  for (int q = 0; q < kQ; ++q)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (m[q] & (1u << j)) cl.list[pre[q]++] = (unsigned short)(((q * kPWarps + warp) << 7) | (4 * lane + j));
   __syncthreads();
   return tot;
 }
@@ -101,14 +119,18 @@ __device__ __forceinline__ u32 live_mask(int4 a) {
   return (u32)(a.x != 0) | ((u32)(a.y != 0) << 1) | ((u32)(a.z != 0) << 2) | ((u32)(a.w != 0) << 3);
 }
 
-// unit of warp k in pass p of this CTA: units are dealt round-robin over the
-// CTAs (unit i -> CTA i mod G), so the crowded low slots spread over all SMs
-__device__ __forceinline__ int unit_of(int k, int pass) {
-  return (int)blockIdx.x + (int)gridDim.x * (k + kPWarps * pass);
+// unit at place v of round r of this CTA: units are dealt round-robin over
+// the CTAs (unit i -> CTA i mod G), so the crowded low slots spread over all SMs
+__device__ __forceinline__ int unit_at(int v, int round) {
+  return (int)blockIdx.x + (int)gridDim.x * (v + kRoundUnits * round);
+}
+
+__device__ __forceinline__ int slot_of(u32 entry, int round) {
+  return (unit_at((int)(entry >> 7), round) << 7) + (int)(entry & 127u);
 }
 
 template <int S>
-__device__ __forceinline__ void move_one(const WorldDev& w, int t, int slot, int4 ag, int L, int metab) {
+__device__ __forceinline__ int4 move_one(const WorldDev& w, int t, int slot, int4 ag, int L, int metab) {
   const SpeciesDev& sp = w.sp[S];
   if (S == 0) w.victim[ag.x] = kNoKey;  // last step's victim entry for this cell
   const u32 dir = draw(w.seed, w.model, (u32)t, (u32)slot, ABM_P_MOVE, (u32)S) >> 29;
@@ -124,35 +146,56 @@ __device__ __forceinline__ void move_one(const WorldDev& w, int t, int slot, int
     if (w.victim[cell] != kNoKey)
       atomicMin(&w.wclaim[cell], claim_key(draw(w.seed, w.model, (u32)t, (u32)slot, ABM_P_PRIO, 1u), slot));
   }
+  return ag;
 }
 
 // phase 1/4: move every live agent; claims for the cell's grass (sheep) or
 // the cell's victim (wolves)
+// A world whose units fit in one round leaves the round's list, live words and
+// moved records in shared memory; `carried` = the list's length (-1 if not).
 template <int S>
-__device__ __forceinline__ void p_move(const WorldDev& w, int t, int ext, const CtaList& cl) {
+__device__ __forceinline__ void p_move(const WorldDev& w, int t, int ext, const CtaList& cl, int& carried) {
+  carried = -1;
   const SpeciesDev& sp = w.sp[S];
   const int L = w.side;
   const int metab = w.params[PRM_SHEEP_METAB + S];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nblk = (ext + 127) >> 7;
-  for (int pass = 0; unit_of(0, pass) < nblk; ++pass) {
-    const int i = unit_of(warp, pass);
-    const int base = (i << 7) + 4 * lane;
-    int4 act = make_int4(0, 0, 0, 0);
-    if (i < nblk && base < ext) act = reinterpret_cast<const int4*>(sp.active)[base >> 2];
-    const int tot = cta_list_live(live_mask(act), cl);
+  for (int round = 0; unit_at(0, round) < nblk; ++round) {
+    u32 m[kQ];
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+      const int i = unit_at(q * kPWarps + warp, round);
+      const int base = (i << 7) + 4 * lane;
+      int4 act = make_int4(0, 0, 0, 0);
+      if (i < nblk && base < ext) act = reinterpret_cast<const int4*>(sp.active)[base >> 2];
+      m[q] = live_mask(act);
+    }
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {  // live words of the round's units, for the count phase
+      u32 vm = m[q] << (4 * (lane & 7));
+#pragma unroll
+      for (int o = 1; o < 8; o <<= 1) vm |= __shfl_xor_sync(0xFFFFFFFFu, vm, o);
+      if ((lane & 7) == 0) cl.live[4 * (q * kPWarps + warp) + (lane >> 3)] = vm;
+    }
+    const int tot = cta_list_live(m, cl);
     for (int e = threadIdx.x; e < tot; e += 2 * kPT) {
-      const u32 ea = cl.list[e];
-      const int eb = e + kPT < tot ? (int)cl.list[e + kPT] : -1;
-      const int sa = (unit_of((int)(ea >> 7), pass) << 7) + (int)(ea & 127u);
-      const int sb = eb >= 0 ? (unit_of(eb >> 7, pass) << 7) + (eb & 127) : -1;
+      const int sa = slot_of(cl.list[e], round);
+      const int sb = e + kPT < tot ? slot_of(cl.list[e + kPT], round) : -1;
       const int4 aa = sp.agent[sa];
       int4 ab = make_int4(0, 0, 0, 0);
       if (sb >= 0) ab = sp.agent[sb];
-      move_one<S>(w, t, sa, aa, L, metab);
-      if (sb >= 0) move_one<S>(w, t, sb, ab, L, metab);
+      const int4 ma = move_one<S>(w, t, sa, aa, L, metab);
+      cl.cell[e] = ma.x;
+      cl.energy[e] = ma.y;
+      if (sb >= 0) {
+        const int4 mb = move_one<S>(w, t, sb, ab, L, metab);
+        cl.cell[e + kPT] = mb.x;
+        cl.energy[e + kPT] = mb.y;
+      }
     }
-    __syncthreads();  // the list is rewritten by the next pass
+    carried = tot;
+    __syncthreads();  // the list is rewritten by the next round
   }
 }
 
@@ -197,7 +240,8 @@ __device__ __forceinline__ u32 count_one(const WorldDev& w, int t, int slot, int
 // segments of the rank phase).
 template <int S>
 __device__ __forceinline__ void p_count(const WorldDev& w, int t, int ext, int kseg, int* acc, const CtaList& cl,
-                                        u32* s_upar /* [kPWarps][4], zero on entry and exit */) {
+                                        int carried, u32* s_upar /* [kRoundUnits][4], zero on entry and exit */,
+                                        int* s_acc /* [2 * kPWarps] */) {
   const SpeciesDev& sp = w.sp[S];
   const PersistDev& ps = w.ps;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -207,23 +251,39 @@ __device__ __forceinline__ void p_count(const WorldDev& w, int t, int ext, int k
   const int regrowth = w.params[PRM_REGROWTH];
   const u64* claim = S == 0 ? w.gclaim : w.wclaim;
   int starved = 0, won = 0;
-  for (int pass = 0; unit_of(0, pass) < nblk; ++pass) {
-    const int i = unit_of(warp, pass);
-    const int base = (i << 7) + 4 * lane;
-    int4 act = make_int4(0, 0, 0, 0);
-    if (i < nblk && base < ext) act = reinterpret_cast<const int4*>(sp.active)[base >> 2];
-    const u32 m = live_mask(act);
-    const u32 valid = (i >= nblk || base >= ext) ? 0u : (ext - base >= 4 ? 0xFu : (1u << (ext - base)) - 1u);
-    const u32 fr = ~m & valid;
-    const int tot = cta_list_live(m, cl);
+  // one round and the move phase's list still in shared memory: neither the
+  // live flags nor the agent records need reading again
+  const bool reuse = carried >= 0 && unit_at(0, 1) >= nblk;
+  for (int round = 0; unit_at(0, round) < nblk; ++round) {
+    u32 m[kQ], fr[kQ];
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+      const int i = unit_at(q * kPWarps + warp, round);
+      const int base = (i << 7) + 4 * lane;
+      if (reuse) {
+        m[q] = (cl.live[4 * (q * kPWarps + warp) + (lane >> 3)] >> (4 * (lane & 7))) & 0xFu;
+      } else {
+        int4 act = make_int4(0, 0, 0, 0);
+        if (i < nblk && base < ext) act = reinterpret_cast<const int4*>(sp.active)[base >> 2];
+        m[q] = live_mask(act);
+      }
+      const u32 valid = (i >= nblk || base >= ext) ? 0u : (ext - base >= 4 ? 0xFu : (1u << (ext - base)) - 1u);
+      fr[q] = ~m[q] & valid;
+    }
+    const int tot = reuse ? carried : cta_list_live(m, cl);
     for (int e = threadIdx.x; e < tot; e += 2 * kPT) {
       const u32 ea = cl.list[e];
       const int eb = e + kPT < tot ? (int)cl.list[e + kPT] : -1;
-      const int sa = (unit_of((int)(ea >> 7), pass) << 7) + (int)(ea & 127u);
-      const int sb = eb >= 0 ? (unit_of(eb >> 7, pass) << 7) + (eb & 127) : -1;
-      const int4 aa = sp.agent[sa];
-      int4 ab = make_int4(0, 0, 0, 0);
-      if (sb >= 0) ab = sp.agent[sb];
+      const int sa = slot_of(ea, round);
+      const int sb = eb >= 0 ? slot_of((u32)eb, round) : -1;
+      int4 aa, ab = make_int4(0, 0, 0, 0);
+      if (reuse) {
+        aa = make_int4(cl.cell[e], cl.energy[e], 0, 0);
+        if (sb >= 0) ab = make_int4(cl.cell[e + kPT], cl.energy[e + kPT], 0, 0);
+      } else {
+        aa = sp.agent[sa];
+        if (sb >= 0) ab = sp.agent[sb];
+      }
       const u64 ca = claim[aa.x];
       const u64 cb = sb >= 0 ? claim[ab.x] : kNoKey;
       u32 r = count_one<S>(w, t, sa, aa, ca, gain, Tr, regrowth);
@@ -238,39 +298,56 @@ __device__ __forceinline__ void p_count(const WorldDev& w, int t, int ext, int k
       }
     }
     __syncthreads();
-    if (i < nblk) {
-      const u32 pw = s_upar[4 * warp + (lane >> 3)];
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+      const int v = q * kPWarps + warp;
+      const int i = unit_at(v, round);
+      if (i >= nblk) continue;
+      const int base = (i << 7) + 4 * lane;
+      const u32 pw = s_upar[4 * v + (lane >> 3)];
       const u32 par = (pw >> (4 * (lane & 7))) & 0xFu;
       // 8 lanes x 4 bits -> one plane word
-      u32 vf = fr << (4 * (lane & 7));
+      u32 vf = fr[q] << (4 * (lane & 7));
 #pragma unroll
       for (int o = 1; o < 8; o <<= 1) vf |= __shfl_xor_sync(0xFFFFFFFFu, vf, o);
       if ((lane & 7) == 0 && base < ext) {
         ps.plane[S][0][base >> 5] = vf;
         ps.plane[S][1][base >> 5] = pw;
       }
-      u32 cu = ((u32)__popc(fr) << 16) | (u32)__popc(par);
+      u32 cu = ((u32)__popc(fr[q]) << 16) | (u32)__popc(par);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) cu += __shfl_xor_sync(0xFFFFFFFFu, cu, o);
       if (lane == 0) {
-        const u64 v = ((u64)(cu >> 16) << 32) | (cu & 0xFFFFu);
-        ps.blk[S][i] = v;
-        atomicAdd(reinterpret_cast<unsigned long long*>(&ps.seg[S][i / kseg]), (unsigned long long)v);
+        const u64 val = ((u64)(cu >> 16) << 32) | (cu & 0xFFFFu);
+        ps.blk[S][i] = val;
+        atomicAdd(reinterpret_cast<unsigned long long*>(&ps.seg[S][i / kseg]), (unsigned long long)val);
       }
       __syncwarp();
-      if (lane < 4) s_upar[4 * warp + lane] = 0u;
+      if (lane < 4) s_upar[4 * v + lane] = 0u;
     }
-    __syncthreads();  // the list and the unit words are rewritten by the next pass
+    __syncthreads();  // the list and the unit words are rewritten by the next round
   }
-  // accumulators (warp-aggregated)
+  // accumulators: summed over the CTA first, so that the two counters see one
+  // atomic per CTA, not one per warp (same-address atomics serialise in L2)
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     starved += __shfl_xor_sync(0xFFFFFFFFu, starved, o);
     won += __shfl_xor_sync(0xFFFFFFFFu, won, o);
   }
   if (lane == 0) {
-    if (starved) atomicAdd(&acc[S], starved);
-    if (won) atomicAdd(&acc[S == 0 ? 3 : 2], won);
+    s_acc[2 * warp] = starved;
+    s_acc[2 * warp + 1] = won;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int a = 0, b = 0;
+#pragma unroll
+    for (int k = 0; k < kPWarps; ++k) {
+      a += s_acc[2 * k];
+      b += s_acc[2 * k + 1];
+    }
+    if (a) atomicAdd(&acc[S], a);
+    if (b) atomicAdd(&acc[S == 0 ? 3 : 2], b);
   }
 }
 
@@ -414,11 +491,16 @@ __global__ void __launch_bounds__(kPT, MINB) k_persistent(WorldDev w, int nsteps
                                                      unsigned long long* phase_ns) {
   __shared__ u64 s_red[2 * kPWarps];
   __shared__ u64 s_pre[kPT];
-  __shared__ unsigned short s_clist[kPWarps * 128];
-  __shared__ int s_wcnt[kPWarps];
-  __shared__ u32 s_upar[kPWarps * 4];
-  const CtaList cl{s_clist, s_wcnt};
-  if (threadIdx.x < kPWarps * 4) s_upar[threadIdx.x] = 0u;
+  __shared__ unsigned short s_clist[kRoundUnits * 128];
+  __shared__ int s_wcnt[kRoundUnits];
+  __shared__ u32 s_upar[kRoundUnits * 4];
+  __shared__ int s_acc[2 * kPWarps];
+  __shared__ u32 s_live[kRoundUnits * 4];
+  __shared__ int s_cell[kRoundUnits * 128];
+  __shared__ int s_energy[kRoundUnits * 128];
+  const CtaList cl{s_clist, s_wcnt, s_live, s_cell, s_energy};
+  int carried = -1;
+  if (threadIdx.x < kRoundUnits * 4) s_upar[threadIdx.x] = 0u;
   PhaseClock clk{phase_ns, 0};
   clk.start();
   u32 bar_target = w.bar_base;  // arrival count that completes the next barrier
@@ -442,7 +524,7 @@ __global__ void __launch_bounds__(kPT, MINB) k_persistent(WorldDev w, int nsteps
     if (blockIdx.x == 0 && threadIdx.x == 0) acc[0] = acc[1] = acc[2] = acc[3] = 0;  // unused since step t-2
     if (blockIdx.x == 0)  // wolf segment sums: last read in phase 6 of the previous step
       for (int j = threadIdx.x; j < (int)gridDim.x; j += kPT) ps.seg[1][j] = 0ull;
-    p_move<0>(w, t, ext[0], cl);
+    p_move<0>(w, t, ext[0], cl, carried);
     if (blockIdx.x == 0 && threadIdx.x == 0 && st) {
       st->n_start[0] = nstart0;
       st->n_start[1] = nstart1;
@@ -454,7 +536,7 @@ __global__ void __launch_bounds__(kPT, MINB) k_persistent(WorldDev w, int nsteps
     if (*(volatile int*)w.err) return;
     // ---- phase 2: sheep eat / select / die / flags
     const int kseg0 = (((ext[0] + 127) >> 7) + (int)gridDim.x - 1) / (int)gridDim.x;
-    p_count<0>(w, t, ext[0], kseg0, acc, cl, s_upar);
+    p_count<0>(w, t, ext[0], kseg0, acc, cl, carried, s_upar, s_acc);
     grid_sync(ps.bar, w.err, bar_target);
     clk.lap(1);
     // ---- phase 3: sheep ranks and lists; sheep counters
@@ -471,7 +553,7 @@ __global__ void __launch_bounds__(kPT, MINB) k_persistent(WorldDev w, int nsteps
     p_births<0>(w, t, sb.r, sb.F, sb.ext, sb.id0);
     if (blockIdx.x == 0)  // sheep segment sums: last read in phase 3
       for (int j = threadIdx.x; j < (int)gridDim.x; j += kPT) ps.seg[0][j] = 0ull;
-    p_move<1>(w, t, ext[1], cl);
+    p_move<1>(w, t, ext[1], cl, carried);
     const int starved0 = acc[0], grass = acc[3];
     {
       const int n_after = nstart0 + r0;
@@ -485,7 +567,7 @@ __global__ void __launch_bounds__(kPT, MINB) k_persistent(WorldDev w, int nsteps
     clk.lap(3);
     // ---- phase 5: wolves eat / kill / select / die / flags
     const int kseg1 = (((ext[1] + 127) >> 7) + (int)gridDim.x - 1) / (int)gridDim.x;
-    p_count<1>(w, t, ext[1], kseg1, acc, cl, s_upar);
+    p_count<1>(w, t, ext[1], kseg1, acc, cl, carried, s_upar, s_acc);
     grid_sync(ps.bar, w.err, bar_target);
     clk.lap(4);
     // ---- phase 6: wolf ranks and lists; counters; statistics
