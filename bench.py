@@ -445,7 +445,7 @@ def run_ours(args, rank, world, local):
                 "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": persistent_traffic(K, W, tw["ctas_per_sm"])
                 if tw["engine"] == abm.ENGINE_PERSISTENT else None,
                 "launch_ms": ms_total, "algorithmic_bytes_per_launch": step_bytes,
-                "note": "latency-bound: dependent random cell accesses and 6 grid barriers per step"}
+                "note": "latency-bound: dependent random cell accesses and 5 grid barriers per step"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": t_max / max(K, 1), "higher_is_better": True, "scaling": "weak",
@@ -457,8 +457,8 @@ def run_ours(args, rank, world, local):
                                             x["ctas_per_sm"], round(x["ms"], 3)] for x in tw.get("trials", [])]),
             "roofline": roofline, "gpu_launches": 1 if tw["engine"] == abm.ENGINE_PERSISTENT else 6 * K,
             "phases_us_per_step": {n: 1e3 * phase[i] / max(K, 1) for i, n in enumerate(
-                ("A_prev_wolf_births_sheep_move", "B_sheep_eat_select_flags", "C_sheep_ranks", "D_sheep_births_wolf_move",
-                 "E_wolf_eat_select_flags", "F_wolf_ranks"))},
+                ("P1_prev_wolf_ranks_sheep_move", "P2_prev_wolf_births_sheep_eat_select", "P3_sheep_ranks_wolf_move",
+                 "P4_sheep_births", "P5_wolf_eat_select", "closing_wolf_ranks"))},
             "end_counters": gw.counters()}
 
     if rank == 0 and not args.no_extras:

@@ -290,9 +290,10 @@ abm_status abm_step_graph(abm_world* w, int32_t nsteps, int32_t reps, abm_step_s
  * events between the launches, [0] sheep move, [1] sheep eat/select/compact,
  * [2] sheep births, [3] wolf move, [4] wolf eat/select/compact, [5] wolf
  * births. Persistent engine: block 0's global-timer laps between the grid
- * barriers, [0] sheep move (+ previous wolf births), [1] sheep
- * eat/select/flags, [2] sheep ranks, [3] sheep births + wolf move, [4] wolf
- * eat/select/flags, [5] wolf ranks. Both: [7] whole call by events, [6] = 0.
+ * barriers, [0] previous step's wolf ranks + sheep move, [1] previous step's
+ * wolf births + sheep eat/select/flags, [2] sheep ranks + wolf move, [3]
+ * sheep births, [4] wolf eat/select/flags, [5] the last step's wolf ranks
+ * (once per call). Both: [7] whole call by events, [6] = 0.
  * Synchronises `stream`. */
 abm_status abm_step_profiled(abm_world* w, int32_t nsteps, abm_step_stats* stats, float* phase_ms,
                              void* stream);

@@ -2,18 +2,16 @@
 // all phases of many steps in one cooperative launch, separated by a bounded
 // grid barrier instead of kernel boundaries.
 //
-// Per step, six barrier-separated phases:
-//   1. sheep move + grass claims            (and the previous step's wolf births)
-//   2. sheep eat / select / die, flags into bit-planes, per-warp and per-CTA counts
-//   3. sheep ranks -> parent list and the first P free slots (P = parents)
-//   4. sheep births, wolves move + victim claims
-//   5. wolves eat / select / die, flags, counts
-//   6. wolves ranks -> lists; counters and statistics of the step
-//   (7. wolf births run together with phase 1 of the next step)
-// Phases 1/2 and 4/5 deal 128-slot units to warps round-robin over the CTAs
-// (the live agents crowd the low slots); phases 3/6 give CTA b a contiguous
-// run of units, so a rank is a prefix over per-run sums, a block scan of the
-// unit counts and a warp scan: no look-back chains.
+// Per step, five barrier-separated phases (each species: move + claims;
+// eat / select / die with flags into bit-planes and per-unit counts; ranks ->
+// parent list and the first P free slots (P = parents); births), with the
+// wolves' ranks and births shifted so that they overlap sheep work (the
+// schedule is spelled out in k_persistent).
+// Move and count phases deal 128-slot units to warps round-robin over the
+// CTAs (the live agents crowd the low slots) and list the live agents of a
+// CTA's units in shared memory for all its threads; the rank phases give CTA
+// b a contiguous run of units, so a rank is a prefix over per-run sums, a
+// block scan of the unit counts and a warp scan: no look-back chains.
 // Every thread keeps the world counters in registers and updates them from
 // the same totals, so no counter needs a broadcast.
 #include <algorithm>
@@ -25,7 +23,7 @@ namespace abm {
 constexpr int kPT = 512;                  // threads per CTA
 constexpr int kPWarps = kPT / 32;
 constexpr int kBarSpin = 1 << 24;
-constexpr int kPhases = 6;                // grid barriers per step         // bounded barrier wait (~2 s with the back-off)
+constexpr int kPhases = 5;                // grid barriers per step (plus one closing a launch)         // bounded barrier wait (~2 s with the back-off)
 
 // Grid barrier (all CTAs co-resident: cooperative launch) over a monotonic
 // arrival counter: the k-th barrier of a launch is passed once the counter
@@ -515,15 +513,59 @@ __global__ void __launch_bounds__(kPT, MINB) k_persistent(WorldDev w, int nsteps
   int ovf[2] = {c->overflow[0], c->overflow[1]};
   const int cap[2] = {w.sp[0].cap, w.sp[1].cap};
   Births wb = {0, 0, 0, 0};  // wolf births pending from the previous step
+  // Wolf ranks of step t-1 run beside the sheep moves of step t, and the wolf
+  // moves of step t beside the sheep ranks: neither needs the other's
+  // results, so a step takes five barrier-separated phases:
+  //   P1  wolf ranks (t-1), wolf counters and statistics | sheep move (t)
+  //   P2  wolf births (t-1) | sheep eat / select / die (t)
+  //   P3  sheep ranks (t) | wolves move + victim claims (t) (a wolf only
+  //       needs a live sheep on its cell: the survivors registered in P2)
+  //   P4  sheep births (t) (lambs register as victims before wolves eat)
+  //   P5  wolves eat / kill / select / die (t)
+  // and the last step's wolf ranks and births close the launch.
+  int kseg1 = 0, nstart1 = 0, r0p = 0, P0p = 0, starved0p = 0, grassp = 0;  // of the previous step
+  abm_step_stats* stp = nullptr;
+  auto wolf_ranks = [&](int tw /* step whose wolves are ranked */) {
+    int* accw = ps.acc + 4 * (tw & 1);
+    u32 F1, P1, preF1, preP1;
+    grand_totals<1>(ps, F1, P1, preF1, preP1, s_red);
+    p_ranks<1>(w, ext[1], kseg1, P1, preF1, preP1, s_red, s_pre);
+    const int starved1 = accw[1], eaten = accw[2];
+    const int avail1 = (int)F1 + (cap[1] - ext[1]);
+    const int r1 = min((int)P1, avail1);
+    wb = {r1, (int)F1, ext[1], nid[1]};
+    const int n_after = nstart1 + r1;
+    if (n_after > hw[1]) hw[1] = n_after;
+    nact[1] = n_after - starved1;
+    nid[1] += r1;
+    if (r1 > (int)F1) ext[1] += r1 - (int)F1;
+    if ((int)P1 > avail1) ovf[1] = 1;
+    nact[0] -= eaten;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && stp) {
+      stp->parents[0] = P0p;
+      stp->parents[1] = (int)P1;
+      stp->births[0] = r0p;
+      stp->births[1] = r1;
+      stp->starved[0] = starved0p;
+      stp->starved[1] = starved1;
+      stp->eaten = eaten;
+      stp->grass_eaten = grassp;
+      for (int s2 = 0; s2 < 2; ++s2) {
+        stp->n_end[s2] = nact[s2];
+        stp->hw[s2] = hw[s2];
+        stp->overflow[s2] = ovf[s2];
+      }
+      stp->step = tw;
+    }
+  };
   for (int it = 0; it < nsteps; ++it) {
     int* acc = ps.acc + 4 * (t & 1);
     abm_step_stats* st = stats ? stats + it : nullptr;
-    const int nstart0 = nact[0], nstart1 = nact[1];
-    // ---- phase 1: sheep move (+ wolf births of the previous step)
-    if (it > 0) p_births<1>(w, t - 1, wb.r, wb.F, wb.ext, wb.id0);
-    if (blockIdx.x == 0 && threadIdx.x == 0) acc[0] = acc[1] = acc[2] = acc[3] = 0;  // unused since step t-2
-    if (blockIdx.x == 0)  // wolf segment sums: last read in phase 6 of the previous step
-      for (int j = threadIdx.x; j < (int)gridDim.x; j += kPT) ps.seg[1][j] = 0ull;
+    // ---- P1: wolf ranks of the previous step | sheep move
+    if (it > 0) wolf_ranks(t - 1);
+    if (blockIdx.x == 0 && threadIdx.x == 0) acc[0] = acc[1] = acc[2] = acc[3] = 0;  // last read in P1 of step t-1
+    const int nstart0 = nact[0];
+    nstart1 = nact[1];
     p_move<0>(w, t, ext[0], cl, carried);
     if (blockIdx.x == 0 && threadIdx.x == 0 && st) {
       st->n_start[0] = nstart0;
@@ -534,81 +576,59 @@ __global__ void __launch_bounds__(kPT, MINB) k_persistent(WorldDev w, int nsteps
     grid_sync(ps.bar, w.err, bar_target);
     clk.lap(0);
     if (*(volatile int*)w.err) return;
-    // ---- phase 2: sheep eat / select / die / flags
+    // ---- P2: wolf births of the previous step | sheep eat / select / die / flags
+    if (it > 0) p_births<1>(w, t - 1, wb.r, wb.F, wb.ext, wb.id0);
+    if (blockIdx.x == 0)  // wolf segment sums: last read in P1
+      for (int j = threadIdx.x; j < (int)gridDim.x; j += kPT) ps.seg[1][j] = 0ull;
     const int kseg0 = (((ext[0] + 127) >> 7) + (int)gridDim.x - 1) / (int)gridDim.x;
     p_count<0>(w, t, ext[0], kseg0, acc, cl, carried, s_upar, s_acc);
     grid_sync(ps.bar, w.err, bar_target);
     clk.lap(1);
-    // ---- phase 3: sheep ranks and lists; sheep counters
+    // ---- P3: sheep ranks and lists | wolves move + claims
     u32 F0, P0, preF, preP;
     grand_totals<0>(ps, F0, P0, preF, preP, s_red);
     p_ranks<0>(w, ext[0], kseg0, P0, preF, preP, s_red, s_pre);
     const int avail0 = (int)F0 + (cap[0] - ext[0]);
     const int r0 = min((int)P0, avail0);
     const Births sb = {r0, (int)F0, ext[0], nid[0]};
+    p_move<1>(w, t, ext[1], cl, carried);
     grid_sync(ps.bar, w.err, bar_target);
     clk.lap(2);
-    // ---- phase 4: sheep births, wolves move + claims (a wolf only needs a live
-    // sheep on its cell; every newborn lamb sits with its live parent)
+    // ---- P4: sheep births; sheep counters
     p_births<0>(w, t, sb.r, sb.F, sb.ext, sb.id0);
-    if (blockIdx.x == 0)  // sheep segment sums: last read in phase 3
+    if (blockIdx.x == 0)  // sheep segment sums: last read in P3
       for (int j = threadIdx.x; j < (int)gridDim.x; j += kPT) ps.seg[0][j] = 0ull;
-    p_move<1>(w, t, ext[1], cl, carried);
-    const int starved0 = acc[0], grass = acc[3];
+    starved0p = acc[0];
+    grassp = acc[3];
     {
       const int n_after = nstart0 + r0;
       if (n_after > hw[0]) hw[0] = n_after;
-      nact[0] = n_after - starved0;
+      nact[0] = n_after - starved0p;
       nid[0] += r0;
       if (r0 > (int)F0) ext[0] += r0 - (int)F0;
       if ((int)P0 > avail0) ovf[0] = 1;
     }
+    r0p = r0;
+    P0p = (int)P0;
     grid_sync(ps.bar, w.err, bar_target);
     clk.lap(3);
-    // ---- phase 5: wolves eat / kill / select / die / flags
-    const int kseg1 = (((ext[1] + 127) >> 7) + (int)gridDim.x - 1) / (int)gridDim.x;
+    // ---- P5: wolves eat / kill / select / die / flags
+    kseg1 = (((ext[1] + 127) >> 7) + (int)gridDim.x - 1) / (int)gridDim.x;
     p_count<1>(w, t, ext[1], kseg1, acc, cl, carried, s_upar, s_acc);
-    grid_sync(ps.bar, w.err, bar_target);
-    clk.lap(4);
-    // ---- phase 6: wolf ranks and lists; counters; statistics
-    u32 F1, P1, preF1, preP1;
-    grand_totals<1>(ps, F1, P1, preF1, preP1, s_red);
-    p_ranks<1>(w, ext[1], kseg1, P1, preF1, preP1, s_red, s_pre);
-    const int starved1 = acc[1], eaten = acc[2];
-    const int avail1 = (int)F1 + (cap[1] - ext[1]);
-    const int r1 = min((int)P1, avail1);
-    wb = {r1, (int)F1, ext[1], nid[1]};
-    {
-      const int n_after = nstart1 + r1;
-      if (n_after > hw[1]) hw[1] = n_after;
-      nact[1] = n_after - starved1;
-      nid[1] += r1;
-      if (r1 > (int)F1) ext[1] += r1 - (int)F1;
-      if ((int)P1 > avail1) ovf[1] = 1;
-      nact[0] -= eaten;
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0 && st) {
-      st->parents[0] = (int)P0;
-      st->parents[1] = (int)P1;
-      st->births[0] = r0;
-      st->births[1] = r1;
-      st->starved[0] = starved0;
-      st->starved[1] = starved1;
-      st->eaten = eaten;
-      st->grass_eaten = grass;
-      for (int s = 0; s < 2; ++s) {
-        st->n_end[s] = nact[s];
-        st->hw[s] = hw[s];
-        st->overflow[s] = ovf[s];
-      }
-      st->step = t;
-    }
+    stp = st;
     ++t;
     grid_sync(ps.bar, w.err, bar_target);
-    clk.lap(5);
+    clk.lap(4);
   }
-  // the last step's wolf births
-  if (nsteps > 0) p_births<1>(w, t - 1, wb.r, wb.F, wb.ext, wb.id0);
+  // the last step's wolf ranks and births
+  if (nsteps > 0) {
+    wolf_ranks(t - 1);
+    grid_sync(ps.bar, w.err, bar_target);
+    clk.lap(5);
+    p_births<1>(w, t - 1, wb.r, wb.F, wb.ext, wb.id0);
+    if (blockIdx.x == 0)  // wolf segment sums, for the next launch
+      for (int j = threadIdx.x; j < (int)gridDim.x; j += kPT) ps.seg[1][j] = 0ull;
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     c->step = t;
     for (int s = 0; s < 2; ++s) {
@@ -646,7 +666,8 @@ abm_status launch_persistent(const WorldDev& d, u32* bar_next, int grid, int nst
   // one CTA per SM: the variant with the larger register budget
   const void* fn = grid <= num_sms() ? (const void*)k_persistent<1> : (const void*)k_persistent<2>;
   ABM_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), dim3(kPT), args, 0, st));
-  *bar_next += (u32)kPhases * (u32)nsteps * (u32)grid;  // arrivals this launch adds to the counter
+  // arrivals this launch adds to the counter
+  if (nsteps > 0) *bar_next += ((u32)kPhases * (u32)nsteps + 1u) * (u32)grid;
   return ABM_OK;
 }
 

@@ -207,6 +207,45 @@ def test_large_config_engines_agree_over_300_steps(eng):
     a.check()
 
 
+def test_large_config_one_cta_per_sm_multi_round(eng):
+    """The persistent engine at one CTA per SM (the 128-register variant):
+    the sheep extent then spans more than one round of units per CTA, so the
+    move and count phases take the multi-round path. 150 steps, whole state,
+    against the per-phase kernel engine."""
+    c = workloads.PRED_LARGE
+    a, _ = make(eng, c, engine=0)
+    a.tune(0, 1)
+    b, _ = make(eng, c, engine=1)
+    sa, sb = a.new_stats(150), b.new_stats(150)
+    for i in range(3):  # several launches: the barrier counter carries over
+        a.step(50, sa[i * 50:(i + 1) * 50])
+    b.step(150, sb)
+    torch.cuda.synchronize()
+    for x, y in zip(eng.decode_stats(sa), eng.decode_stats(sb)):
+        for k in ("n_start", "parents", "births", "starved", "eaten", "grass_eaten", "n_end", "hw", "overflow"):
+            assert x[k] == y[k], (k, x["step"])
+    for s in range(2):
+        for f in FIELDS:
+            assert torch.equal(a.agents(s, f), b.agents(s, f)), (s, f)
+    assert torch.equal(a.grass("wait"), b.grass("wait"))
+    assert a.counters() == b.counters()
+    a.check()
+
+
+def test_engine_switches_mid_run(eng):
+    """Steps alternate between the engines and launch shapes on one world;
+    the result equals the oracle's."""
+    c = workloads.PRED_SMALL
+    gw, ow = make(eng, c)
+    plan = [(0, 2, 7), (1, 1, 5), (0, 1, 9), (0, 2, 1), (1, 1, 3), (0, 2, 25)]
+    for engine, cps, n in plan:
+        gw.tune(engine, cps)
+        gw.step(n)
+    ow.step(sum(n for _, _, n in plan))
+    compare_state(gw, ow, "switches")
+    gw.check()
+
+
 @pytest.mark.slow
 def test_large_config_full_run(eng):
     """The full 1000-step large run: populations every step, full state at the end."""
