@@ -151,8 +151,25 @@ __device__ __forceinline__ int4 move_one(const WorldDev& w, int t, int slot, int
 // the cell's victim (wolves)
 // A world whose units fit in one round leaves the round's list, live words and
 // moved records in shared memory; `carried` = the list's length (-1 if not).
+// live masks of this thread's slots in round `round` of the unit dealing
 template <int S>
-__device__ __forceinline__ void p_move(const WorldDev& w, int t, int ext, const CtaList& cl, int& carried) {
+__device__ __forceinline__ void round_flags(const WorldDev& w, int ext, int round, u32 (&m)[kQ]) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nblk = (ext + 127) >> 7;
+#pragma unroll
+  for (int q = 0; q < kQ; ++q) {
+    const int i = unit_at(q * kPWarps + warp, round);
+    const int base = (i << 7) + 4 * lane;
+    int4 act = make_int4(0, 0, 0, 0);
+    if (i < nblk && base < ext) act = reinterpret_cast<const int4*>(w.sp[S].active)[base >> 2];
+    m[q] = live_mask(act);
+  }
+}
+
+// m0 = round_flags(round 0), loaded by the caller ahead of other work
+template <int S>
+__device__ __forceinline__ void p_move(const WorldDev& w, int t, int ext, const CtaList& cl, int& carried,
+                                       const u32 (&m0)[kQ]) {
   carried = -1;
   const SpeciesDev& sp = w.sp[S];
   const int L = w.side;
@@ -161,13 +178,11 @@ __device__ __forceinline__ void p_move(const WorldDev& w, int t, int ext, const 
   const int nblk = (ext + 127) >> 7;
   for (int round = 0; unit_at(0, round) < nblk; ++round) {
     u32 m[kQ];
+    if (round == 0) {
 #pragma unroll
-    for (int q = 0; q < kQ; ++q) {
-      const int i = unit_at(q * kPWarps + warp, round);
-      const int base = (i << 7) + 4 * lane;
-      int4 act = make_int4(0, 0, 0, 0);
-      if (i < nblk && base < ext) act = reinterpret_cast<const int4*>(sp.active)[base >> 2];
-      m[q] = live_mask(act);
+      for (int q = 0; q < kQ; ++q) m[q] = m0[q];
+    } else {
+      round_flags<S>(w, ext, round, m);
     }
 #pragma unroll
     for (int q = 0; q < kQ; ++q) {  // live words of the round's units, for the count phase
@@ -439,6 +454,100 @@ __device__ __forceinline__ void p_ranks(const WorldDev& w, int ext, int kseg, u3
   }
 }
 
+// A rank phase (grand totals + ranks). When this CTA's run of units is short
+// (kseg <= kPWarps * kRankU, the common case) every load -- the segment sums,
+// the unit counts, the plane words -- is issued up front, so the phase costs
+// one memory round trip instead of three.
+constexpr int kRankU = 4;
+
+template <int S>
+__device__ __forceinline__ void rank_phase(const WorldDev& w, int ext, int kseg, u32& F, u32& P, u64* s_red,
+                                           u64* s_pre) {
+  const PersistDev& ps = w.ps;
+  if (kseg > kPWarps * kRankU || (int)gridDim.x > kPT) {
+    u32 preF, preP;
+    grand_totals<S>(ps, F, P, preF, preP, s_red);
+    p_ranks<S>(w, ext, kseg, P, preF, preP, s_red, s_pre);
+    return;
+  }
+  const SpeciesDev& sp = w.sp[S];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nblk = (ext + 127) >> 7;
+  const int j0 = blockIdx.x * kseg, j1 = min(nblk, j0 + kseg);
+  const int n = max(0, j1 - j0);
+  const u64 sv = threadIdx.x < (int)gridDim.x ? ps.seg[S][threadIdx.x] : 0ull;
+  const u64 bv = threadIdx.x < n ? ps.blk[S][j0 + threadIdx.x] : 0ull;
+  u32 wf[kRankU], wp[kRankU];
+#pragma unroll
+  for (int k = 0; k < kRankU; ++k) {
+    const int q = warp + kPWarps * k;
+    const int base = ((j0 + q) << 7) + 4 * lane;
+    wf[k] = 0u;
+    wp[k] = 0u;
+    if (q < n && base < ext) {
+      wf[k] = ps.plane[S][0][base >> 5];
+      wp[k] = ps.plane[S][1][base >> 5];
+    }
+  }
+  // grand totals and the sums of the segments before this CTA's
+  u64 tot = sv, pre = (int)threadIdx.x < (int)blockIdx.x ? sv : 0ull;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    tot += __shfl_xor_sync(0xFFFFFFFFu, tot, o);
+    pre += __shfl_xor_sync(0xFFFFFFFFu, pre, o);
+  }
+  __syncthreads();
+  if (lane == 0) {
+    s_red[2 * warp] = tot;
+    s_red[2 * warp + 1] = pre;
+  }
+  __syncthreads();
+  tot = pre = 0;
+  for (int i = 0; i < kPWarps; ++i) {
+    tot += s_red[2 * i];
+    pre += s_red[2 * i + 1];
+  }
+  F = (u32)(tot >> 32);
+  P = (u32)tot;
+  const u32 preF = (u32)(pre >> 32), preP = (u32)pre;
+  __syncthreads();  // s_red is reused by the scan
+  // unit prefixes inside the run
+  u32 exf, exp_, tf, tp;
+  block_scan2<kPT>((u32)(bv >> 32), (u32)bv, exf, exp_, tf, tp, s_red);
+  s_pre[threadIdx.x] = ((u64)(preF + exf) << 32) | (u64)(preP + exp_);
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kRankU; ++k) {
+    const int q = warp + kPWarps * k;
+    if (q >= n) break;
+    const u64 pr = s_pre[q];
+    const int base = ((j0 + q) << 7) + 4 * lane;
+    const int sh = 4 * (lane & 7);
+    u32 fr = base < ext ? (wf[k] >> sh) & 0xFu : 0u;
+    u32 par = base < ext ? (wp[k] >> sh) & 0xFu : 0u;
+    const u32 c = (u32)__popc(fr) | ((u32)__popc(par) << 16);
+    u32 inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const u32 x = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+      if (lane >= o) inc += x;
+    }
+    const u32 ex = inc - c;
+    u32 rf = (u32)(pr >> 32) + (ex & 0xFFFFu), rp = (u32)pr + (ex >> 16);
+    while (fr && rf < P) {  // only the first P free slots can receive a child
+      const int jj = __ffs(fr) - 1;
+      fr &= fr - 1;
+      sp.freel[rf++] = base + jj;
+    }
+    while (par) {
+      const int jj = __ffs(par) - 1;
+      par &= par - 1;
+      sp.parents[rp++] = base + jj;
+    }
+  }
+  __syncthreads();  // s_pre and s_red are reused
+}
+
 template <int S>
 __device__ __forceinline__ void p_births(const WorldDev& w, int t, int r, int F, int ext, int id0) {
   const SpeciesDev& sp = w.sp[S];
@@ -527,9 +636,8 @@ __global__ void __launch_bounds__(kPT, MINB) k_persistent(WorldDev w, int nsteps
   abm_step_stats* stp = nullptr;
   auto wolf_ranks = [&](int tw /* step whose wolves are ranked */) {
     int* accw = ps.acc + 4 * (tw & 1);
-    u32 F1, P1, preF1, preP1;
-    grand_totals<1>(ps, F1, P1, preF1, preP1, s_red);
-    p_ranks<1>(w, ext[1], kseg1, P1, preF1, preP1, s_red, s_pre);
+    u32 F1, P1;
+    rank_phase<1>(w, ext[1], kseg1, F1, P1, s_red, s_pre);
     const int starved1 = accw[1], eaten = accw[2];
     const int avail1 = (int)F1 + (cap[1] - ext[1]);
     const int r1 = min((int)P1, avail1);
@@ -562,11 +670,13 @@ __global__ void __launch_bounds__(kPT, MINB) k_persistent(WorldDev w, int nsteps
     int* acc = ps.acc + 4 * (t & 1);
     abm_step_stats* st = stats ? stats + it : nullptr;
     // ---- P1: wolf ranks of the previous step | sheep move
+    u32 mf[kQ];
+    round_flags<0>(w, ext[0], 0, mf);  // issued before the wolf ranks, used by the sheep move
     if (it > 0) wolf_ranks(t - 1);
     if (blockIdx.x == 0 && threadIdx.x == 0) acc[0] = acc[1] = acc[2] = acc[3] = 0;  // last read in P1 of step t-1
     const int nstart0 = nact[0];
     nstart1 = nact[1];
-    p_move<0>(w, t, ext[0], cl, carried);
+    p_move<0>(w, t, ext[0], cl, carried, mf);
     if (blockIdx.x == 0 && threadIdx.x == 0 && st) {
       st->n_start[0] = nstart0;
       st->n_start[1] = nstart1;
@@ -585,13 +695,13 @@ __global__ void __launch_bounds__(kPT, MINB) k_persistent(WorldDev w, int nsteps
     grid_sync(ps.bar, w.err, bar_target);
     clk.lap(1);
     // ---- P3: sheep ranks and lists | wolves move + claims
-    u32 F0, P0, preF, preP;
-    grand_totals<0>(ps, F0, P0, preF, preP, s_red);
-    p_ranks<0>(w, ext[0], kseg0, P0, preF, preP, s_red, s_pre);
+    round_flags<1>(w, ext[1], 0, mf);  // issued before the sheep ranks, used by the wolf move
+    u32 F0, P0;
+    rank_phase<0>(w, ext[0], kseg0, F0, P0, s_red, s_pre);
     const int avail0 = (int)F0 + (cap[0] - ext[0]);
     const int r0 = min((int)P0, avail0);
     const Births sb = {r0, (int)F0, ext[0], nid[0]};
-    p_move<1>(w, t, ext[1], cl, carried);
+    p_move<1>(w, t, ext[1], cl, carried, mf);
     grid_sync(ps.bar, w.err, bar_target);
     clk.lap(2);
     // ---- P4: sheep births; sheep counters
