@@ -330,10 +330,12 @@ def batched_leg(torch, engine, capacity, autotune, abm, hbm_peak, n_models=None,
     default = {"threads": 512, "ctas_per_sm": 2}
     tf = autotune.tune_batch(models, steps, abm.SWEEP_CAPACITY) if tune else default
     th, cps = tf["threads"], tf["ctas_per_sm"]
+    trials = lambda tt: [[x["threads"], x["ctas_per_sm"], round(x["ms"], 2)] for x in tt.get("trials", [])]
     out = {"workload": B["name"] if n_models == B["n_models"] and steps == B["steps"]
            else f"{n_models} models of {B['name']}, {steps} steps",
            "models": n_models, "steps": steps,
-           "launch_fixed": f"{th} threads x {cps} CTAs/SM" + (" (autotuned)" if tune else "")}
+           "launch_fixed": f"{th} threads x {cps} CTAs/SM" + (" (autotuned)" if tune else ""),
+           "tune_trials_fixed_ms": trials(tf)}
     # plain fixed capacity (one persistent launch for all 500 steps)
     b = engine.Batch(models)
     b.tune(th, cps)
@@ -379,6 +381,7 @@ def batched_leg(torch, engine, capacity, autotune, abm, hbm_peak, n_models=None,
     lmodels = [dict(m, cap=(int(cc[0]), int(cc[1]))) for m, cc in zip(models, learned)]
     tl = autotune.tune_batch(lmodels, steps, abm.SWEEP_CAPACITY) if tune else default
     out["launch_learned"] = f"{tl['threads']} threads x {tl['ctas_per_sm']} CTAs/SM" + (" (autotuned)" if tune else "")
+    out["tune_trials_learned_ms"] = trials(tl)
     res = capacity.run_learned(models, learned, fixed, steps, threads=tl["threads"], ctas_per_sm=tl["ctas_per_sm"])
     t_learned = res["ms_learned"] + res["ms_rerun"] + t_mlp
     out["learned"] = {"ms": t_learned, "ms_run": res["ms_learned"], "ms_rerun": res["ms_rerun"], "ms_mlp": t_mlp,

@@ -60,11 +60,14 @@ def _time(fn) -> float:
     return e0.elapsed_time(e1)
 
 
-def tune_batch(models: list, steps: int, sweep: int, trial_steps: int = 12, rounds: int = 2,
+def tune_batch(models: list, steps: int, sweep: int, trial_steps: int | None = None, rounds: int = 1,
                use_cache: bool = True, **_ignored) -> dict:
-    """Pick (threads, ctas_per_sm) for a batch of models: trials run on the
-    whole batch, each candidate for trial_steps, candidates interleaved over
-    `rounds` passes so that the slowly changing populations bias no one."""
+    """Pick (threads, ctas_per_sm) for a batch of models. By default every
+    candidate runs the whole batch for all `steps` from the initial state, so
+    each times exactly the work it will be chosen for (populations change a
+    lot over a run, so a short slice of it misjudges the shapes); a smaller
+    trial_steps trades accuracy for tuning time, with candidates interleaved
+    over `rounds` passes."""
     sig = {"n": len(models), "steps": steps, "sweep": sweep,
            "sides": np.histogram([m["side"] for m in models], bins=8)[0].tolist(),
            "cap": int(sum(int(m["cap"][0]) + int(m["cap"][1]) for m in models))}
@@ -75,15 +78,24 @@ def tune_batch(models: list, steps: int, sweep: int, trial_steps: int = 12, roun
             return hit
     # shapes whose CTAs can all be resident at 64 registers per thread
     cands = [(256, 1), (256, 2), (256, 4), (512, 1), (512, 2), (1024, 1)]
-    b = engine.Batch(models)
-    b.run(2, sweep=sweep)
     acc = {cnd: 0.0 for cnd in cands}
-    for _ in range(rounds):
-        for th, cps in cands:
-            b.tune(th, cps)
-            acc[(th, cps)] += _time(lambda: b.run(trial_steps, sweep=sweep))
-    b.check()
-    del b
+    if trial_steps is None or trial_steps >= steps:
+        for _ in range(rounds):
+            for th, cps in cands:
+                b = engine.Batch(models)
+                b.tune(th, cps)
+                acc[(th, cps)] += _time(lambda: b.run(steps, sweep=sweep))
+                b.check()
+                del b
+    else:
+        b = engine.Batch(models)
+        b.run(2, sweep=sweep)
+        for _ in range(rounds):
+            for th, cps in cands:
+                b.tune(th, cps)
+                acc[(th, cps)] += _time(lambda: b.run(trial_steps, sweep=sweep))
+        b.check()
+        del b
     torch.cuda.empty_cache()
     results = sorted((ms, th, cps) for (th, cps), ms in acc.items())
     ms, th, cps = results[0]

@@ -32,10 +32,12 @@ __global__ void __launch_bounds__(kResThreads) k_claims(const int32_t* __restric
   extern __shared__ unsigned char smem[];
   u64* s_best = reinterpret_cast<u64*>(smem);
   int* s_tag = reinterpret_cast<int*>(s_best + kHash);
+  __shared__ int s_used;  // distinct resources in the table
   for (int h = threadIdx.x; h < kHash; h += kResThreads) {
     s_tag[h] = -1;
     s_best[h] = kNoKey;
   }
+  if (threadIdx.x == 0) s_used = 0;
   __syncthreads();
   const int nchunks = (M + kResChunk - 1) / kResChunk;
   for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
@@ -51,7 +53,10 @@ __global__ void __launch_bounds__(kResThreads) k_claims(const int32_t* __restric
       bool done = false;
       for (int p = 0; p < kMaxProbe; ++p) {
         int t = s_tag[h];
-        if (t == -1) t = atomicCAS(&s_tag[h], -1, r);
+        if (t == -1) {
+          t = atomicCAS(&s_tag[h], -1, r);
+          if (t == -1) atomicAdd(&s_used, 1);
+        }
         if (t == -1 || t == r) {
           atomicMin(&s_best[h], key);
           done = true;
@@ -62,13 +67,20 @@ __global__ void __launch_bounds__(kResThreads) k_claims(const int32_t* __restric
       if (!done) atomicMin(&table[r], key);  // table full around h: go straight to global
     }
     __syncthreads();
-    for (int h = threadIdx.x; h < kHash; h += kResThreads) {
-      const int t = s_tag[h];
-      if (t >= 0) {
-        atomicMin(&table[t], s_best[h]);
-        s_tag[h] = -1;
-        s_best[h] = kNoKey;
+    // The table is folded into global memory only when it is half full or the
+    // CTA has no chunks left: skewed claims (a few hot resources) then cost
+    // one global atomic per distinct resource per CTA, not per chunk.
+    if (s_used > kHash / 2 || c + (int)gridDim.x >= nchunks) {
+      for (int h = threadIdx.x; h < kHash; h += kResThreads) {
+        const int t = s_tag[h];
+        if (t >= 0) {
+          atomicMin(&table[t], s_best[h]);
+          s_tag[h] = -1;
+          s_best[h] = kNoKey;
+        }
       }
+      __syncthreads();
+      if (threadIdx.x == 0) s_used = 0;
     }
     __syncthreads();
   }
