@@ -392,6 +392,14 @@ def batched_leg(torch, engine, capacity, autotune, abm, hbm_peak, n_models=None,
                       "capacity_sum_fixed": int(fixed.sum()), "capacity_sum_learned": int(learned.sum()),
                       "peak_sum": int(hw.sum()),
                       "wasted_capacity": (int(learned.sum()) - int(hw.sum())) / int(hw.sum())}
+    # learned capacities (memory) with extent sweeps (work): both savings at once
+    res = capacity.run_learned(models, learned, fixed, steps, sweep=abm.SWEEP_EXTENT, threads=tl["threads"],
+                               ctas_per_sm=tl["ctas_per_sm"])
+    t_le = res["ms_learned"] + res["ms_rerun"] + t_mlp
+    out["learned_extent_sweep"] = {"ms": t_le, "ms_run": res["ms_learned"], "ms_rerun": res["ms_rerun"],
+                                   "agent_steps_per_s": agents / (t_le * 1e-3), "speedup_vs_fixed": t_fixed / t_le,
+                                   "overflowed_models": len(res["overflowed"]),
+                                   "bit_exact_vs_fixed": bool(np.array_equal(res["digest"], want))}
     return out
 
 
