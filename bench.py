@@ -36,6 +36,7 @@ import numpy as np  # noqa: E402
 import workloads  # noqa: E402
 
 METRIC = "agent-steps/s (predation)"
+NOMINAL_HBM_GBS = 8000.0  # GB300 HBM3e, nominal
 UNIT = "agent-steps/s"
 PHASES = ("sheep_move", "sheep_scan", "sheep_births", "wolf_move", "wolf_scan", "wolf_births")
 KERNELS = ("k_move<0>", "k_scan<0>", "k_births<0>", "k_move<1>", "k_scan<1>", "k_births<1>")
@@ -267,7 +268,7 @@ def selective_update_leg(torch, engine, abm, autotune, hbm_peak, steps=8, warmup
         rec = torch.empty((k, F), dtype=torch.int32, device="cuda")
         dl = torch.empty((k, F), dtype=torch.int32, device="cuda")
         cnt = torch.zeros(3, dtype=torch.int32, device="cuda")
-        times, nbytes = [], []
+        times, nbytes, sbytes = [], [], []
         for it in range(warmup + steps):
             s.philox_records(it, abm.P_NEWREC0, abm.P_NEWREC1, k, out=rec)
             s.philox_records(it, abm.P_DELTA0, abm.P_DELTA1, k, out=dl)
@@ -282,11 +283,16 @@ def selective_update_leg(torch, engine, abm, autotune, hbm_peak, steps=8, warmup
                 removed, added, updated = cnt.tolist()
                 times.append(e0.elapsed_time(e1))
                 nbytes.append(4 * n + 4 * (removed + added) + added * (32 + 32) + updated * (32 + 32 + 32))
+                # sector-granular: every flag change touches its own 32-byte sector (an upper bound)
+                sbytes.append(4 * n + 32 * (removed + added) + added * (32 + 32) + updated * (32 + 32 + 32))
         s.check()
         ms = statistics.median(times)
         b = statistics.median(nbytes)
         gbs = b / (ms * 1e-3) / 1e9
+        sb = statistics.median(sbytes)
         out[str(p)] = {"k": k, "ms": ms, "algorithmic_bytes": int(b), "gbs": gbs, "frac": gbs / hbm_peak,
+                       "frac_of_nominal_8tbs": gbs / NOMINAL_HBM_GBS, "sector_bytes_upper": int(sb),
+                       "sector_gbs_upper": sb / (ms * 1e-3) / 1e9,
                        "launch": f"{tuned['threads']} threads x {tuned['ctas_per_sm']} CTAs/SM"
                                  + (" (autotuned)" if tune else "")}
         del s, rec, dl
@@ -403,6 +409,107 @@ def batched_leg(torch, engine, capacity, autotune, abm, hbm_peak, n_models=None,
     return out
 
 
+def small_world_leg(torch, engine, abm, reps=10):
+    """The 40x40 world (100 sheep / 25 wolves, 200 steps): launch- and
+    latency-bound, so no roofline. Three ways to run it: the persistent
+    kernel (one launch for all steps), the per-phase kernels replayed from a
+    CUDA graph, and the batched runner with a batch of one (one CTA)."""
+    c = workloads.PRED_SMALL
+    n = c["steps"]
+
+    def timed(fn):
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    mk = lambda: engine.World(c["side"], c["seed"], c["model"], c["params"], c["cap"], c["n0"])
+    # agent-steps of the run, from one reference run
+    ref = mk()
+    st = ref.new_stats(n)
+    ref.step(n, st)
+    rows = engine.decode_stats(st)
+    agents = sum(r["n_start"][0] + r["n_start"][1] for r in rows)
+    want = ref.counters()
+    out = {"workload": c["name"], "steps": n, "agent_steps": agents, "timing": f"median of {reps} runs, CUDA events"}
+    # persistent kernel: a fresh world per run (results are checked below)
+    worlds = [mk() for _ in range(reps)]
+    it = iter(worlds)
+    ms = timed(lambda: next(it).step(n))
+    same = all(w_.counters() == want for w_ in worlds)
+    out["persistent_one_launch"] = {"ms": ms, "us_per_step": 1e3 * ms / n, "agent_steps_per_s": agents / (ms * 1e-3),
+                                    "same_result": same}
+    del worlds
+    # per-phase kernels in a CUDA graph (captured once, replayed per run)
+    s = torch.cuda.Stream()
+    worlds = [mk() for _ in range(reps + 1)]
+    for w_ in worlds:
+        w_.tune(abm.ENGINE_KERNELS)
+    with torch.cuda.stream(s):
+        worlds[0].step_graph(n, 1, stream=s)  # capture + first replay
+        s.synchronize()
+        it = iter(worlds[1:])
+        # each world captures its own graph on first use; replay = one graph launch of n steps
+        for w_ in worlds[1:]:
+            w_.step_graph(n, 0, stream=s)  # capture only
+        s.synchronize()
+        ms = timed(lambda: next(it).step_graph(n, 1, stream=s))
+    same = all(w_.counters() == want for w_ in worlds)
+    out["kernels_cuda_graph"] = {"ms": ms, "us_per_step": 1e3 * ms / n, "agent_steps_per_s": agents / (ms * 1e-3),
+                                 "same_result": same}
+    del worlds
+    # one model through the batched runner (one CTA, __syncthreads between phases)
+    model = dict(side=c["side"], seed=c["seed"], model=c["model"], params=c["params"], cap=c["cap"], n0=c["n0"])
+    batches = [engine.Batch([model]) for _ in range(reps)]
+    for b in batches:
+        b.tune(512, 1)
+    it = iter(batches)
+    ms = timed(lambda: next(it).run(n, sweep=abm.SWEEP_EXTENT))
+    same = all(b.counters()[0]["agent_steps"] == agents for b in batches)
+    out["batched_one_cta"] = {"ms": ms, "us_per_step": 1e3 * ms / n, "agent_steps_per_s": agents / (ms * 1e-3),
+                              "same_agent_steps": same}
+    del batches
+    return out
+
+
+def _oracle_model_run(args):
+    """One batched-workload model on the sequential oracle (process-pool worker)."""
+    side, seed, model, params, cap, n0, steps = args
+    import oracle
+    w = oracle.World(side, seed, model, params, cap, n0)
+    t0 = time.perf_counter()
+    st = w.step(steps)
+    dt = time.perf_counter() - t0
+    return sum(r["n_start"][0] + r["n_start"][1] for r in st), dt
+
+
+def batched_cpu_baseline(n_sample=48, sample_seed=7):
+    """The oracle on the batched workload, one model per host core: a random
+    sample of the 4096 models for all 500 steps, scaled to the whole batch."""
+    import multiprocessing as mp
+    B = workloads.BATCH
+    tab = workloads.sample_models(B["n_models"], B["sampler_seed"])
+    fixed = workloads.fixed_caps(tab["side"])
+    pick = np.random.default_rng(sample_seed).choice(B["n_models"], size=n_sample, replace=False)
+    jobs = [(int(tab["side"][i]), B["philox_seed"], int(i), [int(x) for x in tab["params"][i]],
+             [int(x) for x in fixed[i]], [int(x) for x in tab["n0"][i]], B["steps"]) for i in pick]
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_model_run, jobs, chunksize=1)
+    wall = time.perf_counter() - t0
+    agents = sum(a for a, _ in res)
+    return {"value": agents / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n_sample} random models (numpy seed {sample_seed}) of the 4096, all {B['steps']} steps, "
+                      f"one model per core, {wall:.1f} s wall",
+            "cpu_seconds": sum(d for _, d in res)}
+
+
 def run_ours(args, rank, world, local):
     import numpy as _np  # noqa: F401
     import torch
@@ -456,7 +563,11 @@ def run_ours(args, rank, world, local):
                 "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": persistent_traffic(K, W, tw["ctas_per_sm"])
                 if tw["engine"] == abm.ENGINE_PERSISTENT else None,
                 "launch_ms": ms_total, "algorithmic_bytes_per_launch": step_bytes,
+                "frac_of_nominal_8tbs": achieved / NOMINAL_HBM_GBS,
+                "bytes_per_agent_step": {"algorithmic": step_bytes / max(agents, 1)},
                 "note": "latency-bound: dependent random cell accesses and 5 grid barriers per step"}
+    if roofline["traffic"]:
+        roofline["bytes_per_agent_step"]["dram"] = roofline["traffic"] / max(agents, 1)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": t_max / max(K, 1), "higher_is_better": True, "scaling": "weak",
@@ -507,6 +618,7 @@ def run_ours(args, rank, world, local):
         del ew, img_in, img_out
         line["selective_update"] = selective_update_leg(torch, engine, abm, autotune, hbm_peak)
         line["batched"] = batched_leg(torch, engine, capacity, autotune, abm, hbm_peak)
+        line["small_world"] = small_world_leg(torch, engine, abm)
     clk.__exit__(None, None, None)
     line["clocks"] = clk.summary()
     if rank == 0 and not args.no_extras:
@@ -514,7 +626,12 @@ def run_ours(args, rank, world, local):
         rate, n, dt = oracle_predation_rate(10**9, 0, budget_s=15.0)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"first {n} steps of the large predation run "
-                                          f"({dt:.1f} s, sequential C oracle, 1 thread)"}
+                                          f"({dt:.1f} s, sequential C oracle, 1 thread)",
+                                "host_cores": os.cpu_count()}
+        cb = batched_cpu_baseline()
+        line["batched"]["cpu_baseline"] = cb
+        line["batched"]["cpu_baseline"]["full_batch_s_estimate"] = \
+            line["batched"]["fixed"]["agent_steps_per_s"] * line["batched"]["fixed"]["ms"] * 1e-3 / cb["value"]
     if rank == 0:
         print(json.dumps(line), flush=True)
 
