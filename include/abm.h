@@ -121,6 +121,15 @@ typedef struct abm_pred {
 abm_status abm_select(abm_slab* s, const abm_pred* pred, int32_t* out_idx, int32_t* out_count,
                       void* stream);
 
+/* select_agents with SCI's index exposure (Algorithm 2, Section 4): a
+ * permutation of all slots, those satisfying `pred` first, then the others,
+ * each group ascending -- the stable argsort of the mask with true first.
+ * out_perm: device int32[capacity] (required); *out_count (device int32,
+ * required) = the number satisfying `pred`. Two stream compactions on
+ * `stream`. */
+abm_status abm_select_permutation(abm_slab* s, const abm_pred* pred, int32_t* out_perm, int32_t* out_count,
+                                  void* stream);
+
 /* set_agents_mask (Section 2) as removal: every slot satisfying `pred` becomes
  * a placeholder. *out_removed (device, nullable) = number removed. */
 abm_status abm_remove(abm_slab* s, const abm_pred* pred, int32_t* out_removed, void* stream);

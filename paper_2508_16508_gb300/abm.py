@@ -102,6 +102,7 @@ def _sig(L):
         "abm_slab_read": ([vp, i32, vp, i32, vp], st),
         "abm_slab_write": ([vp, i32, vp, i32, vp], st),
         "abm_select": ([vp, C.POINTER(abm_pred), vp, vp, vp], st),
+        "abm_select_permutation": ([vp, C.POINTER(abm_pred), vp, vp, vp], st),
         "abm_remove": ([vp, C.POINTER(abm_pred), vp, vp], st),
         "abm_add": ([vp, vp, i32, i32, vp, vp, vp], st),
         "abm_update_distinct": ([vp, C.POINTER(abm_pred), vp, vp, i32, i32, vp, vp, vp], st),
@@ -149,10 +150,12 @@ def _sig(L):
         "abm_capacity_features": ([vp, i32, vp, vp, vp], st),
         "abm_capacity_from_prediction": ([vp, i32, C.c_float, i32, vp, vp, vp, vp], st),
     }
+    global EXPORTED
     for name, (args, res) in sigs.items():
         f = getattr(L, name)
         f.argtypes = args
         f.restype = res
+    EXPORTED = tuple(sigs)
     return L
 
 

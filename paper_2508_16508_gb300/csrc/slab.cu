@@ -96,6 +96,8 @@ struct ScanArgs {
   int32_t* list_a;         // slots by rank: selected / free (caller's out_idx or scratch)
   int32_t* list_b;         // slots by rank: chosen (fused call)
   int32_t* out_count;      // device outputs (nullable)
+  int negate;              // OP_SELECT: select where the predicate is false
+  const int32_t* list_base;  // OP_SELECT: device offset added to every rank (nullable)
 };
 
 // copy or add one record into a slot's fields
@@ -195,7 +197,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_count(ScanArgs a) {
         if (slot < a.n) {
           if (OP == OP_ARRAY) f = live[j] != 0;
           else if (OP == OP_ADD) f = live[j] == 0;
-          else f = eval_pred(a.pred, s, slot, live[j]);
+          else f = eval_pred(a.pred, s, slot, live[j]) != (a.negate != 0);
         }
         ma |= (u32)f << j;
       }
@@ -294,6 +296,8 @@ __global__ void __launch_bounds__(THREADS) k_scatter(ScanArgs a) {
   const u32 limit = (u32)(OP == OP_UPDATE ? nrec : (OP == OP_SELECT || OP == OP_ARRAY ? 0x7FFFFFFF : a.k));
   const u32 limit_b = (u32)a.k;
   const u32 half_lt = (1u << (lane & 15)) - 1u;
+  // ranks land at list_a + *list_base (the permutation's second half)
+  int32_t* const list_a = a.list_a + (OP == OP_SELECT && a.list_base ? *a.list_base : 0);
   const int seg = a.chunk / WARPS;
   const int wlo = blockIdx.x * a.chunk + warp * seg;
   const int whi = min(a.n, wlo + seg);
@@ -329,7 +333,7 @@ __global__ void __launch_bounds__(THREADS) k_scatter(ScanArgs a) {
       const int slot = b0 + 32 * w + lane;
       const u32 rank = orank + __popc(om & half_lt);
       if (((om >> (lane & 15)) & 1u) && rank < limit) {
-        a.list_a[rank] = slot;
+        list_a[rank] = slot;
         if (OP == OP_ADD || OP == OP_FUSED) s.active[slot] = 1;
       }
     }
@@ -766,6 +770,27 @@ extern "C" abm_status abm_select(abm_slab* s, const abm_pred* pred, int32_t* out
   a.list_a = out_idx;
   a.out_count = out_count;
   return launch_scan<OP_SELECT>(s, a, false, (cudaStream_t)stream);
+}
+
+extern "C" abm_status abm_select_permutation(abm_slab* s, const abm_pred* pred, int32_t* out_perm,
+                                             int32_t* out_count, void* stream) {
+  if (!s || !pred_ok(s, pred) || !out_perm || !out_count) return ABM_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  ScanArgs a = base_args(s);
+  a.pred = to_dev(pred);
+  a.list_a = out_perm;
+  a.out_count = out_count;
+  abm_status e = launch_scan<OP_SELECT>(s, a, false, st);
+  if (e != ABM_OK) return e;
+  // the complement, ranked from *out_count on (read on the device by the
+  // second compaction, after the first one has finished in stream order)
+  ScanArgs b = base_args(s);
+  b.pred = to_dev(pred);
+  b.negate = 1;
+  b.list_a = out_perm;
+  b.list_base = out_count;
+  b.out_count = s->d.meta + 3;
+  return launch_scan<OP_SELECT>(s, b, false, st);
 }
 
 extern "C" abm_status abm_remove(abm_slab* s, const abm_pred* pred, int32_t* out_removed, void* stream) {

@@ -69,6 +69,13 @@ class Slab:
         call("abm_select", self.h, C.byref(p), ptr(idx), ptr(cnt), _stream(stream))
         return idx, cnt
 
+    def select_permutation(self, p: abm.abm_pred, stream=None):
+        """All slots, those satisfying p first (ascending), then the rest (ascending)."""
+        perm = torch.empty(self.capacity, **self._i32)
+        cnt = torch.zeros(1, **self._i32)
+        call("abm_select_permutation", self.h, C.byref(p), ptr(perm), ptr(cnt), _stream(stream))
+        return perm, cnt
+
     def remove(self, p: abm.abm_pred, stream=None) -> torch.Tensor:
         cnt = torch.zeros(1, **self._i32)
         call("abm_remove", self.h, C.byref(p), ptr(cnt), _stream(stream))

@@ -146,6 +146,30 @@ def test_select_predicates(eng, n):
         np.testing.assert_array_equal(np_of(idx[:c]), want)
 
 
+@pytest.mark.parametrize("n", [1, 33, 2049, 4096 * 3 + 17])
+def test_select_permutation(eng, n):
+    """SCI's index exposure (Algorithm 2): the selected slots ascending, then
+    the rest ascending -- the stable argsort of the mask with true first."""
+    from paper_2508_16508_gb300 import abm
+    s = eng.Slab(n, 3, seed=6, init=1)
+    act, fld = slab_state(s)
+    T = workloads.threshold(0.5)
+    cases = [(abm.pred(abm.PRED_LIVE), act != 0),
+             (abm.pred(abm.PRED_FREE), act == 0),
+             (abm.pred(abm.PRED_BERNOULLI, threshold=T, step=3, purpose=abm.P_REPRO, species=1),
+              (act != 0) & (oracle.philox_words(6, 0, 3, oracle.P_REPRO, 1, 0, n) < T)),
+             (abm.pred(abm.PRED_FIELD, field=2, cmp=abm.CMP_LT, and_mask=0xFF, value=100),
+              (act != 0) & ((fld[2] & 0xFF) < 100))]
+    for p, m in cases:
+        perm, cnt = s.select_permutation(p)
+        sel = oracle.flatnonzero(m.astype(np.int32))
+        rest = oracle.flatnonzero((~m).astype(np.int32))
+        assert int(cnt.item()) == sel.size
+        np.testing.assert_array_equal(np_of(perm), np.concatenate([sel, rest]))
+        np.testing.assert_array_equal(np_of(perm), np.argsort(~m, kind="stable"))
+    s.check()
+
+
 @pytest.mark.parametrize("n", [5, 2049, 7000])
 def test_add_remove_update_vs_oracle(eng, n):
     from paper_2508_16508_gb300 import abm
