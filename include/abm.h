@@ -259,12 +259,23 @@ abm_status abm_resolve_static(const int32_t* claim_res, const uint32_t* claim_pr
  */
 typedef struct abm_world abm_world;
 
+/* Rule variants of the wolves' meal (the paper does not fix it):
+ * ONE_WOLF: per cell, the live wolf with the smallest (PRIO draw, slot) eats
+ *   the live sheep with the smallest (VICTIM draw, slot); at most one per cell.
+ * MANY_WOLVES: per cell, the i-th wolf by (PRIO draw, slot) eats the i-th
+ *   sheep by (VICTIM draw, slot), i < min(#wolves, #sheep) (NetLogo lets every
+ *   wolf eat; Algorithm 1's rank matching inside each cell). Persistent engine
+ *   only (abm_world_tune refuses the per-phase kernels for such a world). */
+#define ABM_VARIANT_ONE_WOLF 0
+#define ABM_VARIANT_MANY_WOLVES 1
+
 typedef struct abm_config {
   int32_t side;
   uint32_t seed, model;
   int32_t params[8];
   int32_t cap[2];
   int32_t n0[2];
+  int32_t variant; /* ABM_VARIANT_* */
 } abm_config;
 
 /* Per-step statistics, written by the device (one record per step). */

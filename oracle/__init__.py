@@ -94,6 +94,7 @@ def lib():
             L.orc_pred_create.restype = C.c_void_p
             L.orc_pred_free.argtypes = [C.c_void_p]
             L.orc_pred_step.argtypes = [C.c_void_p, C.POINTER(Stats)]
+            L.orc_pred_set_variant.argtypes = [C.c_void_p, C.c_int32]
             L.orc_pred_agents.argtypes = [C.c_void_p, C.c_int, C.c_int]
             L.orc_pred_agents.restype = i32p
             L.orc_pred_grass.argtypes = [C.c_void_p, C.c_int]
@@ -220,10 +221,15 @@ def resolve(res, prio, R):
 AGENT_FIELDS = ("active", "cell", "energy", "id", "age")
 
 
+VARIANT_ONE_WOLF, VARIANT_MANY_WOLVES = 0, 1
+
+
 class World:
     """One predation model (wolf-sheep-grass) stepped by the sequential oracle."""
 
-    def __init__(self, side, seed, model, params, cap, n0):
+    def __init__(self, side, seed, model, params, cap, n0, variant=0):
+        """variant: VARIANT_ONE_WOLF (at most one wolf eats per cell per step) or
+        VARIANT_MANY_WOLVES (the i-th wolf of a cell eats its i-th sheep)."""
         self.side = int(side)
         p, c, n = _i32(params), _i32(cap), _i32(n0)
         assert p.size == 8 and c.size == 2 and n.size == 2
@@ -231,6 +237,9 @@ class World:
                                         _p(p, C.c_int32), _p(c, C.c_int32), _p(n, C.c_int32))
         if not self._w:
             raise ValueError("invalid predation configuration")
+        if variant not in (VARIANT_ONE_WOLF, VARIANT_MANY_WOLVES):
+            raise ValueError("unknown rule variant")
+        lib().orc_pred_set_variant(self._w, variant)
         self.cap = [int(c[0]), int(c[1])]
 
     def __del__(self):

@@ -227,6 +227,7 @@ struct orc_world {
   uint64_t* victim;    /* per-cell minimum victim key */
   int32_t n_active[2], next_id[2], hw[2], overflow[2];
   uint32_t t;
+  int32_t variant;     /* ORC_VARIANT_*: how wolves eat */
 };
 
 enum { A_ACTIVE = 0, A_CELL = 1, A_ENERGY = 2, A_ID = 3, A_AGE = 4 };
@@ -440,6 +441,66 @@ static void wolves_eat(orc_world* w, orc_stats* st) {
   }
 }
 
+/* (key, slot) pairs of one cell, ascending by key (keys are unique: the slot
+ * is in the low half). */
+typedef struct {
+  uint64_t key;
+  int32_t slot;
+} orc_keyed;
+
+static int cmp_keyed(const void* a, const void* b) {
+  const uint64_t x = ((const orc_keyed*)a)->key, y = ((const orc_keyed*)b)->key;
+  return x < y ? -1 : x > y;
+}
+
+/* Variant: several wolves per cell (NetLogo lets every wolf eat). On every
+ * cell, order the live sheep by (VICTIM draw, slot) and the live wolves by
+ * (PRIO draw, slot); the i-th wolf eats the i-th sheep for i < min(#sheep,
+ * #wolves) -- Algorithm 1's rank matching applied inside each cell. Each
+ * eating wolf gains energy; each eaten sheep is removed. */
+static void wolves_eat_many(orc_world* w, orc_stats* st) {
+  const int32_t n = w->ncells;
+  int32_t* start[2];
+  orc_keyed* items[2];
+  for (int s = 0; s < 2; s++) {
+    /* bucket the live agents by cell (counting sort), in slot order */
+    start[s] = (int32_t*)calloc((size_t)n + 1, sizeof(int32_t));
+    for (int32_t i = 0; i < w->cap[s]; i++)
+      if (w->agent[s][A_ACTIVE][i]) start[s][w->agent[s][A_CELL][i] + 1]++;
+    for (int32_t c = 0; c < n; c++) start[s][c + 1] += start[s][c];
+    items[s] = (orc_keyed*)malloc(sizeof(orc_keyed) * (size_t)(start[s][n] > 0 ? start[s][n] : 1));
+    int32_t* fill = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    memcpy(fill, start[s], sizeof(int32_t) * (size_t)n);
+    for (int32_t i = 0; i < w->cap[s]; i++) {
+      if (!w->agent[s][A_ACTIVE][i]) continue;
+      const uint32_t purpose = s == 0 ? ORC_P_VICTIM : ORC_P_PRIO;
+      const orc_keyed e = {make_key(draw(w->seed, w->model, w->t, (uint32_t)i, purpose, (uint32_t)s, 0), i), i};
+      items[s][fill[w->agent[s][A_CELL][i]]++] = e;
+    }
+    free(fill);
+  }
+  for (int32_t c = 0; c < n; c++) {
+    const int32_t ns = start[0][c + 1] - start[0][c], nw = start[1][c + 1] - start[1][c];
+    if (ns == 0 || nw == 0) continue;
+    orc_keyed* sh = items[0] + start[0][c];
+    orc_keyed* wo = items[1] + start[1][c];
+    qsort(sh, (size_t)ns, sizeof(orc_keyed), cmp_keyed);
+    qsort(wo, (size_t)nw, sizeof(orc_keyed), cmp_keyed);
+    for (int32_t i = 0; i < ns && i < nw; i++) {
+      w->agent[1][A_ENERGY][wo[i].slot] += w->params[1];
+      w->agent[0][A_ACTIVE][sh[i].slot] = 0;
+      w->n_active[0]--;
+      st->eaten++;
+    }
+  }
+  for (int s = 0; s < 2; s++) {
+    free(start[s]);
+    free(items[s]);
+  }
+}
+
+void orc_pred_set_variant(orc_world* w, int32_t variant) { w->variant = variant; }
+
 /* Grass regrowth after a fixed delay: a cell eaten at step t is grown again
  * from step t + delay on. */
 static void grass(orc_world* w) {
@@ -461,7 +522,10 @@ void orc_pred_step(orc_world* w, orc_stats* st) {
   reproduce(w, 0, st);
   die(w, 0, st);
   move_species(w, 1);
-  wolves_eat(w, st);
+  if (w->variant == ORC_VARIANT_MANY_WOLVES)
+    wolves_eat_many(w, st);
+  else
+    wolves_eat(w, st);
   reproduce(w, 1, st);
   die(w, 1, st);
   grass(w);

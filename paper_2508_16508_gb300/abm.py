@@ -45,9 +45,13 @@ class abm_pred(C.Structure):
                 ("value", C.c_int32)]
 
 
+VARIANT_ONE_WOLF, VARIANT_MANY_WOLVES = 0, 1
+
+
 class abm_config(C.Structure):
     _fields_ = [("side", C.c_int32), ("seed", C.c_uint32), ("model", C.c_uint32),
-                ("params", C.c_int32 * 8), ("cap", C.c_int32 * 2), ("n0", C.c_int32 * 2)]
+                ("params", C.c_int32 * 8), ("cap", C.c_int32 * 2), ("n0", C.c_int32 * 2),
+                ("variant", C.c_int32)]
 
 
 class abm_step_stats(C.Structure):
@@ -60,6 +64,7 @@ class abm_step_stats(C.Structure):
 
 STATS_BYTES = C.sizeof(abm_step_stats)
 STATS_WORDS = STATS_BYTES // 4
+STATS_FIELD_OFFSETS = {name: getattr(abm_step_stats, name).offset for name, _ in abm_step_stats._fields_}
 
 
 class abm_world_counters(C.Structure):

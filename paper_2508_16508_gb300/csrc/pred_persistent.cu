@@ -127,10 +127,17 @@ __device__ __forceinline__ int slot_of(u32 entry, int round) {
   return (unit_at((int)(entry >> 7), round) << 7) + (int)(entry & 127u);
 }
 
+// ---- several-wolves variant: per-cell lists tagged with the step
+__device__ __forceinline__ void list_push(u64* head, u64* next, u64* keys, int cell, int slot, int t, u64 key) {
+  keys[slot] = key;
+  next[slot] = atomicExch(reinterpret_cast<unsigned long long*>(head + cell),
+                          (unsigned long long)(((u64)(u32)t << 32) | (u32)slot));
+}
+
 template <int S>
 __device__ __forceinline__ int4 move_one(const WorldDev& w, int t, int slot, int4 ag, int L, int metab) {
   const SpeciesDev& sp = w.sp[S];
-  if (S == 0) w.victim[ag.x] = kNoKey;  // last step's victim entry for this cell
+  if (S == 0 && w.variant == ABM_VARIANT_ONE_WOLF) w.victim[ag.x] = kNoKey;  // last step's victim entry here
   const u32 dir = draw(w.seed, w.model, (u32)t, (u32)slot, ABM_P_MOVE, (u32)S) >> 29;
   const int cell = step_cell(ag.x, L, dir);
   ag.x = cell;
@@ -141,8 +148,11 @@ __device__ __forceinline__ int4 move_one(const WorldDev& w, int t, int slot, int
     if (w.regrow[cell] <= t)
       atomicMin(&w.gclaim[cell], claim_key(draw(w.seed, w.model, (u32)t, (u32)slot, ABM_P_PRIO, 0u), slot));
   } else {
-    if (w.victim[cell] != kNoKey)
-      atomicMin(&w.wclaim[cell], claim_key(draw(w.seed, w.model, (u32)t, (u32)slot, ABM_P_PRIO, 1u), slot));
+    const u64 key = claim_key(draw(w.seed, w.model, (u32)t, (u32)slot, ABM_P_PRIO, 1u), slot);
+    if (w.variant == ABM_VARIANT_MANY_WOLVES)  // every wolf joins its cell's list
+      list_push(w.wclaim, w.wnext, w.wkey, cell, slot, t, key);
+    else if (w.victim[cell] != kNoKey)
+      atomicMin(&w.wclaim[cell], key);
   }
   return ag;
 }
@@ -212,6 +222,39 @@ __device__ __forceinline__ void p_move(const WorldDev& w, int t, int ext, const 
   }
 }
 
+// The wolf `slot` on `cell` eats if its rank among the cell's wolves (by key)
+// is below the number of sheep there; it eats the sheep of the same rank.
+// Lists only hold this step's entries (tag = t); a walk longer than the
+// species' capacity means a broken list: the error flag is set.
+__device__ __forceinline__ bool eat_rank_matched(const WorldDev& w, int t, int slot, int cell) {
+  const u64 tag = (u64)(u32)t;
+  const u64 mine = w.wkey[slot];
+  int rank = 0, n = 0;
+  for (u64 e = w.wclaim[cell]; (e >> 32) == tag; e = w.wnext[(u32)e]) {
+    if (++n > w.sp[1].cap) {
+      atomicExch(w.err, kErrTimeout);
+      return false;
+    }
+    rank += w.wkey[(u32)e] < mine;
+  }
+  n = 0;
+  for (u64 e = w.victim[cell]; (e >> 32) == tag; e = w.snext[(u32)e]) {
+    if (++n > w.sp[0].cap) {
+      atomicExch(w.err, kErrTimeout);
+      return false;
+    }
+    const u64 k = w.skey[(u32)e];
+    int below = 0, m = 0;
+    for (u64 f = w.victim[cell]; (f >> 32) == tag && m <= w.sp[0].cap; f = w.snext[(u32)f], ++m)
+      below += w.skey[(u32)f] < k;
+    if (below == rank) {
+      w.sp[0].active[(u32)e] = 0;
+      return true;
+    }
+  }
+  return false;
+}
+
 // one live agent of phase 2/5: eat if it won its cell, then die (energy
 // below zero) or be drawn as a parent. Returns bit 0 = parent, bit 1 = died,
 // bit 2 = ate.
@@ -221,7 +264,13 @@ __device__ __forceinline__ u32 count_one(const WorldDev& w, int t, int slot, int
   const SpeciesDev& sp = w.sp[S];
   const int cell = ag.x;
   u32 r = 0;
-  if (cl != kNoKey && (u32)cl == (u32)slot) {
+  if (S == 1 && w.variant == ABM_VARIANT_MANY_WOLVES) {
+    if (eat_rank_matched(w, t, slot, cell)) {
+      ag.y += gain;
+      sp.agent[slot].y = ag.y;
+      r |= 4u;
+    }
+  } else if (cl != kNoKey && (u32)cl == (u32)slot) {
     ag.y += gain;
     sp.agent[slot].y = ag.y;
     r |= 4u;
@@ -240,8 +289,13 @@ __device__ __forceinline__ u32 count_one(const WorldDev& w, int t, int slot, int
     r |= 2u;
   } else {
     if (draw(w.seed, w.model, (u32)t, (u32)slot, ABM_P_REPRO, (u32)S) < Tr) r |= 1u;
-    if (S == 0)
-      atomicMin(&w.victim[cell], claim_key(draw(w.seed, w.model, (u32)t, (u32)slot, ABM_P_VICTIM, 0u), slot));
+    if (S == 0) {
+      const u64 key = claim_key(draw(w.seed, w.model, (u32)t, (u32)slot, ABM_P_VICTIM, 0u), slot);
+      if (w.variant == ABM_VARIANT_MANY_WOLVES)
+        list_push(w.victim, w.snext, w.skey, cell, slot, t, key);
+      else
+        atomicMin(&w.victim[cell], key);
+    }
   }
   return r;
 }
@@ -560,8 +614,13 @@ __device__ __forceinline__ void p_births(const WorldDev& w, int t, int r, int F,
     sp.agent[p].y = pa.y - half;
     sp.agent[slot] = make_int4(pa.x, half, (int)((u32)id0 + (u32)i), 0);
     sp.active[slot] = 1;
-    if (S == 0)
-      atomicMin(&w.victim[pa.x], claim_key(draw(w.seed, w.model, (u32)t, (u32)slot, ABM_P_VICTIM, 0u), slot));
+    if (S == 0) {
+      const u64 key = claim_key(draw(w.seed, w.model, (u32)t, (u32)slot, ABM_P_VICTIM, 0u), slot);
+      if (w.variant == ABM_VARIANT_MANY_WOLVES)
+        list_push(w.victim, w.snext, w.skey, pa.x, slot, t, key);
+      else
+        atomicMin(&w.victim[pa.x], key);
+    }
   }
 }
 

@@ -51,6 +51,15 @@ struct WorldDev {
   u32 seed, model;
   u32 bar_base;     // barrier arrivals before this launch (persistent kernel)
   int params[8];
+  // ABM_VARIANT_MANY_WOLVES: per-cell lists of this step's live sheep and
+  // wolves. Heads reuse `victim` (sheep) and `wclaim` (wolves); a head or link
+  // is (step << 32 | slot), so entries of earlier steps end a list and no list
+  // is ever cleared. key = the agent's (draw, slot) key.
+  int variant;
+  u64* skey;        // [cap sheep]
+  u64* snext;       // [cap sheep]
+  u64* wkey;        // [cap wolves]
+  u64* wnext;       // [cap wolves]
 };
 
 // persistent step kernel (pred_persistent.cu)

@@ -317,6 +317,10 @@ static void world_free(abm_world* w) {
   }
   cudaFree(w->d.ps.bar);
   cudaFree(w->d.ps.acc);
+  cudaFree(w->d.skey);
+  cudaFree(w->d.snext);
+  cudaFree(w->d.wkey);
+  cudaFree(w->d.wnext);
   if (w->gexec) cudaGraphExecDestroy(w->gexec);
   delete w;
 }
@@ -335,6 +339,7 @@ extern "C" abm_status abm_create(const abm_config* cfg, void* stream, abm_world*
     if (cfg->params[s] < 0 || cfg->params[5 + s] < 0) return ABM_ERR_ARG;
   }
   if (cfg->params[4] < 1) return ABM_ERR_ARG;
+  if (cfg->variant != ABM_VARIANT_ONE_WOLF && cfg->variant != ABM_VARIANT_MANY_WOLVES) return ABM_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   abm_world* w = new (std::nothrow) abm_world();
   if (!w) return ABM_ERR_OOM;
@@ -344,6 +349,7 @@ extern "C" abm_status abm_create(const abm_config* cfg, void* stream, abm_world*
   d.ncells = cfg->side * cfg->side;
   d.seed = cfg->seed;
   d.model = cfg->model;
+  d.variant = cfg->variant;
   std::memcpy(d.params, cfg->params, sizeof(d.params));
   bool ok = true;
   for (int s = 0; s < 2; ++s) {
@@ -380,6 +386,12 @@ extern "C" abm_status abm_create(const abm_config* cfg, void* stream, abm_world*
     ok = cudaMalloc(&d.ps.blk[s], sizeof(u64) * (size_t)(w->cap_pad[s] / 128)) == cudaSuccess &&
          cudaMalloc(&d.ps.seg[s], sizeof(u64) * (size_t)pmax) == cudaSuccess &&
          cudaMemsetAsync(d.ps.seg[s], 0, sizeof(u64) * (size_t)pmax, st) == cudaSuccess;
+  }
+  if (d.variant == ABM_VARIANT_MANY_WOLVES) {
+    ok = ok && cudaMalloc(&d.skey, sizeof(u64) * (size_t)cfg->cap[0]) == cudaSuccess;
+    ok = ok && cudaMalloc(&d.snext, sizeof(u64) * (size_t)cfg->cap[0]) == cudaSuccess;
+    ok = ok && cudaMalloc(&d.wkey, sizeof(u64) * (size_t)cfg->cap[1]) == cudaSuccess;
+    ok = ok && cudaMalloc(&d.wnext, sizeof(u64) * (size_t)cfg->cap[1]) == cudaSuccess;
   }
   ok = ok && cudaMalloc(&d.ps.bar, sizeof(u32) * 2) == cudaSuccess;
   ok = ok && cudaMalloc(&d.ps.acc, sizeof(int) * 8) == cudaSuccess;
@@ -500,6 +512,9 @@ extern "C" abm_status abm_step_profiled(abm_world* w, int32_t nsteps, abm_step_s
 extern "C" abm_status abm_step(abm_world* w, int32_t nsteps, abm_step_stats* stats, int32_t want_energy,
                                void* stream) {
   if (!w || nsteps < 0) return ABM_ERR_ARG;
+  // the per-phase kernels (which also compute the energy statistics) do not
+  // implement the several-wolves variant
+  if (want_energy && w->d.variant != ABM_VARIANT_ONE_WOLF) return ABM_ERR_ARG;
   if (w->engine == ABM_ENGINE_PERSISTENT && !want_energy) {
     if (nsteps == 0) return ABM_OK;
     abm_status e = launch_persistent(w->d, &w->bar_next, w->pgrid, nsteps, stats, (cudaStream_t)stream);
@@ -517,6 +532,7 @@ extern "C" abm_status abm_step(abm_world* w, int32_t nsteps, abm_step_stats* sta
 extern "C" abm_status abm_step_graph(abm_world* w, int32_t nsteps, int32_t reps, abm_step_stats* stats,
                                      void* stream) {
   if (!w || nsteps < 1 || reps < 0 || !stream) return ABM_ERR_ARG;
+  if (w->d.variant != ABM_VARIANT_ONE_WOLF) return ABM_ERR_STATE;  // per-phase kernels only
   cudaStream_t st = (cudaStream_t)stream;
   if (!w->gexec || w->g_nsteps != nsteps || w->g_stats != stats) {
     if (w->gexec) {
@@ -546,6 +562,7 @@ extern "C" abm_status abm_step_graph(abm_world* w, int32_t nsteps, int32_t reps,
 
 extern "C" abm_status abm_world_tune(abm_world* w, int32_t engine, int32_t ctas_per_sm) {
   if (!w || (engine != ABM_ENGINE_PERSISTENT && engine != ABM_ENGINE_KERNELS) || ctas_per_sm < 1) return ABM_ERR_ARG;
+  if (engine == ABM_ENGINE_KERNELS && w->d.variant != ABM_VARIANT_ONE_WOLF) return ABM_ERR_ARG;
   const int g = num_sms() * ctas_per_sm;
   if (engine == ABM_ENGINE_PERSISTENT && g > w->pgrid_max) return ABM_ERR_ARG;
   w->engine = engine;

@@ -144,9 +144,10 @@ AGENT_FIELDS = ("active", "cell", "energy", "id", "age")
 class World:
     """One predation model (wolf-sheep-grass) on the GPU."""
 
-    def __init__(self, side, seed, model, params, cap, n0, stream=None):
+    def __init__(self, side, seed, model, params, cap, n0, stream=None, variant=abm.VARIANT_ONE_WOLF):
         cfg = abm.abm_config()
         cfg.side, cfg.seed, cfg.model = int(side), seed & 0xFFFFFFFF, model & 0xFFFFFFFF
+        cfg.variant = int(variant)
         for i in range(8):
             cfg.params[i] = int(params[i])
         for s in range(2):

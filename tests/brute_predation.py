@@ -14,8 +14,9 @@ MOVES = {0: (-1, -1), 1: (0, -1), 2: (1, -1), 3: (-1, 0), 4: (1, 0), 5: (-1, 1),
 
 
 class BruteWorld:
-    def __init__(self, side, seed, model, params, cap, n0):
+    def __init__(self, side, seed, model, params, cap, n0, many_wolves=False):
         self.L = side
+        self.many_wolves = many_wolves
         self.seed, self.model = seed, model
         self.p = [int(x) & 0xFFFFFFFF for x in params]
         self.gain = [self.p[0], self.p[1]]
@@ -104,12 +105,16 @@ class BruteWorld:
             cell = (a["x"], a["y"])
             if cell in sheep_at:
                 wolf_claims.setdefault(cell, []).append((self.draw(slot, oracle.P_PRIO, 1), slot))
+        eaten = 0
         for cell, c in wolf_claims.items():
-            wolf = sorted(c)[0][1]
-            victim = sorted(sheep_at[cell])[0][1]
-            self.agents[1][wolf]["e"] += self.gain[1]
-            del self.agents[0][victim]
-        st["eaten"] = len(wolf_claims)
+            # one wolf per cell eats, or (variant) the k-th wolf the k-th sheep
+            pairs = zip(sorted(c), sorted(sheep_at[cell])) if self.many_wolves else \
+                [(sorted(c)[0], sorted(sheep_at[cell])[0])]
+            for (_, wolf), (_, victim) in pairs:
+                self.agents[1][wolf]["e"] += self.gain[1]
+                del self.agents[0][victim]
+                eaten += 1
+        st["eaten"] = eaten
         st["parents1"], st["births1"] = self.reproduce(1)
         st["starved1"] = self.die(1)
         for g in self.grass.values():

@@ -53,6 +53,45 @@ def test_brute_force_tiny_worlds(seed):
         compare(ow, bw)
 
 
+@pytest.mark.parametrize("seed", range(60))
+def test_brute_force_tiny_worlds_many_wolves(seed):
+    """The several-wolves-per-cell variant against the list-of-agents
+    simulator: tiny, crowded worlds so that cells often hold several wolves."""
+    rng = np.random.default_rng(3000 + seed)
+    side = int(rng.integers(1, 5))
+    cap = (int(rng.integers(1, 30)), int(rng.integers(1, 20)))
+    n0 = (int(rng.integers(0, cap[0] + 1)), int(rng.integers(0, cap[1] + 1)))
+    params = workloads.predation_params(
+        sheep_gain=int(rng.integers(1, 6)), wolf_gain=int(rng.integers(2, 25)),
+        sheep_repro=float(rng.choice([0.04, 0.2, 0.5])), wolf_repro=float(rng.choice([0.05, 0.2, 0.5])),
+        regrowth=int(rng.integers(1, 12)), grass_init=float(rng.choice([0.25, 0.5, 0.9])))
+    ow = oracle.World(side, seed, 7, params, cap, n0, variant=oracle.VARIANT_MANY_WOLVES)
+    bw = BruteWorld(side, seed, 7, params, cap, n0, many_wolves=True)
+    compare(ow, bw)
+    for _ in range(40):
+        st = ow.step()[0]
+        bst = bw.step()
+        assert st["grass_eaten"] == bst["grass_eaten"] and st["eaten"] == bst["eaten"]
+        assert st["births"] == [bst["births0"], bst["births1"]]
+        assert st["starved"] == [bst["starved0"], bst["starved1"]]
+        compare(ow, bw)
+
+
+def test_many_wolves_single_cell_eat_min():
+    """One cell: every wolf faces every sheep, so min(#sheep, #wolves) sheep
+    are eaten (no reproduction, so the counts are those after the sheep die)."""
+    params = workloads.predation_params(sheep_repro=0.0, wolf_repro=0.0, sheep_gain=3, wolf_gain=5)
+    for n0 in [(10, 4), (3, 7), (5, 5), (0, 3), (4, 0)]:
+        ow = oracle.World(1, 11, 0, params, (16, 16), n0, variant=oracle.VARIANT_MANY_WOLVES)
+        for _ in range(5):
+            st = ow.step()[0]
+            sheep_left = st["n_start"][0] - st["starved"][0]
+            assert st["eaten"] == min(sheep_left, st["n_start"][1]), (n0, st)
+        one = oracle.World(1, 11, 0, params, (16, 16), n0)  # default: one wolf eats per cell
+        st = one.step()[0]
+        assert st["eaten"] == min(1, st["n_start"][0] - st["starved"][0], st["n_start"][1])
+
+
 def check_invariants(before, after, st, counters_before, counters_after, params, ncells):
     p = [int(x) & 0xFFFFFFFF for x in params]
     gain, metab = (p[0], p[1]), (p[5], p[6])
