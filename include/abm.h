@@ -259,15 +259,20 @@ abm_status abm_resolve_static(const int32_t* claim_res, const uint32_t* claim_pr
  */
 typedef struct abm_world abm_world;
 
-/* Rule variants of the wolves' meal (the paper does not fix it):
- * ONE_WOLF: per cell, the live wolf with the smallest (PRIO draw, slot) eats
- *   the live sheep with the smallest (VICTIM draw, slot); at most one per cell.
+/* Rule variants (bits; the paper fixes neither):
+ * 0 (ONE_WOLF): per cell, the live wolf with the smallest (PRIO draw, slot)
+ *   eats the live sheep with the smallest (VICTIM draw, slot); at most one per
+ *   cell and step.
  * MANY_WOLVES: per cell, the i-th wolf by (PRIO draw, slot) eats the i-th
  *   sheep by (VICTIM draw, slot), i < min(#wolves, #sheep) (NetLogo lets every
- *   wolf eat; Algorithm 1's rank matching inside each cell). Persistent engine
- *   only (abm_world_tune refuses the per-phase kernels for such a world). */
+ *   wolf eat; Algorithm 1's rank matching inside each cell).
+ * GRASS_OFF: sheep neither eat grass nor spend energy moving (Wilensky's
+ *   model without grass); the grass state still evolves.
+ * Any variant bit: persistent engine only (abm_world_tune refuses the
+ * per-phase kernels for such a world, and so do energy statistics). */
 #define ABM_VARIANT_ONE_WOLF 0
 #define ABM_VARIANT_MANY_WOLVES 1
+#define ABM_VARIANT_GRASS_OFF 2
 
 typedef struct abm_config {
   int32_t side;

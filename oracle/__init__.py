@@ -221,15 +221,16 @@ def resolve(res, prio, R):
 AGENT_FIELDS = ("active", "cell", "energy", "id", "age")
 
 
-VARIANT_ONE_WOLF, VARIANT_MANY_WOLVES = 0, 1
+VARIANT_ONE_WOLF, VARIANT_MANY_WOLVES, VARIANT_GRASS_OFF = 0, 1, 2  # bits
 
 
 class World:
     """One predation model (wolf-sheep-grass) stepped by the sequential oracle."""
 
     def __init__(self, side, seed, model, params, cap, n0, variant=0):
-        """variant: VARIANT_ONE_WOLF (at most one wolf eats per cell per step) or
-        VARIANT_MANY_WOLVES (the i-th wolf of a cell eats its i-th sheep)."""
+        """variant: bits -- VARIANT_MANY_WOLVES (the i-th wolf of a cell eats its
+        i-th sheep; default: at most one wolf eats per cell per step) and
+        VARIANT_GRASS_OFF (sheep neither eat grass nor spend energy)."""
         self.side = int(side)
         p, c, n = _i32(params), _i32(cap), _i32(n0)
         assert p.size == 8 and c.size == 2 and n.size == 2
@@ -237,7 +238,7 @@ class World:
                                         _p(p, C.c_int32), _p(c, C.c_int32), _p(n, C.c_int32))
         if not self._w:
             raise ValueError("invalid predation configuration")
-        if variant not in (VARIANT_ONE_WOLF, VARIANT_MANY_WOLVES):
+        if variant & ~(VARIANT_MANY_WOLVES | VARIANT_GRASS_OFF):
             raise ValueError("unknown rule variant")
         lib().orc_pred_set_variant(self._w, variant)
         self.cap = [int(c[0]), int(c[1])]

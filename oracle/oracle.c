@@ -227,7 +227,7 @@ struct orc_world {
   uint64_t* victim;    /* per-cell minimum victim key */
   int32_t n_active[2], next_id[2], hw[2], overflow[2];
   uint32_t t;
-  int32_t variant;     /* ORC_VARIANT_*: how wolves eat */
+  int32_t variant;     /* ORC_VARIANT_* bits */
 };
 
 enum { A_ACTIVE = 0, A_CELL = 1, A_ENERGY = 2, A_ID = 3, A_AGE = 4 };
@@ -314,7 +314,8 @@ static const int DY[8] = {-1, -1, -1, 0, 0, 1, 1, 1};
  * metabolism, ageing -- for every live agent of the species. */
 static void move_species(orc_world* w, int s) {
   int32_t L = w->side;
-  int32_t metab = w->params[5 + s];
+  /* without grass (variant), sheep neither eat nor spend energy */
+  int32_t metab = (s == 0 && (w->variant & ORC_VARIANT_GRASS_OFF)) ? 0 : w->params[5 + s];
   for (int32_t i = 0; i < w->cap[s]; i++) {
     if (!w->agent[s][A_ACTIVE][i]) continue;
     uint32_t u = draw(w->seed, w->model, w->t, (uint32_t)i, ORC_P_MOVE, (uint32_t)s, 0);
@@ -518,11 +519,11 @@ void orc_pred_step(orc_world* w, orc_stats* st) {
   st->n_start[0] = w->n_active[0];
   st->n_start[1] = w->n_active[1];
   move_species(w, 0);
-  sheep_eat(w, st);
+  if (!(w->variant & ORC_VARIANT_GRASS_OFF)) sheep_eat(w, st);
   reproduce(w, 0, st);
   die(w, 0, st);
   move_species(w, 1);
-  if (w->variant == ORC_VARIANT_MANY_WOLVES)
+  if (w->variant & ORC_VARIANT_MANY_WOLVES)
     wolves_eat_many(w, st);
   else
     wolves_eat(w, st);

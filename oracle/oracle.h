@@ -82,10 +82,12 @@ orc_world* orc_pred_create(int32_t side, uint32_t seed, uint32_t model, const in
                            const int32_t cap[2], const int32_t n0[2]);
 void orc_pred_free(orc_world* w);
 void orc_pred_step(orc_world* w, orc_stats* st);
-/* Rule variant of a world: ORC_VARIANT_ONE_WOLF (default, at most one wolf
- * eats per cell per step) or ORC_VARIANT_MANY_WOLVES (the i-th wolf of a cell
- * eats its i-th sheep, both ordered by their keys). */
-enum { ORC_VARIANT_ONE_WOLF = 0, ORC_VARIANT_MANY_WOLVES = 1 };
+/* Rule variants of a world, as bits (0 = the default rules):
+ * ORC_VARIANT_MANY_WOLVES: the i-th wolf of a cell eats its i-th sheep, both
+ *   ordered by their keys (default: at most one wolf eats per cell per step);
+ * ORC_VARIANT_GRASS_OFF: sheep neither eat grass nor spend energy moving
+ *   (Wilensky's model without grass). */
+enum { ORC_VARIANT_ONE_WOLF = 0, ORC_VARIANT_MANY_WOLVES = 1, ORC_VARIANT_GRASS_OFF = 2 };
 void orc_pred_set_variant(orc_world* w, int32_t variant);
 /* which: 0 active, 1 cell, 2 energy, 3 id, 4 age */
 int32_t* orc_pred_agents(orc_world* w, int species, int which);

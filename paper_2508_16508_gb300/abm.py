@@ -45,7 +45,7 @@ class abm_pred(C.Structure):
                 ("value", C.c_int32)]
 
 
-VARIANT_ONE_WOLF, VARIANT_MANY_WOLVES = 0, 1
+VARIANT_ONE_WOLF, VARIANT_MANY_WOLVES, VARIANT_GRASS_OFF = 0, 1, 2  # bits
 
 
 class abm_config(C.Structure):

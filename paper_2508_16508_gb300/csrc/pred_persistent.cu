@@ -137,7 +137,7 @@ __device__ __forceinline__ void list_push(u64* head, u64* next, u64* keys, int c
 template <int S>
 __device__ __forceinline__ int4 move_one(const WorldDev& w, int t, int slot, int4 ag, int L, int metab) {
   const SpeciesDev& sp = w.sp[S];
-  if (S == 0 && w.variant == ABM_VARIANT_ONE_WOLF) w.victim[ag.x] = kNoKey;  // last step's victim entry here
+  if (S == 0 && !(w.variant & ABM_VARIANT_MANY_WOLVES)) w.victim[ag.x] = kNoKey;  // last step's victim entry here
   const u32 dir = draw(w.seed, w.model, (u32)t, (u32)slot, ABM_P_MOVE, (u32)S) >> 29;
   const int cell = step_cell(ag.x, L, dir);
   ag.x = cell;
@@ -145,11 +145,11 @@ __device__ __forceinline__ int4 move_one(const WorldDev& w, int t, int slot, int
   ag.w += 1;
   sp.agent[slot] = ag;
   if (S == 0) {
-    if (w.regrow[cell] <= t)
+    if (!(w.variant & ABM_VARIANT_GRASS_OFF) && w.regrow[cell] <= t)
       atomicMin(&w.gclaim[cell], claim_key(draw(w.seed, w.model, (u32)t, (u32)slot, ABM_P_PRIO, 0u), slot));
   } else {
     const u64 key = claim_key(draw(w.seed, w.model, (u32)t, (u32)slot, ABM_P_PRIO, 1u), slot);
-    if (w.variant == ABM_VARIANT_MANY_WOLVES)  // every wolf joins its cell's list
+    if (w.variant & ABM_VARIANT_MANY_WOLVES)  // every wolf joins its cell's list
       list_push(w.wclaim, w.wnext, w.wkey, cell, slot, t, key);
     else if (w.victim[cell] != kNoKey)
       atomicMin(&w.wclaim[cell], key);
@@ -183,7 +183,8 @@ __device__ __forceinline__ void p_move(const WorldDev& w, int t, int ext, const 
   carried = -1;
   const SpeciesDev& sp = w.sp[S];
   const int L = w.side;
-  const int metab = w.params[PRM_SHEEP_METAB + S];
+  // without grass (variant) sheep neither spend energy nor claim grass
+  const int metab = (S == 0 && (w.variant & ABM_VARIANT_GRASS_OFF)) ? 0 : w.params[PRM_SHEEP_METAB + S];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nblk = (ext + 127) >> 7;
   for (int round = 0; unit_at(0, round) < nblk; ++round) {
@@ -264,7 +265,7 @@ __device__ __forceinline__ u32 count_one(const WorldDev& w, int t, int slot, int
   const SpeciesDev& sp = w.sp[S];
   const int cell = ag.x;
   u32 r = 0;
-  if (S == 1 && w.variant == ABM_VARIANT_MANY_WOLVES) {
+  if (S == 1 && (w.variant & ABM_VARIANT_MANY_WOLVES)) {
     if (eat_rank_matched(w, t, slot, cell)) {
       ag.y += gain;
       sp.agent[slot].y = ag.y;
@@ -291,7 +292,7 @@ __device__ __forceinline__ u32 count_one(const WorldDev& w, int t, int slot, int
     if (draw(w.seed, w.model, (u32)t, (u32)slot, ABM_P_REPRO, (u32)S) < Tr) r |= 1u;
     if (S == 0) {
       const u64 key = claim_key(draw(w.seed, w.model, (u32)t, (u32)slot, ABM_P_VICTIM, 0u), slot);
-      if (w.variant == ABM_VARIANT_MANY_WOLVES)
+      if (w.variant & ABM_VARIANT_MANY_WOLVES)
         list_push(w.victim, w.snext, w.skey, cell, slot, t, key);
       else
         atomicMin(&w.victim[cell], key);
@@ -616,7 +617,7 @@ __device__ __forceinline__ void p_births(const WorldDev& w, int t, int r, int F,
     sp.active[slot] = 1;
     if (S == 0) {
       const u64 key = claim_key(draw(w.seed, w.model, (u32)t, (u32)slot, ABM_P_VICTIM, 0u), slot);
-      if (w.variant == ABM_VARIANT_MANY_WOLVES)
+      if (w.variant & ABM_VARIANT_MANY_WOLVES)
         list_push(w.victim, w.snext, w.skey, pa.x, slot, t, key);
       else
         atomicMin(&w.victim[pa.x], key);

@@ -339,7 +339,7 @@ extern "C" abm_status abm_create(const abm_config* cfg, void* stream, abm_world*
     if (cfg->params[s] < 0 || cfg->params[5 + s] < 0) return ABM_ERR_ARG;
   }
   if (cfg->params[4] < 1) return ABM_ERR_ARG;
-  if (cfg->variant != ABM_VARIANT_ONE_WOLF && cfg->variant != ABM_VARIANT_MANY_WOLVES) return ABM_ERR_ARG;
+  if (cfg->variant & ~(ABM_VARIANT_MANY_WOLVES | ABM_VARIANT_GRASS_OFF)) return ABM_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   abm_world* w = new (std::nothrow) abm_world();
   if (!w) return ABM_ERR_OOM;
@@ -387,7 +387,7 @@ extern "C" abm_status abm_create(const abm_config* cfg, void* stream, abm_world*
          cudaMalloc(&d.ps.seg[s], sizeof(u64) * (size_t)pmax) == cudaSuccess &&
          cudaMemsetAsync(d.ps.seg[s], 0, sizeof(u64) * (size_t)pmax, st) == cudaSuccess;
   }
-  if (d.variant == ABM_VARIANT_MANY_WOLVES) {
+  if (d.variant & ABM_VARIANT_MANY_WOLVES) {
     ok = ok && cudaMalloc(&d.skey, sizeof(u64) * (size_t)cfg->cap[0]) == cudaSuccess;
     ok = ok && cudaMalloc(&d.snext, sizeof(u64) * (size_t)cfg->cap[0]) == cudaSuccess;
     ok = ok && cudaMalloc(&d.wkey, sizeof(u64) * (size_t)cfg->cap[1]) == cudaSuccess;

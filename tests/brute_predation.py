@@ -14,15 +14,16 @@ MOVES = {0: (-1, -1), 1: (0, -1), 2: (1, -1), 3: (-1, 0), 4: (1, 0), 5: (-1, 1),
 
 
 class BruteWorld:
-    def __init__(self, side, seed, model, params, cap, n0, many_wolves=False):
+    def __init__(self, side, seed, model, params, cap, n0, many_wolves=False, grass_off=False):
         self.L = side
         self.many_wolves = many_wolves
+        self.grass_off = grass_off
         self.seed, self.model = seed, model
         self.p = [int(x) & 0xFFFFFFFF for x in params]
         self.gain = [self.p[0], self.p[1]]
         self.T = [self.p[2], self.p[3]]
         self.regrowth = self.p[4] if self.p[4] < 2**31 else self.p[4] - 2**32
-        self.metab = [self.p[5], self.p[6]]
+        self.metab = [0 if grass_off else self.p[5], self.p[6]]
         self.cap = list(cap)
         self.t = 0
         self.next_id = list(n0)
@@ -87,7 +88,7 @@ class BruteWorld:
         self.move(0)
         claims = {}
         for slot, a in self.agents[0].items():
-            if self.grass[(a["x"], a["y"])]["grown"]:
+            if self.grass[(a["x"], a["y"])]["grown"] and not self.grass_off:
                 claims.setdefault((a["x"], a["y"]), []).append((self.draw(slot, oracle.P_PRIO, 0), slot))
         for cell, c in claims.items():
             winner = sorted(c)[0][1]

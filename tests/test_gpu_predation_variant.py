@@ -1,7 +1,8 @@
-"""GPU parity of the several-wolves-per-cell variant (the i-th wolf of a cell,
-by (PRIO draw, slot), eats the i-th sheep, by (VICTIM draw, slot)) against the
-oracle's variant, which is itself pinned by the list-of-agents simulator.
-Whole state every step, bit for bit."""
+"""GPU parity of the rule variants against the oracle's (which are pinned by
+the list-of-agents simulator): several wolves per cell (the i-th wolf of a
+cell, by (PRIO draw, slot), eats the i-th sheep, by (VICTIM draw, slot)),
+grass off (sheep neither eat nor spend energy), and both. Whole state, bit
+for bit."""
 import numpy as np
 import pytest
 
@@ -21,18 +22,22 @@ def eng():
     return engine
 
 
-def make(eng, c, cps=2):
+MANY, OFF = oracle.VARIANT_MANY_WOLVES, oracle.VARIANT_GRASS_OFF
+VARIANTS = [MANY, OFF, MANY | OFF]
+
+
+def make(eng, c, cps=2, variant=MANY):
     from paper_2508_16508_gb300 import abm
-    gw = eng.World(c["side"], c["seed"], c["model"], c["params"], c["cap"], c["n0"], variant=abm.VARIANT_MANY_WOLVES)
+    gw = eng.World(c["side"], c["seed"], c["model"], c["params"], c["cap"], c["n0"], variant=variant)
     gw.tune(abm.ENGINE_PERSISTENT, cps)
-    ow = oracle.World(c["side"], c["seed"], c["model"], c["params"], c["cap"], c["n0"],
-                      variant=oracle.VARIANT_MANY_WOLVES)
+    ow = oracle.World(c["side"], c["seed"], c["model"], c["params"], c["cap"], c["n0"], variant=variant)
     return gw, ow
 
 
-def test_small_config_every_step(eng):
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_small_config_every_step(eng, variant):
     c = workloads.PRED_SMALL
-    gw, ow = make(eng, c)
+    gw, ow = make(eng, c, variant=variant)
     stats = gw.new_stats(1)
     eaten = 0
     for t in range(c["steps"]):
@@ -41,6 +46,8 @@ def test_small_config_every_step(eng):
         compare_stats(eng.decode_stats(stats)[0], ost, energy=False)
         compare_state(gw, ow, f"step {t}")
         eaten += ost["eaten"]
+        if variant & OFF:
+            assert ost["grass_eaten"] == 0
     assert eaten > 0
     gw.check()
 
@@ -57,7 +64,7 @@ def test_crowded_random_worlds(eng, seed):
         sheep_repro=float(rng.choice([0.0, 0.04, 0.3, 0.9])), wolf_repro=float(rng.choice([0.0, 0.05, 0.5])),
         regrowth=int(rng.integers(1, 40)), grass_init=float(rng.choice([0.1, 0.5, 0.95])))
     c = dict(side=side, n0=n0, cap=cap, seed=seed, model=int(rng.integers(0, 1000)), params=params)
-    gw, ow = make(eng, c)
+    gw, ow = make(eng, c, variant=VARIANTS[seed % 3])
     stats = gw.new_stats(60)
     for k in range(3):
         gw.step(20, stats[20 * k:20 * (k + 1)])

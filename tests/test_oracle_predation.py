@@ -55,9 +55,12 @@ def test_brute_force_tiny_worlds(seed):
 
 @pytest.mark.parametrize("seed", range(60))
 def test_brute_force_tiny_worlds_many_wolves(seed):
-    """The several-wolves-per-cell variant against the list-of-agents
-    simulator: tiny, crowded worlds so that cells often hold several wolves."""
+    """The rule variants (several wolves per cell, grass off, both) against
+    the list-of-agents simulator: tiny, crowded worlds so that cells often
+    hold several wolves."""
     rng = np.random.default_rng(3000 + seed)
+    variant = [oracle.VARIANT_MANY_WOLVES, oracle.VARIANT_GRASS_OFF,
+               oracle.VARIANT_MANY_WOLVES | oracle.VARIANT_GRASS_OFF][seed % 3]
     side = int(rng.integers(1, 5))
     cap = (int(rng.integers(1, 30)), int(rng.integers(1, 20)))
     n0 = (int(rng.integers(0, cap[0] + 1)), int(rng.integers(0, cap[1] + 1)))
@@ -65,8 +68,9 @@ def test_brute_force_tiny_worlds_many_wolves(seed):
         sheep_gain=int(rng.integers(1, 6)), wolf_gain=int(rng.integers(2, 25)),
         sheep_repro=float(rng.choice([0.04, 0.2, 0.5])), wolf_repro=float(rng.choice([0.05, 0.2, 0.5])),
         regrowth=int(rng.integers(1, 12)), grass_init=float(rng.choice([0.25, 0.5, 0.9])))
-    ow = oracle.World(side, seed, 7, params, cap, n0, variant=oracle.VARIANT_MANY_WOLVES)
-    bw = BruteWorld(side, seed, 7, params, cap, n0, many_wolves=True)
+    ow = oracle.World(side, seed, 7, params, cap, n0, variant=variant)
+    bw = BruteWorld(side, seed, 7, params, cap, n0, many_wolves=bool(variant & oracle.VARIANT_MANY_WOLVES),
+                    grass_off=bool(variant & oracle.VARIANT_GRASS_OFF))
     compare(ow, bw)
     for _ in range(40):
         st = ow.step()[0]
@@ -90,6 +94,18 @@ def test_many_wolves_single_cell_eat_min():
         one = oracle.World(1, 11, 0, params, (16, 16), n0)  # default: one wolf eats per cell
         st = one.step()[0]
         assert st["eaten"] == min(1, st["n_start"][0] - st["starved"][0], st["n_start"][1])
+
+
+def test_grass_off_sheep_alone_keep_their_energy():
+    """Without grass, wolves and reproduction, sheep never gain, spend or lose
+    energy: every sheep keeps its initial energy and none dies."""
+    params = workloads.predation_params(sheep_repro=0.0, wolf_repro=0.0)
+    ow = oracle.World(12, 5, 0, params, (300, 10), (200, 0), variant=oracle.VARIANT_GRASS_OFF)
+    e0 = ow.agents(0, "energy").copy()
+    for st in ow.step(30):
+        assert st["grass_eaten"] == 0 and st["starved"] == [0, 0] and st["n_end"][0] == 200
+    np.testing.assert_array_equal(ow.agents(0, "energy"), e0)
+    np.testing.assert_array_equal(ow.agents(0, "age")[:200], np.full(200, 30))
 
 
 def check_invariants(before, after, st, counters_before, counters_after, params, ncells):
