@@ -296,6 +296,28 @@ def selective_update_leg(torch, engine, abm, autotune, hbm_peak, steps=8, warmup
                        "launch": f"{tuned['threads']} threads x {tuned['ctas_per_sm']} CTAs/SM"
                                  + (" (autotuned)" if tune else "")}
         del s, rec, dl
+    # sort_agents on the same slab shape: live agents first, ascending by one field
+    s = engine.Slab(n, F, seed=c["seed"], init=abm.INIT_HALF_LIVE)
+    times = []
+    for it in range(warmup + steps):
+        flush.max()
+        torch.cuda._sleep(100000)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        s.sort(it % F)
+        e1.record()
+        e1.synchronize()
+        if it >= warmup:
+            times.append(e0.elapsed_time(e1))
+    s.check()
+    del s
+    ms = statistics.median(times)
+    # per slot: key + value built (read flag + key field, write 8 B), five passes of
+    # (histogram read 8 B, scatter read 8 B + write 8 B), the row gather (read + write 4 + 32 B)
+    b = n * (8 + 8 + 5 * 24 + 2 * (4 + 4 * F))
+    out["sort_agents"] = {"ms": ms, "algorithmic_bytes": b, "gbs": b / (ms * 1e-3) / 1e9,
+                          "frac": b / (ms * 1e-3) / 1e9 / hbm_peak,
+                          "method": "LSD radix sort, 4 key-byte passes + 1 live-flag pass, then the row gather"}
     # conflict pass: M = N/4 claims over R = N/64 resources, Zipf(1.1)
     M, R = n // 4, n // 64
     res = torch.from_numpy(workloads.zipf_claims(M, R, s=c["zipf_s"], seed=c["zipf_seed"])).cuda()

@@ -91,7 +91,8 @@ abm_status abm_slab_create(int32_t capacity, int32_t n_fields, uint32_t seed, ui
 abm_status abm_slab_destroy(abm_slab* s);
 /* Synchronises `stream`, then reports any device-side error recorded for the slab. */
 abm_status abm_slab_check(abm_slab* s, void* stream);
-/* Device pointers to the slab's arrays (valid until destroy). */
+/* Device pointers to the slab's arrays (valid until destroy or abm_sort,
+ * which replaces them). */
 abm_status abm_slab_arrays(abm_slab* s, int32_t** active, int32_t** fields, int32_t* fields_stride);
 /* Copy `n` slots starting at slot 0 of field `field` (or the live flags for
  * field = -1) into / out of a device buffer of n int32. */
@@ -120,6 +121,17 @@ typedef struct abm_pred {
  * *out_count (device int32, required). Stable stream compaction. */
 abm_status abm_select(abm_slab* s, const abm_pred* pred, int32_t* out_idx, int32_t* out_count,
                       void* stream);
+
+/* sort_agents (Section 2 API list): reorder the slab so that the live agents
+ * come first, ascending by the int32 `field` (signed order; ties keep their
+ * slot order), and the placeholders after them in slot order. Every row
+ * moves whole (all fields and the live flag); counters are unchanged.
+ * out_perm (device int32[capacity], nullable): out_perm[i] = the old slot of
+ * the row now in slot i. The first call allocates the sort's buffers (about
+ * 16 bytes a slot plus one spare copy of the slab, kept until destroy); the
+ * slab's arrays are replaced by the sorted copies (abm_slab_arrays changes).
+ * LSD radix sort: four passes over the key bytes and one over the live flag. */
+abm_status abm_sort(abm_slab* s, int32_t field, int32_t* out_perm, void* stream);
 
 /* select_agents with SCI's index exposure (Algorithm 2, Section 4): a
  * permutation of all slots, those satisfying `pred` first, then the others,

@@ -90,6 +90,7 @@ def lib():
             L.orc_c1_records.argtypes = [C.c_uint32] * 5 + [C.c_int64, C.c_int, i32p]
             L.orc_c1_call.argtypes = [i32p, i32p, C.c_int64, C.c_int, C.c_uint32, C.c_uint32,
                                       C.c_uint32, C.c_uint32, C.c_int64, i64p]
+            L.orc_sort.argtypes = [i32p, i32p, C.c_int64, C.c_int, C.c_int, i32p]
             L.orc_pred_create.argtypes = [C.c_int32, C.c_uint32, C.c_uint32, i32p, i32p, i32p]
             L.orc_pred_create.restype = C.c_void_p
             L.orc_pred_free.argtypes = [C.c_void_p]
@@ -158,6 +159,14 @@ class Slab:
         self.n, self.F = int(n), int(F)
         self.active = np.zeros(self.n, dtype=np.int32)
         self.fields = np.zeros((self.F, self.n), dtype=np.int32)
+
+    def sort(self, field: int) -> np.ndarray:
+        """sort_agents: live agents first ascending by fields[field], then the
+        placeholders; returns the permutation (old slot of each new slot)."""
+        perm = np.zeros(max(self.n, 1), dtype=np.int32)
+        lib().orc_sort(_p(self.active, C.c_int32), _p(self.fields, C.c_int32), self.n, self.F, int(field),
+                       _p(perm, C.c_int32))
+        return perm[:self.n].copy()
 
     def remove(self, mask) -> int:
         m = _i32(mask)

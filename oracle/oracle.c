@@ -207,6 +207,41 @@ void orc_c1_call(int32_t* active, int32_t* fields, int64_t n, int F, uint32_t se
   free(rec);
 }
 
+/* sort_agents (Section 2 API list): the live agents first, ascending by the
+ * signed int32 `field` with ties in slot order, then the placeholders in slot
+ * order; every row (live flag and all fields) moves whole. fields is F rows
+ * of n. perm[i] = the old slot of the row placed in slot i. */
+typedef struct {
+  int32_t placeholder, key, slot;
+} orc_sortkey;
+
+static int cmp_sortkey(const void* a, const void* b) {
+  const orc_sortkey* x = (const orc_sortkey*)a;
+  const orc_sortkey* y = (const orc_sortkey*)b;
+  if (x->placeholder != y->placeholder) return x->placeholder < y->placeholder ? -1 : 1;
+  if (x->key != y->key) return x->key < y->key ? -1 : 1;
+  return x->slot < y->slot ? -1 : x->slot > y->slot;
+}
+
+void orc_sort(int32_t* active, int32_t* fields, int64_t n, int F, int field, int32_t* perm) {
+  orc_sortkey* k = (orc_sortkey*)malloc(sizeof(orc_sortkey) * (size_t)(n > 0 ? n : 1));
+  int32_t* tmp = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  for (int64_t i = 0; i < n; i++) {
+    k[i].placeholder = active[i] ? 0 : 1;
+    k[i].key = active[i] ? fields[(int64_t)field * n + i] : 0;
+    k[i].slot = (int32_t)i;
+  }
+  qsort(k, (size_t)n, sizeof(orc_sortkey), cmp_sortkey);
+  for (int64_t i = 0; i < n; i++) perm[i] = k[i].slot;
+  for (int f = -1; f < F; f++) {
+    int32_t* row = f < 0 ? active : fields + (int64_t)f * n;
+    for (int64_t i = 0; i < n; i++) tmp[i] = row[perm[i]];
+    memcpy(row, tmp, sizeof(int32_t) * (size_t)n);
+  }
+  free(k);
+  free(tmp);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Predation (Section 5.1 and Fig. 3: grass, sheep and wolves on a periodic
  * 2-D lattice; random moves; sheep eat grass, wolves eat sheep; grass regrows

@@ -77,6 +77,11 @@ typedef struct orc_stats {
   int64_t energy[2];    /* sum of live energy at the end of the step */
 } orc_stats;
 
+/* sort_agents: live agents first ascending by fields[field] (signed, ties in
+ * slot order), then the placeholders in slot order; rows move whole. fields
+ * is F rows of n; perm[i] = old slot of new slot i. */
+void orc_sort(int32_t* active, int32_t* fields, int64_t n, int F, int field, int32_t* perm);
+
 typedef struct orc_world orc_world;
 orc_world* orc_pred_create(int32_t side, uint32_t seed, uint32_t model, const int32_t params[8],
                            const int32_t cap[2], const int32_t n0[2]);

@@ -108,6 +108,7 @@ def _sig(L):
         "abm_slab_write": ([vp, i32, vp, i32, vp], st),
         "abm_select": ([vp, C.POINTER(abm_pred), vp, vp, vp], st),
         "abm_select_permutation": ([vp, C.POINTER(abm_pred), vp, vp, vp], st),
+        "abm_sort": ([vp, i32, vp, vp], st),
         "abm_remove": ([vp, C.POINTER(abm_pred), vp, vp], st),
         "abm_add": ([vp, vp, i32, i32, vp, vp, vp], st),
         "abm_update_distinct": ([vp, C.POINTER(abm_pred), vp, vp, i32, i32, vp, vp, vp], st),

@@ -1,20 +1,21 @@
 // Generic fixed-capacity agent set ("Set", ABMax Section 2) and the selection /
-// compaction / distinct-update primitives of Section 4 (Algorithms 1 and 2),
-// plus per-resource conflict resolution.
+// compaction / distinct-update primitives of Section 4 (Algorithms 1 and 2).
 //
-// Every rank-matched operation is ONE pass over the slab: each CTA takes a
-// tile, computes per-slot flags from the 128-bit loaded live flags, ranks them
-// with a block scan plus a decoupled look-back, and scatters the records at
-// those ranks while the tile is still in registers. The i-th selected slot
-// receiving the i-th record is exactly Rank-Match's pairing (cumsum(mask) *
-// mask on both sides, matched on equal nonzero ranks), computed in O(n + k)
-// instead of O(n * k).
+// Every rank-matched operation is count -> scatter -> apply over a static
+// partition of the slab: pass 1 evaluates the per-slot flags (from 128-bit
+// loads of live flags) into bit-planes and per-warp / per-CTA counts; pass 2
+// turns a slot's position into its rank (prefix of the CTA counts + prefix of
+// the warp counts + a warp scan) and writes rank-ordered slot lists; pass 3
+// moves the records. The i-th selected slot receiving the i-th record is
+// exactly Rank-Match's pairing (cumsum(mask) * mask on both sides, matched on
+// equal nonzero ranks), computed in O(n + k) instead of O(n * k). The passes
+// are chained with programmatic dependent launch; no pass spins on another CTA.
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <new>
 
-#include "common.cuh"
+#include "slab.cuh"
 
 namespace abm {
 
@@ -30,19 +31,9 @@ int num_sms() {
 }
 
 constexpr int kSlabThreads = 256;    // default CTA size of the slab passes
-constexpr int kSlabTileMax = 16384;  // slab arrays are padded to a multiple of this
 constexpr int kMaxFields = 16;
 
-struct SlabDev {
-  int32_t* active;
-  int32_t* fields;   // cap x Fp, agent-major
-  int32_t* counters; // [0] n_active [1] next_id [2] overflow [3] scratch count
-  int32_t* rec_idx;  // [cap] compacted record indices (scratch)
-  int32_t* meta;     // [4] pass-2 results for pass 3: rank counts, first id
-  int* err;
-  int cap, F, Fp;
-  u32 seed, model;
-};
+
 
 struct PredDev {
   int kind;
@@ -528,22 +519,7 @@ __global__ void k_philox_records(SlabDev s, u32 step, u32 p0, u32 p1, int k, int
 // host side
 using namespace abm;
 
-struct abm_slab {
-  SlabDev d;
-  u32* planes;    // 2 x n_pad / 32 words: bit-planes A, B of the slab passes
-  u32* planes2;   // n_pad / 32 words: plane A of record-mask compaction
-  u32* totals;    // [2 * max CTAs] per-CTA counts (slab passes)
-  u32* totals2;   // the same for record-mask compaction
-  u32* wtotals;   // [2 * max CTAs * 16 warps] per-warp counts
-  u32* wtotals2;
-  int32_t* lista;  // [cap] scratch slot lists when the caller wants none
-  int32_t* listb;
-  u32* ctrl;      // [0..4) slab passes, [4..8) record-mask compaction
-  int n_pad;
-  int max_ctas;
-  // shape of the fused selective-update pass (abm_slab_tune)
-  int fused_threads, fused_ctas_per_sm;
-};
+
 
 extern "C" const char* abm_strerror(abm_status st) {
   switch (st) {
@@ -578,6 +554,7 @@ extern "C" abm_status abm_slab_destroy(abm_slab* s) {
   cudaFree(s->listb);
   cudaFree(s->d.meta);
   cudaFree(s->ctrl);
+  sort_scratch_free(s->sort);
   delete s;
   return ABM_OK;
 }

@@ -1,0 +1,42 @@
+// Device and host state of a slab (a fixed-capacity agent set), shared by the
+// slab passes (slab.cu) and the slab sort (sort.cu).
+#pragma once
+#include "common.cuh"
+
+namespace abm {
+
+constexpr int kSlabTileMax = 16384;  // slab arrays are padded to a multiple of this
+
+struct SlabDev {
+  int32_t* active;
+  int32_t* fields;   // cap x Fp, agent-major
+  int32_t* counters; // [0] n_active [1] next_id [2] overflow [3] scratch count
+  int32_t* rec_idx;  // [cap] compacted record indices (scratch)
+  int32_t* meta;     // [4] pass-2 results for pass 3: rank counts, first id
+  int* err;
+  int cap, F, Fp;
+  u32 seed, model;
+};
+
+struct SortScratch;
+void sort_scratch_free(SortScratch* p);
+
+}  // namespace abm
+
+struct abm_slab {
+  abm::SlabDev d;
+  abm::u32* planes;    // 2 x n_pad / 32 words: bit-planes A, B of the slab passes
+  abm::u32* planes2;   // n_pad / 32 words: plane A of record-mask compaction
+  abm::u32* totals;    // [2 * max CTAs] per-CTA counts (slab passes)
+  abm::u32* totals2;   // the same for record-mask compaction
+  abm::u32* wtotals;   // [2 * max CTAs * 16 warps] per-warp counts
+  abm::u32* wtotals2;
+  int32_t* lista;  // [cap] scratch slot lists when the caller wants none
+  int32_t* listb;
+  abm::u32* ctrl;      // [0..4) slab passes, [4..8) record-mask compaction
+  int n_pad;
+  int max_ctas;
+  // shape of the fused selective-update pass (abm_slab_tune)
+  int fused_threads, fused_ctas_per_sm;
+  abm::SortScratch* sort;  // buffers of abm_sort, allocated by its first call
+};

@@ -76,6 +76,13 @@ class Slab:
         call("abm_select_permutation", self.h, C.byref(p), ptr(perm), ptr(cnt), _stream(stream))
         return perm, cnt
 
+    def sort(self, field: int, stream=None) -> torch.Tensor:
+        """sort_agents: live agents first, ascending by `field` (stable), then the
+        placeholders; returns the permutation (old slot of each new slot)."""
+        perm = torch.empty(self.capacity, **self._i32)
+        call("abm_sort", self.h, int(field), ptr(perm), _stream(stream))
+        return perm
+
     def remove(self, p: abm.abm_pred, stream=None) -> torch.Tensor:
         cnt = torch.zeros(1, **self._i32)
         call("abm_remove", self.h, C.byref(p), ptr(cnt), _stream(stream))

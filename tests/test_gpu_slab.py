@@ -170,6 +170,53 @@ def test_select_permutation(eng, n):
     s.check()
 
 
+@pytest.mark.parametrize("n", [1, 33, 2049, 4096 * 3 + 17, 100_003])
+def test_sort_agents(eng, n):
+    """sort_agents vs the oracle: whole state and permutation, keys with many
+    ties (stability) and full-range keys, twice in a row (the second call
+    sorts by another field and reuses the buffers)."""
+    F = 5
+    rng = np.random.default_rng(n)
+    s = eng.Slab(n, F, seed=4, init=1)
+    o = oracle.Slab(n, F)
+    o.c1_init(seed=4)
+    ties = rng.integers(-3, 4, size=n).astype(np.int32)
+    s.write(1, torch.from_numpy(ties).cuda())
+    o.fields[1] = ties
+    for field in (1, 3, 0):
+        perm = np_of(s.sort(field))
+        want = o.sort(field)
+        np.testing.assert_array_equal(perm, want)
+        act, fld = slab_state(s)
+        np.testing.assert_array_equal(act, o.active)
+        np.testing.assert_array_equal(fld, o.fields)
+    assert s.counters()["n_active"] == int(o.active.sum())
+    s.check()
+
+
+def test_sort_agents_full_size(eng):
+    """2^24 slots x 8 fields (the selective-update slab), after three
+    selective-update calls; sorted by two fields."""
+    from paper_2508_16508_gb300 import abm
+    c = workloads.SELECTIVE
+    n, F, p = c["n"], c["F"], 0.05
+    T, k = workloads.threshold(p), workloads.k_for(p, n)
+    s = eng.Slab(n, F, seed=c["seed"], init=1)
+    o = oracle.Slab(n, F)
+    o.c1_init(seed=c["seed"])
+    for step in range(3):
+        rec = s.philox_records(step, abm.P_NEWREC0, abm.P_NEWREC1, k)
+        dl = s.philox_records(step, abm.P_DELTA0, abm.P_DELTA1, k)
+        s.selective_update(step, T, rec, dl)
+        o.c1_call(step, T, k, seed=c["seed"])
+    for field in (2, 7):
+        np.testing.assert_array_equal(np_of(s.sort(field)), o.sort(field))
+    act, fld = slab_state(s)
+    np.testing.assert_array_equal(act, o.active)
+    np.testing.assert_array_equal(fld, o.fields)
+    s.check()
+
+
 @pytest.mark.parametrize("n", [5, 2049, 7000])
 def test_add_remove_update_vs_oracle(eng, n):
     from paper_2508_16508_gb300 import abm

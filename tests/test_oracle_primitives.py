@@ -240,3 +240,27 @@ def test_c1_call_matches_numpy_restatement(n, p):
         assert (cnt["removed"], cnt["added"], cnt["updated"]) == (rm, ra, ru)
         np.testing.assert_array_equal(s.active, act)
         np.testing.assert_array_equal(s.fields, fld)
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_sort_agents_vs_numpy_and_brute_force(seed):
+    """sort_agents against numpy's stable lexsort and a Python sorted() on
+    tuples (placeholder flag, key, slot); rows move whole."""
+    rng = np.random.default_rng(70 + seed)
+    n, F = int(rng.integers(0, 300)), int(rng.integers(1, 5))
+    o = oracle.Slab(n, F)
+    o.active[:] = rng.random(n) < rng.random()
+    o.fields[:] = rng.integers(-5, 6, size=(F, n)) if seed % 2 else rng.integers(-2**31, 2**31, size=(F, n))
+    field = int(rng.integers(0, F))
+    act0, fld0 = o.active.copy(), o.fields.copy()
+    perm = o.sort(field)
+    key = np.where(act0 != 0, fld0[field], 0)
+    want = np.lexsort((np.arange(n), key, act0 == 0))  # last key sorts first
+    np.testing.assert_array_equal(perm, want)
+    brute = [s for _, _, s in sorted((0 if act0[i] else 1, int(key[i]), i) for i in range(n))]
+    assert perm.tolist() == brute
+    np.testing.assert_array_equal(o.active, act0[perm])
+    np.testing.assert_array_equal(o.fields, fld0[:, perm])
+    live = int((act0 != 0).sum())
+    assert (o.active[:live] != 0).all() and (o.active[live:] == 0).all()
+    assert (np.diff(o.fields[field][:live].astype(np.int64)) >= 0).all()
