@@ -61,118 +61,173 @@ struct MCtx {
   int n_start[2], P[2], F[2], starved[2], eaten, grass;
 };
 
+// Live agents of a chunk of 16 * T slots, listed in shared memory (offsets
+// within the chunk, in the order of the threads' masks) so that all T threads
+// share the work whatever the chunk's density. m = the thread's 16-bit live
+// mask over slots base16[j]; returns the list's length.
 template <int T>
-__device__ __forceinline__ void b_move(const BatchDev& b, MCtx& c, int S, int sweep, int t) {
-  const int32_t* act = b.active[S] + c.m.oa[S];
+__device__ __forceinline__ int chunk_list(u32 m, int first_off, int stride_off, unsigned short* s_list, u64* s_warp) {
+  u32 ex, ex2, tot, tot2;
+  block_scan2<T>((u32)__popc(m), 0u, ex, ex2, tot, tot2, s_warp);
+  u32 pos = ex;
+  while (m) {
+    const int j = __ffs(m) - 1;
+    m &= m - 1;
+    s_list[pos++] = (unsigned short)(first_off + j * stride_off);
+  }
+  __syncthreads();
+  return (int)tot;
+}
+
+template <int T>
+__device__ __forceinline__ void move_agent(const BatchDev& b, const MCtx& c, int S, int t, int slot, int4 a) {
   int4* ag = b.agent[S] + c.m.oa[S];
   u64* victim = b.victim + c.m.oc;
-  const int L = c.m.side;
-  const int metab = c.m.prm[PRM_SHEEP_METAB + S];
-  const int nq = (sweep + 3) >> 2;
-  // four 128-bit loads of live flags in flight per thread, then the work
-  for (int q0 = threadIdx.x; q0 < nq; q0 += 4 * T) {
-    int4 a4v[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int q = q0 + u * T;
-      a4v[u] = q < nq ? reinterpret_cast<const int4*>(act)[q] : make_int4(0, 0, 0, 0);
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int a4[4] = {a4v[u].x, a4v[u].y, a4v[u].z, a4v[u].w};
-      if (!(a4[0] | a4[1] | a4[2] | a4[3])) continue;
-      const int q = q0 + u * T;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        if (!a4[j]) continue;
-        const int slot = 4 * q + j;
-        int4 a = ag[slot];
-        if (S == 0) victim[a.x] = kNoKey;
-        const u32 dir = draw(c.m.seed, c.m.model, (u32)t, (u32)slot, ABM_P_MOVE, (u32)S) >> 29;
-        const int cell = step_cell(a.x, L, dir);
-        a.x = cell;
-        a.y -= metab;
-        a.w += 1;
-        ag[slot] = a;
-        if (S == 0) {
-          if (b.regrow[c.m.oc + cell] <= t)
-            atomicMin(&b.gclaim[c.m.oc + cell], claim_key(draw(c.m.seed, c.m.model, (u32)t, (u32)slot, ABM_P_PRIO, 0u), slot));
-        } else {
-          if (victim[cell] != kNoKey)
-            atomicMin(&b.wclaim[c.m.oc + cell], claim_key(draw(c.m.seed, c.m.model, (u32)t, (u32)slot, ABM_P_PRIO, 1u), slot));
-        }
-      }
-    }
+  if (S == 0) victim[a.x] = kNoKey;
+  const u32 dir = draw(c.m.seed, c.m.model, (u32)t, (u32)slot, ABM_P_MOVE, (u32)S) >> 29;
+  const int cell = step_cell(a.x, c.m.side, dir);
+  a.x = cell;
+  a.y -= c.m.prm[PRM_SHEEP_METAB + S];
+  a.w += 1;
+  ag[slot] = a;
+  if (S == 0) {
+    if (b.regrow[c.m.oc + cell] <= t)
+      atomicMin(&b.gclaim[c.m.oc + cell], claim_key(draw(c.m.seed, c.m.model, (u32)t, (u32)slot, ABM_P_PRIO, 0u), slot));
+  } else {
+    if (victim[cell] != kNoKey)
+      atomicMin(&b.wclaim[c.m.oc + cell], claim_key(draw(c.m.seed, c.m.model, (u32)t, (u32)slot, ABM_P_PRIO, 1u), slot));
   }
 }
 
-// eat (claim winners), select parents, kill the starving, compact the free
-// slots and the parents (ranks by block scans, chunk by chunk)
 template <int T>
-__device__ __forceinline__ void b_scan(const BatchDev& b, MCtx& c, int S, int sweep, int t, u64* s_warp,
-                                       int* s_acc) {
+__device__ __forceinline__ void b_move(const BatchDev& b, MCtx& c, int S, int sweep, int t, unsigned short* s_list,
+                                       u64* s_warp) {
+  const int32_t* act = b.active[S] + c.m.oa[S];
+  const int4* ag = b.agent[S] + c.m.oa[S];
+  // per chunk: four 128-bit loads of live flags per thread (int4 q0 + u*T),
+  // the live slots listed, then two agents in flight per thread
+  for (int c0 = 0; c0 < sweep; c0 += 16 * T) {
+    const int q0 = (c0 >> 2) + threadIdx.x;
+    const int nq = (sweep + 3) >> 2;
+    u32 m = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int q = q0 + u * T;
+      const int4 a = q < nq ? reinterpret_cast<const int4*>(act)[q] : make_int4(0, 0, 0, 0);
+      m |= ((u32)(a.x != 0) | ((u32)(a.y != 0) << 1) | ((u32)(a.z != 0) << 2) | ((u32)(a.w != 0) << 3)) << (4 * u);
+    }
+    // bit 4u + j of m is slot 4 (q0 + u T) + j = c0 + 4 tid + 4 u T + j
+    if (!__syncthreads_or(m != 0)) continue;  // no live agent in the chunk
+    u32 ex, ex2, tot, tot2;
+    block_scan2<T>((u32)__popc(m), 0u, ex, ex2, tot, tot2, s_warp);
+    {
+      u32 pos = ex, mb = m;
+      while (mb) {
+        const int bit = __ffs(mb) - 1;
+        mb &= mb - 1;
+        s_list[pos++] = (unsigned short)(4 * threadIdx.x + 4 * (bit >> 2) * T + (bit & 3));
+      }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < (int)tot; e += 2 * T) {
+      const int sa = c0 + s_list[e];
+      const int sb = e + T < (int)tot ? c0 + s_list[e + T] : -1;
+      const int4 aa = ag[sa];
+      int4 ab = make_int4(0, 0, 0, 0);
+      if (sb >= 0) ab = ag[sb];
+      move_agent<T>(b, c, S, t, sa, aa);
+      if (sb >= 0) move_agent<T>(b, c, S, t, sb, ab);
+    }
+    __syncthreads();  // the list is rewritten by the next chunk
+  }
+}
+
+// eat (claim winners), select parents or die; returns bit 0 = parent, bit 1 =
+// died, bit 2 = ate
+template <int T>
+__device__ __forceinline__ u32 scan_agent(const BatchDev& b, const MCtx& c, int S, int t, int slot) {
   int32_t* act = b.active[S] + c.m.oa[S];
   int4* ag = b.agent[S] + c.m.oa[S];
-  int32_t* plist = b.plist[S] + c.m.oa[S];
-  int32_t* flist = b.flist[S] + c.m.oa[S];
   u64* claim = (S == 0 ? b.gclaim : b.wclaim) + c.m.oc;
   u64* victim = b.victim + c.m.oc;
-  const int gain = c.m.prm[S];
-  const u32 Tr = (u32)c.m.prm[PRM_SHEEP_T + S];
-  const int regrowth = c.m.prm[PRM_REGROWTH];
+  int4 a = ag[slot];
+  const int cell = a.x;
+  const u64 cl = claim[cell];
+  u32 r = 0;
+  if (cl != kNoKey && (u32)cl == (u32)slot) {
+    a.y += c.m.prm[S];
+    ag[slot].y = a.y;
+    claim[cell] = kNoKey;
+    r |= 4u;
+    if (S == 0) {
+      b.regrow[c.m.oc + cell] = t + c.m.prm[PRM_REGROWTH];
+    } else {
+      const u64 v = victim[cell];
+      b.active[0][c.m.oa[0] + (u32)v] = 0;
+      victim[cell] = kNoKey;
+    }
+  }
+  if (a.y < 0) {
+    act[slot] = 0;
+    r |= 2u;
+  } else {
+    if (draw(c.m.seed, c.m.model, (u32)t, (u32)slot, ABM_P_REPRO, (u32)S) < (u32)c.m.prm[PRM_SHEEP_T + S]) r |= 1u;
+    if (S == 0)
+      atomicMin(&victim[cell], claim_key(draw(c.m.seed, c.m.model, (u32)t, (u32)slot, ABM_P_VICTIM, 0u), slot));
+  }
+  return r;
+}
+
+// eat (claim winners), select parents, kill the starving, compact the free
+// slots and the parents (ranks by block scans, chunk by chunk). Thread i holds
+// the 16 contiguous slots 16 i.. of a chunk for the ranks; the live agents of
+// the chunk are listed and shared by all threads.
+template <int T>
+__device__ __forceinline__ void b_scan(const BatchDev& b, MCtx& c, int S, int sweep, int t, u64* s_warp,
+                                       int* s_acc, unsigned short* s_list, u32* s_par) {
+  const int32_t* act = b.active[S] + c.m.oa[S];
+  int32_t* plist = b.plist[S] + c.m.oa[S];
+  int32_t* flist = b.flist[S] + c.m.oa[S];
   const int bound = c.n_active[S];
   int starved = 0, won = 0;
   u32 pf = 0, pp = 0;
   for (int c0 = 0; c0 < sweep; c0 += 16 * T) {
     const int base = c0 + 16 * threadIdx.x;
-    int a16[16];
+    u32 m = 0, valid = 0;
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       int4 q = make_int4(0, 0, 0, 0);
       if (base + 4 * v < sweep) q = reinterpret_cast<const int4*>(act)[(base >> 2) + v];
-      a16[4 * v] = q.x; a16[4 * v + 1] = q.y; a16[4 * v + 2] = q.z; a16[4 * v + 3] = q.w;
+      m |= ((u32)(q.x != 0) | ((u32)(q.y != 0) << 1) | ((u32)(q.z != 0) << 2) | ((u32)(q.w != 0) << 3)) << (4 * v);
     }
-    u32 fr = 0, par = 0, died = 0;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const int slot = base + j;
-      if (slot >= sweep) continue;
-      if (!a16[j]) {
-        fr |= 1u << j;
-        continue;
-      }
-      int4 a = ag[slot];
-      const int cell = a.x;
-      const u64 cl = claim[cell];
-      if (cl != kNoKey && (u32)cl == (u32)slot) {
-        a.y += gain;
-        ag[slot].y = a.y;
-        claim[cell] = kNoKey;
-        ++won;
-        if (S == 0) {
-          b.regrow[c.m.oc + cell] = t + regrowth;
-        } else {
-          const u64 v = victim[cell];
-          b.active[0][c.m.oa[0] + (u32)v] = 0;
-          victim[cell] = kNoKey;
-        }
-      }
-      if (a.y < 0) {
-        a16[j] = 0;
-        died |= 1u << j;
-        ++starved;
-      } else {
-        if (draw(c.m.seed, c.m.model, (u32)t, (u32)slot, ABM_P_REPRO, (u32)S) < Tr) par |= 1u << j;
-        if (S == 0)
-          atomicMin(&victim[cell], claim_key(draw(c.m.seed, c.m.model, (u32)t, (u32)slot, ABM_P_VICTIM, 0u), slot));
-      }
+    for (int j = 0; j < 16; ++j) valid |= (u32)(base + j < sweep) << j;
+    m &= valid;
+    const u32 fr = ~m & valid;
+    // a chunk without live agents whose free slots all rank past the free-list
+    // bound only adds to the free count
+    if ((int)pf >= bound && !__syncthreads_or(m != 0)) {
+      pf += (u32)min(16 * T, sweep - c0);
+      continue;
     }
+    const int tot = chunk_list<T>(m, 16 * threadIdx.x, 1, s_list, s_warp);
+    for (int e = threadIdx.x; e < tot; e += T) {
+      const int off = s_list[e];
+      const u32 r = scan_agent<T>(b, c, S, t, c0 + off);
+      if (r & 1u) atomicOr(&s_par[off >> 5], 1u << (off & 31));
+      starved += (r >> 1) & 1u;
+      won += (r >> 2) & 1u;
+    }
+    __syncthreads();
+    u32 par = (s_par[threadIdx.x >> 1] >> (16 * (threadIdx.x & 1))) & 0xFFFFu;
     u32 ex_f, ex_p, tot_f, tot_p;
     block_scan2<T>(__popc(fr), __popc(par), ex_f, ex_p, tot_f, tot_p, s_warp);
+    if (!(threadIdx.x & 1)) s_par[threadIdx.x >> 1] = 0u;  // both halves were read before the scan's barrier
     u32 rf = pf + ex_f, rp = pp + ex_p;
-    while (fr) {
-      const int j = __ffs(fr) - 1;
-      fr &= fr - 1;
+    u32 frm = fr;
+    while (frm) {
+      const int j = __ffs(frm) - 1;
+      frm &= frm - 1;
       if ((int)rf < bound) flist[rf] = base + j;
       ++rf;
     }
@@ -181,15 +236,9 @@ __device__ __forceinline__ void b_scan(const BatchDev& b, MCtx& c, int S, int sw
       par &= par - 1;
       plist[rp++] = base + j;
     }
-    if (died) {
-#pragma unroll
-      for (int v = 0; v < 4; ++v)
-        if ((died >> (4 * v)) & 0xFu)
-          reinterpret_cast<int4*>(act)[(base >> 2) + v] =
-              make_int4(a16[4 * v], a16[4 * v + 1], a16[4 * v + 2], a16[4 * v + 3]);
-    }
     pf += tot_f;
     pp += tot_p;
+    __syncthreads();  // the list and the parent words are rewritten by the next chunk
   }
   // per-CTA sums of the winners and the starved
 #pragma unroll
@@ -252,6 +301,9 @@ __global__ void __launch_bounds__(T) k_batch_run(BatchDev b, int nsteps, int swe
   __shared__ u64 s_warp[T / 32 + 1];
   __shared__ int s_acc[4];
   __shared__ int s_idx;
+  __shared__ unsigned short s_list[16 * T];  // live agents of a chunk
+  __shared__ u32 s_par[16 * T / 32];         // parent bits of a chunk
+  if (threadIdx.x < 16 * T / 32) s_par[threadIdx.x] = 0u;
   while (true) {
     __syncthreads();
     if (threadIdx.x == 0) s_idx = (int)atomicAdd(&b.ctrl[0], 1u);
@@ -284,9 +336,9 @@ __global__ void __launch_bounds__(T) k_batch_run(BatchDev b, int nsteps, int swe
       const int sw0 = sweep_extent ? c.extent[0] : c.m.cap[0];
       __syncthreads();
       // sheep: move + grass claims; eat, select, die, compact
-      b_move<T>(b, c, 0, sw0, t);
+      b_move<T>(b, c, 0, sw0, t, s_list, s_warp);
       __syncthreads();
-      b_scan<T>(b, c, 0, sw0, t, s_warp, s_acc);
+      b_scan<T>(b, c, 0, sw0, t, s_warp, s_acc, s_list, s_par);
       __syncthreads();
       const int avail0 = c.F[0] + (sweep_extent ? c.m.cap[0] - c.extent[0] : 0);
       const int r0 = min(c.P[0], avail0);
@@ -295,7 +347,7 @@ __global__ void __launch_bounds__(T) k_batch_run(BatchDev b, int nsteps, int swe
       // claim only needs the cell to hold a live sheep; every newborn lamb
       // sits with its live parent)
       b_births<T>(b, c, 0, r0, t);
-      b_move<T>(b, c, 1, sw1, t);
+      b_move<T>(b, c, 1, sw1, t, s_list, s_warp);
       __syncthreads();
       if (threadIdx.x == 0) {
         b_count_births(b, c, 0, r0, s_acc[0], avail0);
@@ -304,7 +356,7 @@ __global__ void __launch_bounds__(T) k_batch_run(BatchDev b, int nsteps, int swe
         s_acc[0] = s_acc[1] = 0;
       }
       __syncthreads();
-      b_scan<T>(b, c, 1, sw1, t, s_warp, s_acc);
+      b_scan<T>(b, c, 1, sw1, t, s_warp, s_acc, s_list, s_par);
       __syncthreads();
       const int avail1 = c.F[1] + (sweep_extent ? c.m.cap[1] - c.extent[1] : 0);
       const int r1 = min(c.P[1], avail1);
