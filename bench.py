@@ -313,8 +313,9 @@ def selective_update_leg(torch, engine, abm, autotune, hbm_peak, steps=8, warmup
     del s
     ms = statistics.median(times)
     # per slot: key + value built (read flag + key field, write 8 B), five passes of
-    # (histogram read 8 B, scatter read 8 B + write 8 B), the row gather (read + write 4 + 32 B)
-    b = n * (8 + 8 + 5 * 24 + 2 * (4 + 4 * F))
+    # (histogram read 4 B, scatter read 8 B + write 8 B), the row gather (value read 4 B,
+    # row read + write 4 F B each, live flag and permutation written 4 B each)
+    b = n * (8 + 8 + 5 * 20 + 4 + 2 * 4 * F + 8)
     out["sort_agents"] = {"ms": ms, "algorithmic_bytes": b, "gbs": b / (ms * 1e-3) / 1e9,
                           "frac": b / (ms * 1e-3) / 1e9 / hbm_peak,
                           "method": "LSD radix sort, 4 key-byte passes + 1 live-flag pass, then the row gather"}

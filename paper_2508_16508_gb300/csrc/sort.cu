@@ -35,6 +35,7 @@ struct SortScratch {
   u32* sums;        // per scan block
   int32_t* fields;  // [n_pad * Fp]: the next fields array
   int32_t* active;  // [n_pad]: the next live-flag array
+  int* nonbinary;   // set when a live flag is neither 0 nor 1 (the gather then copies them)
 };
 
 void sort_scratch_free(SortScratch* p) {
@@ -47,12 +48,15 @@ void sort_scratch_free(SortScratch* p) {
   cudaFree(p->sums);
   cudaFree(p->fields);
   cudaFree(p->active);
+  cudaFree(p->nonbinary);
   delete p;
 }
 
-__global__ void k_sort_init(SlabDev s, int field, u32* key, u32* val) {
+__global__ void k_sort_init(SlabDev s, int field, u32* key, u32* val, int* nonbinary) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s.cap; i += gridDim.x * blockDim.x) {
-    const bool live = s.active[i] != 0;
+    const int a = s.active[i];
+    if (a != 0 && a != 1) *nonbinary = 1;
+    const bool live = a != 0;
     key[i] = live ? ((u32)s.fields[(size_t)i * s.Fp + field] ^ 0x80000000u) : 0u;
     val[i] = (u32)i | (live ? 0u : kPlaceholder);
   }
@@ -72,7 +76,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const u32* __restric
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
     const int i = t * kSortTile + r * kSortThreads + threadIdx.x;
-    if (i < n) atomicAdd(&s_cnt[digit_of(key[i], val[i], pass)], 1u);
+    if (i < n) atomicAdd(&s_cnt[pass < 4 ? digit_of(key[i], 0u, pass) : digit_of(0u, val[i], pass)], 1u);
   }
   __syncthreads();
   hist[(size_t)threadIdx.x * G + t] = s_cnt[threadIdx.x];
@@ -124,33 +128,57 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_add(u32* a, int n, const 
 // (slot order within the tile = round, warp, lane); an item's rank among the
 // tile's items with its digit = the count from earlier rounds + the counts of
 // lower warps in this round + the lower lanes of its warp with that digit.
+// The items are first placed in shared memory in (digit, rank) order, then
+// written out in that order, so that consecutive threads write consecutive
+// addresses of one digit's run.
 __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const u32* __restrict__ key, const u32* __restrict__ val,
                                                                int n, int pass, int G, const u32* __restrict__ off,
                                                                u32* key_out, u32* val_out) {
+  __shared__ u32 s_key[kSortTile], s_val[kSortTile];  // the tile in (digit, rank) order
   __shared__ u32 s_run[kBins];                // items of each digit in earlier rounds
   __shared__ u32 s_off[kBins];                // the tile's global offset of each digit
+  __shared__ u32 s_start[kBins];              // a digit's first position in the tile order
   __shared__ unsigned short s_wc[kSortWarps][kBins];  // this round's count per warp and digit
+  __shared__ u64 s_warp[kSortWarps + 1];
   const int t = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  s_run[threadIdx.x] = 0u;
-  s_off[threadIdx.x] = off[(size_t)threadIdx.x * G + t];
+  const int n_tile = min(kSortTile, n - t * kSortTile);
+  {
+    // the tile's count of digit d: the next (digit, tile) entry's offset minus its own
+    const size_t e = (size_t)threadIdx.x * G + t;
+    const u32 o = off[e];
+    const u32 next = e + 1 < (size_t)kBins * G ? off[e + 1] : (u32)n;
+    u32 ex, ex2, tot, tot2;
+    block_scan2<kSortThreads>(next - o, 0u, ex, ex2, tot, tot2, s_warp);
+    s_off[threadIdx.x] = o;
+    s_start[threadIdx.x] = ex;
+    s_run[threadIdx.x] = 0u;
+  }
   for (int w = 0; w < kSortWarps; ++w) s_wc[w][threadIdx.x] = 0;
   __syncthreads();
   const u32 lt = (1u << lane) - 1u;
+  u32 kr[kSortItems], vr[kSortItems];  // all of the thread's items in flight at once
+#pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
-    const int i = t * kSortTile + r * kSortThreads + threadIdx.x;
-    const bool ok = i < n;
-    const u32 k = ok ? key[i] : 0u, v = ok ? val[i] : 0u;
+    const int j = r * kSortThreads + threadIdx.x;
+    kr[r] = j < n_tile ? key[t * kSortTile + j] : 0u;
+    vr[r] = j < n_tile ? val[t * kSortTile + j] : 0u;
+  }
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    const int j = r * kSortThreads + threadIdx.x;
+    const bool ok = j < n_tile;
+    const u32 k = kr[r], v = vr[r];
     const u32 d = ok ? digit_of(k, v, pass) : (u32)kBins;  // kBins: no item
     const u32 peers = __match_any_sync(0xFFFFFFFFu, d);
     const u32 below = (u32)__popc(peers & lt);
     if (ok && below == 0) s_wc[warp][d] = (unsigned short)__popc(peers);
     __syncthreads();
     if (ok) {
-      u32 pos = s_off[d] + s_run[d] + below;
+      u32 pos = s_start[d] + s_run[d] + below;
       for (int w = 0; w < warp; ++w) pos += s_wc[w][d];
-      key_out[pos] = k;
-      val_out[pos] = v;
+      s_key[pos] = k;
+      s_val[pos] = v;
     }
     __syncthreads();
     {
@@ -163,14 +191,24 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const u32* __rest
     }
     __syncthreads();
   }
+  for (int j = threadIdx.x; j < n_tile; j += kSortThreads) {
+    const u32 k = s_key[j], v = s_val[j];
+    const u32 d = digit_of(k, v, pass);
+    const u32 pos = s_off[d] + ((u32)j - s_start[d]);
+    key_out[pos] = k;
+    val_out[pos] = v;
+  }
 }
 
 // row i of the sorted slab <- row (val[i] without the flag) of the old one
 __global__ void k_sort_gather(SlabDev s, const u32* __restrict__ val, int32_t* fields_out, int32_t* active_out,
-                              int32_t* perm_out) {
+                              int32_t* perm_out, const int* nonbinary) {
+  const bool exact = *nonbinary != 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s.cap; i += gridDim.x * blockDim.x) {
-    const int src = (int)(val[i] & ~kPlaceholder);
-    active_out[i] = s.active[src];
+    const u32 v = val[i];
+    const int src = (int)(v & ~kPlaceholder);
+    // the flag travels with the value; only other nonzero live values need the old array
+    active_out[i] = exact ? s.active[src] : ((v & kPlaceholder) ? 0 : 1);
     const int32_t* a = s.fields + (size_t)src * s.Fp;
     int32_t* b = fields_out + (size_t)i * s.Fp;
     for (int f = 0; f < s.Fp; f += 4) *reinterpret_cast<int4*>(b + f) = *reinterpret_cast<const int4*>(a + f);
@@ -199,6 +237,7 @@ static abm_status sort_scratch(abm_slab* s, SortScratch** out) {
   ok = ok && cudaMalloc(&p->sums, sizeof(u32) * nb) == cudaSuccess;
   ok = ok && cudaMalloc(&p->fields, sizeof(int32_t) * (size_t)p->n_pad * p->Fp) == cudaSuccess;
   ok = ok && cudaMalloc(&p->active, sizeof(int32_t) * (size_t)p->n_pad) == cudaSuccess;
+  ok = ok && cudaMalloc(&p->nonbinary, sizeof(int)) == cudaSuccess;
   // rows past the capacity are never gathered: keep them as the slab keeps its own
   ok = ok && cudaMemset(p->fields, 0, sizeof(int32_t) * (size_t)p->n_pad * p->Fp) == cudaSuccess;
   ok = ok && cudaMemset(p->active, 0, sizeof(int32_t) * (size_t)p->n_pad) == cudaSuccess;
@@ -226,7 +265,8 @@ extern "C" abm_status abm_sort(abm_slab* s, int32_t field, int32_t* out_perm, vo
   const int nh = kBins * G;
   const int nb = (nh + kScanBlock - 1) / kScanBlock;
   const int grid = std::max(1, std::min((n + 255) / 256, num_sms() * 8));
-  k_sort_init<<<grid, 256, 0, st>>>(s->d, field, p->key[0], p->val[0]);
+  ABM_CUDA_TRY(cudaMemsetAsync(p->nonbinary, 0, sizeof(int), st));
+  k_sort_init<<<grid, 256, 0, st>>>(s->d, field, p->key[0], p->val[0], p->nonbinary);
   ABM_LAUNCH_CHECK();
   int cur = 0;
   for (int pass = 0; pass < 5; ++pass) {
@@ -243,7 +283,7 @@ extern "C" abm_status abm_sort(abm_slab* s, int32_t field, int32_t* out_perm, vo
     ABM_LAUNCH_CHECK();
     cur ^= 1;
   }
-  k_sort_gather<<<grid, 256, 0, st>>>(s->d, p->val[cur], p->fields, p->active, out_perm);
+  k_sort_gather<<<grid, 256, 0, st>>>(s->d, p->val[cur], p->fields, p->active, out_perm, p->nonbinary);
   ABM_LAUNCH_CHECK();
   // the gathered arrays become the slab's; the old ones are the next sort's targets
   std::swap(s->d.fields, p->fields);

@@ -191,6 +191,14 @@ def test_sort_agents(eng, n):
         np.testing.assert_array_equal(act, o.active)
         np.testing.assert_array_equal(fld, o.fields)
     assert s.counters()["n_active"] == int(o.active.sum())
+    # live flags other than 0 / 1 (written by the caller) move unchanged
+    odd = np.where(o.active != 0, 7, 0).astype(np.int32)
+    s.write(-1, torch.from_numpy(odd).cuda())
+    o.active[:] = odd
+    np.testing.assert_array_equal(np_of(s.sort(2)), o.sort(2))
+    act, fld = slab_state(s)
+    np.testing.assert_array_equal(act, o.active)
+    np.testing.assert_array_equal(fld, o.fields)
     s.check()
 
 
