@@ -202,6 +202,46 @@ def test_sort_agents(eng, n):
     s.check()
 
 
+def test_maximum_capacity(eng):
+    """The largest slab abm_slab_create accepts (2^28 - 1 slots, one field):
+    half-live init, one selective-update call and a select, against the
+    oracle; then a sort by the field."""
+    from paper_2508_16508_gb300 import abm
+    n, F, p = (1 << 28) - 1, 1, 0.001
+    T, k = workloads.threshold(p), workloads.k_for(p, n)
+    s = eng.Slab(n, F, seed=8, init=1)
+    o = oracle.Slab(n, F)
+    o.c1_init(seed=8)
+    rec = s.philox_records(0, abm.P_NEWREC0, abm.P_NEWREC1, k)
+    dl = s.philox_records(0, abm.P_DELTA0, abm.P_DELTA1, k)
+    cnt = np_of(s.selective_update(0, T, rec, dl))
+    want = o.c1_call(0, T, k, seed=8)
+    assert cnt.tolist() == [want["removed"], want["added"], want["updated"]]
+    act, fld = slab_state(s)
+    np.testing.assert_array_equal(act, o.active)
+    np.testing.assert_array_equal(fld, o.fields)
+    del act, fld
+    idx, c = s.select(abm.pred(abm.PRED_LIVE))
+    live = int(c.item())
+    assert live == int(o.active.sum()) == s.counters()["n_active"]
+    assert bool((idx[1:live] > idx[:live - 1]).all())
+    del idx
+    # the sort, by the properties that define it (the oracle's sort is O(n log n)
+    # on one core; the small and 2^24 cases compare with it directly)
+    act0, key0 = o.active, o.fields[0]
+    perm = np_of(s.sort(0)).astype(np.int64)
+    assert (np.bincount(perm, minlength=n) == 1).all()  # a permutation
+    act, fld = slab_state(s)
+    np.testing.assert_array_equal(act, act0[perm])
+    np.testing.assert_array_equal(fld[0], key0[perm])
+    assert (act[:live] != 0).all() and (act[live:] == 0).all()
+    k = fld[0][:live].astype(np.int64)
+    pl = perm[:live]
+    assert ((k[1:] > k[:-1]) | ((k[1:] == k[:-1]) & (pl[1:] > pl[:-1]))).all()  # ascending, stable
+    assert (np.diff(perm[live:]) > 0).all()  # placeholders in slot order
+    s.check()
+
+
 def test_sort_agents_full_size(eng):
     """2^24 slots x 8 fields (the selective-update slab), after three
     selective-update calls; sorted by two fields."""
