@@ -91,6 +91,9 @@ def lib():
             L.orc_c1_call.argtypes = [i32p, i32p, C.c_int64, C.c_int, C.c_uint32, C.c_uint32,
                                       C.c_uint32, C.c_uint32, C.c_int64, i64p]
             L.orc_sort.argtypes = [i32p, i32p, C.c_int64, C.c_int, C.c_int, i32p]
+            L.orc_lob_match.argtypes = [C.c_int32, C.c_int32, i32p, i32p, i32p, i32p, i32p, i64p, i32p]
+            L.orc_lob_add.argtypes = [C.c_int32, C.c_int32, i32p, i32p, i32p, i32p, i32p, i32p, i32p,
+                                      C.c_int32, i32p]
             L.orc_pred_create.argtypes = [C.c_int32, C.c_uint32, C.c_uint32, i32p, i32p, i32p]
             L.orc_pred_create.restype = C.c_void_p
             L.orc_pred_free.argtypes = [C.c_void_p]
@@ -228,6 +231,38 @@ def resolve(res, prio, R):
 # predation (Section 5.1)
 
 AGENT_FIELDS = ("active", "cell", "energy", "id", "age")
+
+
+def lob_match(book: dict):
+    """One matching round of every order book (Section 5.3; rules in
+    orc_lob_match). book: arrays [nbooks][cap] active, side, price, qty, time;
+    active and qty are updated in place. Returns (volume int64[nbooks],
+    clearing price int32[nbooks])."""
+    a = book["active"]
+    nb, cap = a.shape
+    for f in ("active", "side", "price", "qty", "time"):
+        assert book[f].dtype == np.int32 and book[f].flags.c_contiguous and book[f].shape == (nb, cap)
+    vol = np.zeros(max(nb, 1), dtype=np.int64)
+    px = np.zeros(max(nb, 1), dtype=np.int32)
+    lib().orc_lob_match(nb, cap, _p(book["active"], C.c_int32), _p(book["side"], C.c_int32),
+                        _p(book["price"], C.c_int32), _p(book["qty"], C.c_int32), _p(book["time"], C.c_int32),
+                        _p(vol, C.c_int64), _p(px, C.c_int32))
+    return vol[:nb], px[:nb]
+
+
+def lob_add(book: dict, new_orders: np.ndarray, k: np.ndarray) -> np.ndarray:
+    """New orders (new_orders[nbooks][kmax][4] = side, price, qty, time; k[b]
+    of them for book b) into each book's lowest free slots. Returns the
+    orders placed per book."""
+    a = book["active"]
+    nb, cap = a.shape
+    no = np.ascontiguousarray(new_orders, dtype=np.int32)
+    kk = np.ascontiguousarray(k, dtype=np.int32)
+    out = np.zeros(max(nb, 1), dtype=np.int32)
+    lib().orc_lob_add(nb, cap, _p(book["active"], C.c_int32), _p(book["side"], C.c_int32),
+                      _p(book["price"], C.c_int32), _p(book["qty"], C.c_int32), _p(book["time"], C.c_int32),
+                      _p(no, C.c_int32), _p(kk, C.c_int32), no.shape[1], _p(out, C.c_int32))
+    return out[:nb]
 
 
 VARIANT_ONE_WOLF, VARIANT_MANY_WOLVES, VARIANT_GRASS_OFF = 0, 1, 2  # bits

@@ -243,6 +243,121 @@ void orc_sort(int32_t* active, int32_t* fields, int64_t n, int F, int field, int
 }
 
 /* ------------------------------------------------------------------------ */
+/* Limit order books (Section 5.3: noisy traders place limit orders into the
+ * vacant slots of an order book; all books are matched in parallel by sorting
+ * the buy and sell orders by price and taking cumulative sums of shares). The
+ * paper gives no exact rules; the ones restated here are the engine's:
+ * a book is a fixed-capacity set of orders (active, side 0 buy / 1 sell,
+ * price > 0, qty > 0, time); priority = price (bids descending, asks
+ * ascending), then time, then slot. */
+
+typedef struct {
+  int32_t price, time, slot;
+  int64_t qty;
+} orc_order;
+
+static int cmp_bid(const void* a, const void* b) {
+  const orc_order* x = (const orc_order*)a;
+  const orc_order* y = (const orc_order*)b;
+  if (x->price != y->price) return x->price > y->price ? -1 : 1;
+  if (x->time != y->time) return x->time < y->time ? -1 : 1;
+  return x->slot < y->slot ? -1 : x->slot > y->slot;
+}
+
+static int cmp_ask(const void* a, const void* b) {
+  const orc_order* x = (const orc_order*)a;
+  const orc_order* y = (const orc_order*)b;
+  if (x->price != y->price) return x->price < y->price ? -1 : 1;
+  if (x->time != y->time) return x->time < y->time ? -1 : 1;
+  return x->slot < y->slot ? -1 : x->slot > y->slot;
+}
+
+/* One matching round of every book (arrays [nbooks][cap], updated in place).
+ * With the bids and asks in priority order and QB_i, QA_j their cumulative
+ * quantities, the traded volume V is the largest v such that the bid holding
+ * share v (QB_{i-1} < v <= QB_i) is priced at or above the ask holding share v
+ * (0 if none): bid prices fall and ask prices rise along the shares, so the
+ * first V shares of each side trade. Order k fills clamp(V - Q_{k-1}, 0,
+ * qty_k); filled orders leave the book. out_volume[b] = V; out_price[b] = the
+ * price of the ask holding share V (-1 if V = 0). */
+void orc_lob_match(int32_t nbooks, int32_t cap, int32_t* active, const int32_t* side, const int32_t* price,
+                   int32_t* qty, const int32_t* time, int64_t* out_volume, int32_t* out_price) {
+  orc_order* bid = (orc_order*)malloc(sizeof(orc_order) * (size_t)(cap > 0 ? cap : 1));
+  orc_order* ask = (orc_order*)malloc(sizeof(orc_order) * (size_t)(cap > 0 ? cap : 1));
+  for (int32_t b = 0; b < nbooks; b++) {
+    const int64_t o = (int64_t)b * cap;
+    int32_t nb = 0, na = 0;
+    for (int32_t i = 0; i < cap; i++) {
+      if (!active[o + i]) continue;
+      const orc_order e = {price[o + i], time[o + i], i, qty[o + i]};
+      if (side[o + i] == 0)
+        bid[nb++] = e;
+      else
+        ask[na++] = e;
+    }
+    qsort(bid, (size_t)nb, sizeof(orc_order), cmp_bid);
+    qsort(ask, (size_t)na, sizeof(orc_order), cmp_ask);
+    /* walk the shares: the two fronts trade while the bid front is priced at
+     * or above the ask front */
+    int64_t v = 0;
+    int32_t i = 0, j = 0, last_ask_price = -1;
+    int64_t left_b = nb > 0 ? bid[0].qty : 0, left_a = na > 0 ? ask[0].qty : 0;
+    while (i < nb && j < na && bid[i].price >= ask[j].price) {
+      const int64_t t = left_b < left_a ? left_b : left_a;
+      v += t;
+      last_ask_price = ask[j].price;
+      left_b -= t;
+      left_a -= t;
+      if (left_b == 0 && ++i < nb) left_b = bid[i].qty;
+      if (left_a == 0 && ++j < na) left_a = ask[j].qty;
+    }
+    out_volume[b] = v;
+    out_price[b] = v > 0 ? last_ask_price : -1;
+    /* the first v shares of each side fill */
+    for (int s = 0; s < 2; s++) {
+      orc_order* q = s == 0 ? bid : ask;
+      const int32_t n = s == 0 ? nb : na;
+      int64_t before = 0;
+      for (int32_t k = 0; k < n; k++) {
+        int64_t fill = v - before;
+        if (fill < 0) fill = 0;
+        if (fill > q[k].qty) fill = q[k].qty;
+        before += q[k].qty;
+        const int64_t slot = o + q[k].slot;
+        qty[slot] = (int32_t)(q[k].qty - fill);
+        if (qty[slot] == 0) active[slot] = 0;
+      }
+    }
+  }
+  free(bid);
+  free(ask);
+}
+
+/* Traders' new orders into each book: order j < k[b] of book b (rows of
+ * new_orders[b][kmax][4] = side, price, qty, time) goes into the j-th free
+ * slot of book b (ascending), j < min(k[b], free) -- the add primitive of
+ * Section 4 per book. out_added[b] = orders placed. */
+void orc_lob_add(int32_t nbooks, int32_t cap, int32_t* active, int32_t* side, int32_t* price, int32_t* qty,
+                 int32_t* time, const int32_t* new_orders, const int32_t* k, int32_t kmax, int32_t* out_added) {
+  for (int32_t b = 0; b < nbooks; b++) {
+    const int64_t o = (int64_t)b * cap;
+    const int32_t kb = k[b] < 0 ? 0 : (k[b] < kmax ? k[b] : kmax); /* [0, kmax] rows */
+    int32_t j = 0;
+    for (int32_t i = 0; i < cap && j < kb; i++) {
+      if (active[o + i]) continue;
+      const int32_t* r = new_orders + ((int64_t)b * kmax + j) * 4;
+      active[o + i] = 1;
+      side[o + i] = r[0];
+      price[o + i] = r[1];
+      qty[o + i] = r[2];
+      time[o + i] = r[3];
+      j++;
+    }
+    out_added[b] = j;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Predation (Section 5.1 and Fig. 3: grass, sheep and wolves on a periodic
  * 2-D lattice; random moves; sheep eat grass, wolves eat sheep; grass regrows
  * after a fixed delay; asexual reproduction with a given probability, the

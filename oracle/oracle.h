@@ -82,6 +82,13 @@ typedef struct orc_stats {
  * is F rows of n; perm[i] = old slot of new slot i. */
 void orc_sort(int32_t* active, int32_t* fields, int64_t n, int F, int field, int32_t* perm);
 
+/* limit order books: one matching round of every book, and new orders into
+ * the books' free slots (arrays [nbooks][cap]) */
+void orc_lob_match(int32_t nbooks, int32_t cap, int32_t* active, const int32_t* side, const int32_t* price,
+                   int32_t* qty, const int32_t* time, int64_t* out_volume, int32_t* out_price);
+void orc_lob_add(int32_t nbooks, int32_t cap, int32_t* active, int32_t* side, int32_t* price, int32_t* qty,
+                 int32_t* time, const int32_t* new_orders, const int32_t* k, int32_t kmax, int32_t* out_added);
+
 typedef struct orc_world orc_world;
 orc_world* orc_pred_create(int32_t side, uint32_t seed, uint32_t model, const int32_t params[8],
                            const int32_t cap[2], const int32_t n0[2]);

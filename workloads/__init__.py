@@ -107,3 +107,52 @@ def sample_models(n_models: int, sampler_seed: int, side_lo: int = 16, side_hi: 
 def fixed_caps(side: np.ndarray, factor: int = 4) -> np.ndarray:
     c = factor * side.astype(np.int64) ** 2
     return np.stack([c, c], axis=1).astype(np.int32)
+
+
+# Limit order books (Section 5.3: noisy traders, books of at most 1000 orders):
+# 65,536 books of 1024 slots, about half holding an order; prices around 100
+# ticks, quantities 1..100, arrival times unique within a book.
+LOB = dict(name="lob_65536x1024", n_books=65536, cap=1024, fill=0.5, seed=21)
+# the finance model's scale (Section 5.3, Table 4: 500 books of at most 1000
+# orders, 100 steps); each step up to `traders` new orders per book, then a
+# matching round of every book
+LOB_MARKET = dict(name="lob_market_500x1000_100steps", n_books=500, cap=1000, fill=0.2, traders=10, steps=100,
+                  seed=23)
+
+
+def market_orders(n_books: int, traders: int, steps: int, seed: int):
+    """Every step's new orders ([steps][n_books][traders][4]) and counts
+    ([steps][n_books]), times increasing from step to step."""
+    out = [random_new_orders(n_books, traders, seed + 1 + s, time0=(1 << 20) + s * traders) for s in range(steps)]
+    return np.stack([o for o, _ in out]), np.stack([k for _, k in out])
+
+
+def random_books(n_books: int, cap: int, fill: float, seed: int, price_mid: int = 100, price_spread: int = 10,
+                 qty_max: int = 100) -> dict:
+    """Seeded random order books: arrays [n_books][cap] active, side, price,
+    qty, time (int32). Buy prices sit a little below the mid, sell prices a
+    little above, with overlap, so that books cross."""
+    rng = np.random.default_rng(seed)
+    shape = (n_books, cap)
+    active = (rng.random(shape) < fill).astype(np.int32)
+    side = rng.integers(0, 2, size=shape, dtype=np.int32)
+    offset = rng.integers(-price_spread, price_spread + 1, size=shape, dtype=np.int32)
+    price = np.where(side == 0, price_mid - 2 + offset, price_mid + 2 + offset).astype(np.int32)
+    qty = rng.integers(1, qty_max + 1, size=shape, dtype=np.int32)
+    # time: a permutation of 0 .. cap - 1 per book
+    time = np.ascontiguousarray(rng.permuted(np.broadcast_to(np.arange(cap, dtype=np.int32), shape), axis=1))
+    return dict(active=active, side=side, price=price, qty=qty, time=time)
+
+
+def random_new_orders(n_books: int, kmax: int, seed: int, price_mid: int = 100, price_spread: int = 10,
+                      qty_max: int = 100, time0: int = 1 << 20):
+    """Seeded new orders per book ([n_books][kmax][4] = side, price, qty, time)
+    and how many each book gets (k[b] <= kmax)."""
+    rng = np.random.default_rng(seed)
+    side = rng.integers(0, 2, size=(n_books, kmax), dtype=np.int32)
+    offset = rng.integers(-price_spread, price_spread + 1, size=(n_books, kmax), dtype=np.int32)
+    price = np.where(side == 0, price_mid - 2 + offset, price_mid + 2 + offset).astype(np.int32)
+    qty = rng.integers(1, qty_max + 1, size=(n_books, kmax), dtype=np.int32)
+    time = (time0 + np.arange(kmax, dtype=np.int32))[None, :].repeat(n_books, axis=0)
+    k = rng.integers(0, kmax + 1, size=n_books, dtype=np.int32)
+    return np.stack([side, price, qty, time], axis=2).astype(np.int32), k
