@@ -50,13 +50,14 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the microbenchmark, batched and CPU legs")
-    ap.add_argument("--leg", default="all", choices=["all", "predation", "selective", "batched"],
+    ap.add_argument("--leg", default="all", choices=["all", "predation", "selective", "batched", "lob"],
                     help="run one leg alone (profiling); 'all' prints the benchmark line")
     ap.add_argument("--no-tune", action="store_true",
                     help="default launch shapes instead of the autotuner (fixed launch sequence for ncu)")
     ap.add_argument("--p", type=float, action="append", help="selective leg: only these p")
     ap.add_argument("--batch-models", type=int, default=None)
     ap.add_argument("--batch-steps", type=int, default=None)
+    ap.add_argument("--lob-books", type=int, default=None, help="lob leg: books in the matching round")
     a = ap.parse_args()
     if a.leg == "predation":
         a.no_extras = True
@@ -524,6 +525,127 @@ def many_wolves_leg(torch, engine, abm, K, W, ctas_per_sm):
             "eaten": sum(r["eaten"] for r in rows), "end_counters": gw.counters()}
 
 
+def lob_leg(torch, engine, hbm_peak, reps=10, n_books=None):
+    """Order-book matching (Section 5.3): one matching round of 65536 books x
+    1024 slots (half live), timed kernel-only on a freshly restored book each
+    rep (inputs 1.3 GB, larger than L2; L2 also flushed); plus the finance
+    model's scale (500 books x 1000 slots, 100 steps of order placement +
+    matching)."""
+    W = workloads.LOB
+    nb_ = n_books or W["n_books"]
+    book = workloads.random_books(nb_, W["cap"], W["fill"], W["seed"])
+    pristine = engine.OrderBooks(book)
+    work = engine.OrderBooks(book)
+    vol = torch.empty(nb_, dtype=torch.int64, device="cuda")
+    px = torch.empty(nb_, dtype=torch.int32, device="cuda")
+    flush = torch.ones(64 << 20, dtype=torch.int32, device="cuda")
+
+    def restore():
+        for f in engine.OrderBooks.FIELDS:
+            work.t[f].copy_(pristine.t[f])
+
+    # the words the matching round must move (see the roofline note)
+    restore()
+    work.match(vol, px)
+    torch.cuda.synchronize()
+    live = int(pristine.t["active"].sum())
+    qty_w = int((work.t["qty"] != pristine.t["qty"]).sum())
+    act_w = int((work.t["active"] != pristine.t["active"]).sum())
+    slots = nb_ * W["cap"]
+    alg = 4 * slots + 12 * live + 4 * qty_w + 4 * act_w + 12 * nb_
+    want = (int(vol.sum()), int(px.sum()))
+    ts = []
+    for _ in range(reps):
+        restore()
+        flush.max()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        work.match(vol, px)
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    same = (int(vol.sum()), int(px.sum())) == want
+    ms = statistics.median(ts)
+    gbs = alg / (ms * 1e-3) / 1e9
+    out = {"workload": W["name"] if nb_ == W["n_books"] else f"lob_{nb_}x{W['cap']}",
+           "kernel": "k_lob_match", "ms": ms, "ms_all": ts, "books_per_s": nb_ / (ms * 1e-3),
+           "live_orders_per_s": live / (ms * 1e-3), "live_orders": live, "traded_shares": want[0],
+           "books_crossed": int((vol > 0).sum()), "same_result_every_rep": same,
+           "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                        "algorithmic_bytes_per_launch": alg,
+                        "bytes_per_slot": {"algorithmic": alg / slots, "sector_min": None},
+                        "note": "algorithmic words: active of every slot, side/price/qty of live slots, the "
+                                "qty/active words written, 12 B of output per book (time words of the few "
+                                "orders on the two marginal price levels not counted)"},
+           "timing": f"median of {reps} launches, CUDA events, book restored and L2 flushed before each"}
+    # 32-byte sectors that hold those words (what DRAM must move at the least)
+    act = pristine.t["active"].view(-1, 8)
+    sec_live = int((act != 0).any(dim=1).sum())
+    out["roofline"]["bytes_per_slot"]["sector_min"] = (32 * act.shape[0] + 3 * 32 * sec_live + 8 * (
+        qty_w + act_w)) / slots if W["cap"] % 8 == 0 else None
+    del pristine, work, flush
+    torch.cuda.empty_cache()
+
+    # the finance model's scale: each step up to 10 new orders per book, then
+    # a matching round (inputs for all steps resident on the device)
+    M = workloads.LOB_MARKET
+    orders, ks = workloads.market_orders(M["n_books"], M["traders"], M["steps"], M["seed"])
+    mbook = workloads.random_books(M["n_books"], M["cap"], M["fill"], M["seed"])
+    d_orders = torch.from_numpy(orders).cuda()
+    d_k = torch.from_numpy(ks).cuda()
+    mv = torch.empty(M["steps"], M["n_books"], dtype=torch.int64, device="cuda")
+    mp = torch.empty(M["steps"], M["n_books"], dtype=torch.int32, device="cuda")
+    ma = torch.empty(M["steps"], M["n_books"], dtype=torch.int32, device="cuda")
+    mts = []
+    for _ in range(5):
+        mb = engine.OrderBooks(mbook)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for st in range(M["steps"]):
+            mb.add(d_orders[st], d_k[st], out=ma[st])
+            mb.match(mv[st], mp[st])
+        e1.record()
+        e1.synchronize()
+        mts.append(e0.elapsed_time(e1))
+    out["market"] = {"workload": M["name"], "ms_100_steps": statistics.median(mts), "ms_all": mts,
+                     "us_per_step": 1e3 * statistics.median(mts) / M["steps"],
+                     "traded_shares": int(mv.sum()), "orders_placed": int(ma.sum()),
+                     "launches": 2 * M["steps"],
+                     "paper_ms_100_steps_500_books": 2212.47,
+                     "note": "paper figure: Table 4 (JAX, its own hardware): context, not a target"}
+    return out
+
+
+def lob_cpu_baseline(n_sample=4096, budget_s=15.0):
+    """The oracle (sequential C, 1 thread) on a bounded sample of the same
+    workloads: the first n_sample books of the 65536 x 1024 matching round,
+    and the whole 500-book market run."""
+    import oracle
+    W = workloads.LOB
+    book = workloads.random_books(n_sample, W["cap"], W["fill"], W["seed"])
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        b = {f: v.copy() for f, v in book.items()}
+        oracle.lob_match(b)
+        reps += 1
+        if time.perf_counter() - t0 > budget_s / 2 or reps >= 50:
+            break
+    dt = (time.perf_counter() - t0) / reps
+    M = workloads.LOB_MARKET
+    orders, ks = workloads.market_orders(M["n_books"], M["traders"], M["steps"], M["seed"])
+    mb = workloads.random_books(M["n_books"], M["cap"], M["fill"], M["seed"])
+    t1 = time.perf_counter()
+    for st in range(M["steps"]):
+        oracle.lob_add(mb, orders[st], ks[st])
+        oracle.lob_match(mb)
+    mdt = time.perf_counter() - t1
+    return {"value": n_sample / dt, "unit": "books/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {n_sample} books of {W['name']}, {reps} matching rounds",
+            "market_ms_100_steps": 1e3 * mdt}
+
+
 def _oracle_model_run(args):
     """One batched-workload model on the sequential oracle (process-pool worker)."""
     side, seed, model, params, cap, n0, steps = args
@@ -564,12 +686,14 @@ def run_ours(args, rank, world, local):
     from paper_2508_16508_gb300 import abm, autotune, capacity, engine
     abm.lib()
     hbm_peak, peak_kind = peaks()
-    if args.leg in ("selective", "batched"):
+    if args.leg in ("selective", "batched", "lob"):
         if rank == 0:
             with ClockSampler(local) as clk:
                 if args.leg == "selective":
                     out = selective_update_leg(torch, engine, abm, autotune, hbm_peak, tune=not args.no_tune,
                                                ps=args.p)
+                elif args.leg == "lob":
+                    out = lob_leg(torch, engine, hbm_peak, n_books=args.lob_books)
                 else:
                     out = batched_leg(torch, engine, capacity, autotune, abm, hbm_peak, n_models=args.batch_models,
                                       steps=args.batch_steps, tune=not args.no_tune)
@@ -677,6 +801,7 @@ def run_ours(args, rank, world, local):
         line["batched"] = batched_leg(torch, engine, capacity, autotune, abm, hbm_peak)
         line["small_world"] = small_world_leg(torch, engine, abm)
         line["many_wolves"] = many_wolves_leg(torch, engine, abm, K, W, tw["ctas_per_sm"])
+        line["lob"] = lob_leg(torch, engine, hbm_peak)
     clk.__exit__(None, None, None)
     line["clocks"] = clk.summary()
     if rank == 0 and not args.no_extras:
@@ -688,6 +813,7 @@ def run_ours(args, rank, world, local):
                                 "host_cores": os.cpu_count()}
         cb = batched_cpu_baseline()
         line["batched"]["cpu_baseline"] = cb
+        line["lob"]["cpu_baseline"] = lob_cpu_baseline()
         line["batched"]["cpu_baseline"]["full_batch_s_estimate"] = \
             line["batched"]["fixed"]["agent_steps_per_s"] * line["batched"]["fixed"]["ms"] * 1e-3 / cb["value"]
     if rank == 0:

@@ -133,6 +133,45 @@ abm_status abm_select(abm_slab* s, const abm_pred* pred, int32_t* out_idx, int32
  * LSD radix sort: four passes over the key bytes and one over the live flag. */
 abm_status abm_sort(abm_slab* s, int32_t field, int32_t* out_perm, void* stream);
 
+/* ========================================================================== */
+/* Limit order books (Section 5.3: noisy traders' limit orders in fixed-size   */
+/* books, all books matched in parallel by price sorting and share cumsums)    */
+/* ========================================================================== */
+/*
+ * n_books books of `cap` order slots (1 <= cap <= ABM_LOB_MAX_CAP), each
+ * array device int32[n_books][cap] (book-major): active (0/1), side (0 buy,
+ * any other value sell), price (ticks, 1 .. 2^31 - 1), qty (shares >= 1),
+ * time (any int32; priority among equal prices). Values outside these ranges
+ * give unspecified books but no out-of-bounds access. ABM_ERR_ARG for
+ * n_books < 0, cap outside [1, ABM_LOB_MAX_CAP], kmax < 0 or a null array;
+ * n_books = 0 launches nothing. Asynchronous on `stream`; the caller owns
+ * every buffer. The paper gives no exact rules; these are:
+ *
+ * abm_lob_match -- one matching round of every book. Bids in priority order
+ * (price descending, then time, then slot), asks likewise (price ascending);
+ * the traded volume V is the largest share count such that the bid holding
+ * share V is priced at or above the ask holding share V (0 if none), and the
+ * first V shares of each side trade: an order fills clamp(V - shares ahead of
+ * it, 0, qty); filled orders become inactive, the others keep the rest of
+ * their qty. out_volume (device int64[n_books]) = V; out_price (device
+ * int32[n_books]) = the price of the ask holding share V, -1 if V = 0.
+ * One CTA per book, sorted in shared memory.
+ *
+ * abm_lob_add -- new orders into each book's vacant slots (the add of
+ * Section 4 per book; the stock-exchange case of Section 4's example): order
+ * j < k[b] of book b (new_orders device int32[n_books][kmax][4] = side,
+ * price, qty, time; k device int32[n_books], values clamped to [0, kmax])
+ * goes into the j-th free slot of book b, ascending, j < min(k[b], free);
+ * new_orders may be null when kmax = 0. out_added device int32[n_books] =
+ * orders placed.
+ */
+#define ABM_LOB_MAX_CAP 2048
+abm_status abm_lob_match(int32_t n_books, int32_t cap, int32_t* active, const int32_t* side, const int32_t* price,
+                         int32_t* qty, const int32_t* time, int64_t* out_volume, int32_t* out_price, void* stream);
+abm_status abm_lob_add(int32_t n_books, int32_t cap, int32_t* active, int32_t* side, int32_t* price, int32_t* qty,
+                       int32_t* time, const int32_t* new_orders, const int32_t* k, int32_t kmax, int32_t* out_added,
+                       void* stream);
+
 /* select_agents with SCI's index exposure (Algorithm 2, Section 4): a
  * permutation of all slots, those satisfying `pred` first, then the others,
  * each group ascending -- the stable argsort of the mask with true first.

@@ -46,6 +46,7 @@ class abm_pred(C.Structure):
 
 
 VARIANT_ONE_WOLF, VARIANT_MANY_WOLVES, VARIANT_GRASS_OFF = 0, 1, 2  # bits
+LOB_MAX_CAP = 2048  # order slots per book, at most
 
 
 class abm_config(C.Structure):
@@ -155,6 +156,8 @@ def _sig(L):
         "abm_batch_digest": ([vp, vp, vp], st),
         "abm_capacity_features": ([vp, i32, vp, vp, vp], st),
         "abm_capacity_from_prediction": ([vp, i32, C.c_float, i32, vp, vp, vp, vp], st),
+        "abm_lob_match": ([i32, i32, vp, vp, vp, vp, vp, vp, vp, vp], st),
+        "abm_lob_add": ([i32, i32, vp, vp, vp, vp, vp, vp, vp, i32, vp, vp], st),
     }
     global EXPORTED
     for name, (args, res) in sigs.items():

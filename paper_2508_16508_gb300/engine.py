@@ -241,6 +241,44 @@ class World:
         call("abm_load", self.h, ptr(host), host.numel(), _stream(stream))
 
 
+class OrderBooks:
+    """n_books limit order books of `cap` slots (Section 5.3): int32 device
+    arrays [n_books][cap] active, side, price, qty, time."""
+
+    FIELDS = ("active", "side", "price", "qty", "time")
+
+    def __init__(self, arrays: dict, device=None):
+        dev = device if device is not None else f"cuda:{torch.cuda.current_device()}"
+        self.t = {f: torch.as_tensor(arrays[f], dtype=torch.int32).to(dev).contiguous() for f in self.FIELDS}
+        self.n_books, self.cap = self.t["active"].shape
+
+    def _ptrs(self):
+        return [ptr(self.t[f]) for f in self.FIELDS]
+
+    def match(self, out_volume=None, out_price=None, stream=None):
+        """One matching round of every book; returns (volume int64, price int32)."""
+        dev = self.t["active"].device
+        vol = out_volume if out_volume is not None else torch.empty(self.n_books, dtype=torch.int64, device=dev)
+        px = out_price if out_price is not None else torch.empty(self.n_books, dtype=torch.int32, device=dev)
+        call("abm_lob_match", self.n_books, self.cap, *self._ptrs(), ptr(vol), ptr(px), _stream(stream))
+        return vol, px
+
+    def add(self, new_orders: torch.Tensor, k: torch.Tensor, out=None, stream=None) -> torch.Tensor:
+        """new_orders [n_books][kmax][4] (side, price, qty, time), k[b] of them
+        for book b, into each book's lowest free slots; returns orders placed."""
+        dev = self.t["active"].device
+        no = new_orders.to(device=dev, dtype=torch.int32).contiguous()
+        kk = k.to(device=dev, dtype=torch.int32).contiguous()
+        kmax = int(no.shape[1]) if no.dim() == 3 else 0
+        out = out if out is not None else torch.empty(self.n_books, dtype=torch.int32, device=dev)
+        call("abm_lob_add", self.n_books, self.cap, *self._ptrs(), ptr(no) if no.numel() else None, ptr(kk),
+             kmax, ptr(out), _stream(stream))
+        return out
+
+    def numpy(self) -> dict:
+        return {f: self.t[f].cpu().numpy() for f in self.FIELDS}
+
+
 def decode_stats(t: torch.Tensor) -> list[dict]:
     """Device stats rows (int32 words) -> list of dicts."""
     rows = t.cpu().contiguous()

@@ -52,3 +52,9 @@ def test_host_only_calls(lib_path):
     assert L.abm_step(None, 1, None, 0, None) == abm.ERR_ARG
     assert L.abm_resolve_static(None, None, -1, 1, None, None, None) == abm.ERR_ARG
     assert L.abm_resolve_static(None, None, 0, (1 << 18) + 1, C.c_void_p(16), None, None) == abm.ERR_TOO_LARGE
+    assert L.abm_lob_match(-1, 8, None, None, None, None, None, None, None, None) == abm.ERR_ARG
+    assert L.abm_lob_match(1, 0, None, None, None, None, None, None, None, None) == abm.ERR_ARG
+    assert L.abm_lob_match(1, abm.LOB_MAX_CAP + 1, None, None, None, None, None, None, None, None) == abm.ERR_ARG
+    assert L.abm_lob_match(0, 8, None, None, None, None, None, None, None, None) == abm.OK
+    assert L.abm_lob_add(1, 8, None, None, None, None, None, None, None, -1, None, None) == abm.ERR_ARG
+    assert L.abm_lob_add(1, 8, None, None, None, None, None, None, None, 0, None, None) == abm.ERR_ARG
