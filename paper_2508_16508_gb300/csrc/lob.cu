@@ -11,38 +11,41 @@
 // the ask holding share V.
 //
 // The paper matches by sorting both sides by price and taking cumulative sums
-// of shares. Here one CTA matches one book at a time, and most books need no
-// sort: with D(p) = bid shares priced >= p and S(p) = ask shares priced <= p,
+// of shares. Here most books need no sort: with D(p) = bid shares priced >= p
+// and S(p) = ask shares priced <= p,
 //   V = max over p of min(D(p), S(p)),
 // because the bid holding share min(D(p), S(p)) is priced >= p and the ask
 // holding it <= p, while at p = the price of the ask holding share V both sums
-// reach V. Only prices in [lowest ask, highest bid] matter, so the level path
-// builds per-price share histograms of that range in shared memory (one
-// atomic per order), scans them into D and S, and takes V, the bid level pb
-// holding share V (largest p with D(p) >= V) and the ask level pa holding it
-// (smallest p with S(p) >= V). Bids above pb and asks below pa fill whole,
-// those beyond fill nothing, and only the orders on the two marginal levels
-// are ranked by (time, slot) -- by counting, they are few. A book whose range
-// is wider than kLobLevels prices, whose marginal levels hold more than
-// kLobMarginal orders, or with a qty >= kLobQtyMax takes the sort path:
-// bitonic sort of the whole book in shared memory, cumulative sums, and a
-// binary search per bid.
+// reach V. Only prices in [lowest ask, highest bid] matter.
 //
-// Each CTA streams the next book's active, side, price and qty words into a
-// second shared-memory buffer with cp.async while it matches the current one.
+// Level path (k_lob_match_warp): one warp per book. The warp stages the book's
+// active, side, price and qty words into shared memory with cp.async, keeps
+// each lane's slots in registers, builds per-price histograms of the range
+// (shares | orders << 21, one shared atomic per order), scans them into D and
+// S, and takes V, the bid level pb holding share V (largest p with D(p) >= V)
+// and the ask level pa holding it (smallest p with S(p) >= V). Bids above pb
+// and asks below pa fill whole, those beyond fill nothing, and only the orders
+// on the two marginal levels are ranked by (time, slot), by counting.
+//
+// Sort path (k_lob_deferred): a book whose range is wider than kWarpLevels
+// prices, whose marginal level holds more than kWarpMarginal orders, or whose
+// bid or ask shares reach 2^21 is left untouched by the warp (its volume set
+// to -1) and matched by a second kernel, one CTA per book: bitonic sort of the
+// whole book in shared memory, cumulative sums, a binary search per bid.
 #include <algorithm>
 
 #include "common.cuh"
 
 namespace abm {
 
-constexpr int kLobThreads = 256;
+constexpr int kLobThreads = 256;        // sort path: threads per book
 constexpr int kLobWarps = kLobThreads / 32;
-constexpr int kLobLevels = 1024;       // prices in the level path's range, at most
-constexpr int kLobLevelsPerThread = kLobLevels / kLobThreads;
-constexpr int kLobMarginal = 256;      // orders on one marginal level, at most
-constexpr u32 kLobQtyMax = 1u << 20;   // every qty below this keeps share sums in 32 bits
-constexpr size_t kLobLevelBytes = 2 * kLobLevels * sizeof(u32) + 2 * kLobMarginal * (sizeof(u64) + sizeof(u32));
+constexpr int kWarpsPerBlock = 2;       // level path: books in flight per CTA
+constexpr int kWarpLevels = 256;        // level path: prices in [lowest ask, highest bid], at most
+constexpr int kWarpMarginal = 64;       // level path: orders on one marginal level, at most
+constexpr u32 kShareBits = 21;          // level words: shares in the low 21 bits, orders above
+constexpr u32 kShareMask = (1u << kShareBits) - 1u;
+constexpr u32 kLive = 1u << 31, kAsk = 1u << 30;  // packed slot word: live | ask | qty
 
 __device__ __forceinline__ u32 smem_u32(const void* p) { return (u32)__cvta_generic_to_shared(p); }
 
@@ -53,36 +56,10 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // order-preserving map of int32 onto u32
 __device__ __forceinline__ u32 ord32(int32_t p) { return (u32)p ^ 0x80000000u; }
-
-// Block-wide (sum, sum, min, max) of u32 values; every thread gets the result.
-// One barrier; two alternating buffers make back-to-back calls safe.
-struct Red4 {
-  u32 a, b, mn, mx;
-};
-__device__ __forceinline__ Red4 block_red4(u32 a, u32 b, u32 mn, u32 mx, uint4 (*s)[kLobWarps], int& par) {
-  a = __reduce_add_sync(0xFFFFFFFFu, a);
-  b = __reduce_add_sync(0xFFFFFFFFu, b);
-  mn = __reduce_min_sync(0xFFFFFFFFu, mn);
-  mx = __reduce_max_sync(0xFFFFFFFFu, mx);
-  if ((threadIdx.x & 31) == 0) s[par][threadIdx.x >> 5] = make_uint4(a, b, mn, mx);
-  __syncthreads();
-  Red4 r{0u, 0u, 0xFFFFFFFFu, 0u};
-#pragma unroll
-  for (int w = 0; w < kLobWarps; ++w) {
-    const uint4 v = s[par][w];
-    r.a += v.x;
-    r.b += v.y;
-    r.mn = min(r.mn, v.z);
-    r.mx = max(r.mx, v.w);
-  }
-  par ^= 1;
-  return r;
-}
 
 // Block-wide exclusive scan of a u64 (every thread gets its prefix and the
 // total). Three barriers; the buffer is free again when it returns.
@@ -114,7 +91,7 @@ __device__ __forceinline__ u64 block_sum_scan_u64(u64 v, u64& total, u64* s_warp
   return ex;
 }
 
-// One book's staged words in shared memory (n entries each; slots >= cap hold
+// One book's words in shared memory (n entries each; slots >= cap hold
 // active = 0).
 struct LobBook {
   int32_t* act;
@@ -122,23 +99,6 @@ struct LobBook {
   int32_t* px;
   int32_t* qt;
 };
-
-// Book b's words into the staging buffer (asynchronous; the caller commits).
-template <bool kVec16>
-__device__ __forceinline__ void lob_issue(const LobBook& d, int b, int cap, const int32_t* active,
-                                          const int32_t* side, const int32_t* price, const int32_t* qty) {
-  const size_t o = (size_t)b * cap;
-  const int32_t* src[4] = {active + o, side + o, price + o, qty + o};
-  int32_t* dst[4] = {d.act, d.sid, d.px, d.qt};
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    if (kVec16) {
-      for (int c = threadIdx.x; c < (cap >> 2); c += kLobThreads) cp_async16(dst[a] + 4 * c, src[a] + 4 * c);
-    } else {
-      for (int c = threadIdx.x; c < cap; c += kLobThreads) cp_async4(dst[a] + c, src[a] + c);
-    }
-  }
-}
 
 // The sort path for one book (see the file comment). n = R * kLobThreads
 // padded slots; key/cum share one u64 array and ord a u32 array, both [n], in
@@ -238,211 +198,297 @@ __device__ void lob_match_sorted(const LobBook& d, int n, int b, int cap, int nb
   }
 }
 
-// Dynamic shared memory: two staging buffers of 4 * n int32, then the work
-// area (level tables and marginal lists, or the sort path's key/ord arrays).
-template <int R, bool kVec16>
-__global__ void __launch_bounds__(kLobThreads, R >= 8 ? 2 : 4)
-    k_lob_match(int n_books, int cap, int32_t* active, const int32_t* __restrict__ side,
-                const int32_t* __restrict__ price, int32_t* qty, const int32_t* __restrict__ time,
-                long long* out_volume, int32_t* out_price) {
-  constexpr int n = R * kLobThreads;
-  extern __shared__ __align__(16) unsigned char lob_smem[];
-  int32_t* stage = reinterpret_cast<int32_t*>(lob_smem);
-  auto staged = [&](int s) -> LobBook {
-    int32_t* q = stage + 4 * n * s;
-    return LobBook{q, q + n, q + 2 * n, q + 3 * n};
-  };
-  unsigned char* work = lob_smem + 8 * (size_t)n * sizeof(int32_t);
-  u32* hb = reinterpret_cast<u32*>(work);  // bid shares per level, then D
-  u32* ha = hb + kLobLevels;               // ask shares per level, then S
-  u64* mk = reinterpret_cast<u64*>(ha + kLobLevels);  // marginal keys [2][kLobMarginal]
-  u32* mq = reinterpret_cast<u32*>(mk + 2 * kLobMarginal);  // marginal qty [2][kLobMarginal]
-  u64* skey = reinterpret_cast<u64*>(work);
-  u32* sord = reinterpret_cast<u32*>(skey + n);
-  __shared__ uint4 s_red[2][kLobWarps];
-  __shared__ u64 s_scan[2][kLobWarps + 1];
-  __shared__ int s_nm[2];
-  __shared__ unsigned long long s_v;
-  int par = 0, spar = 0;
+// Shared memory of one warp of the level path: the staged book (4 arrays of
+// capr = cap rounded up to 4 words), the level words of both sides, and the
+// marginal lists (slot, qty, key) of both sides.
+__host__ __device__ constexpr size_t warp_smem_bytes(int capr) {
+  return 16 * (size_t)capr + 2 * kWarpLevels * sizeof(u32) + 2 * kWarpMarginal * (2 * sizeof(u32) + sizeof(u64));
+}
 
-  // padding slots stay inactive in both buffers (the copies never reach them)
-  for (int i = cap + threadIdx.x; i < n; i += kLobThreads) {
-    stage[i] = 0;
-    stage[4 * n + i] = 0;
-  }
-  if ((int)blockIdx.x < n_books) lob_issue<kVec16>(staged(0), blockIdx.x, cap, active, side, price, qty);
-  cp_async_commit();
-  int it = 0;
-  for (int b = blockIdx.x; b < n_books; b += gridDim.x, ++it) {
-    const LobBook d = staged(it & 1);
-    const int nxt = b + gridDim.x;
-    if (nxt < n_books) lob_issue<kVec16>(staged((it & 1) ^ 1), nxt, cap, active, side, price, qty);
-    cp_async_commit();
-    cp_async_wait_1();  // this thread's copies of book b have landed
-    __syncthreads();    // everyone's have
-    const size_t o = (size_t)b * cap;
-
-    // this thread's slots: live flag, side, price, qty
-    int32_t px[R];
-    u32 qv[R], fl[R];  // fl: bit 0 live, bit 1 ask
-    u32 big = 0, cnt = 0, mn = 0xFFFFFFFFu, mx = 0u;
+// Inclusive warp scan of a u32.
+__device__ __forceinline__ u32 warp_incl_scan(u32 v, int lane) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int i = threadIdx.x + r * kLobThreads;
-      const bool live = d.act[i] != 0;
-      const bool ask = d.sid[i] != 0;
-      px[r] = d.px[i];
-      qv[r] = (u32)d.qt[i];
-      fl[r] = live ? (ask ? 3u : 1u) : 0u;
-      if (live) {
-        big += qv[r] >= kLobQtyMax;
-        cnt += ask ? 0x10000u : 1u;  // bids in the low half, asks in the high half
-        if (ask) mn = min(mn, ord32(px[r]));
-        else mx = max(mx, ord32(px[r]));
+  for (int o = 1; o < 32; o <<= 1) {
+    const u32 t = __shfl_up_sync(0xFFFFFFFFu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// Level path, one warp per book; SPL = slots per lane (cap <= 32 * SPL).
+// Deferred books get out_volume = -1 and are left untouched.
+template <int SPL, bool kVec16>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    k_lob_match_warp(int n_books, int cap, int capr, int32_t* active, const int32_t* __restrict__ side,
+                     const int32_t* __restrict__ price, int32_t* qty, const int32_t* __restrict__ time,
+                     long long* out_volume, int32_t* out_price) {
+  constexpr int LPL = kWarpLevels / 32;  // levels per lane in the scan
+  extern __shared__ __align__(16) unsigned char lob_smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  unsigned char* base = lob_smem + wib * warp_smem_bytes(capr);
+  int32_t* s_act = reinterpret_cast<int32_t*>(base);
+  int32_t* s_sid = s_act + capr;
+  int32_t* s_px = s_act + 2 * capr;
+  int32_t* s_qt = s_act + 3 * capr;
+  u32* lvb = reinterpret_cast<u32*>(s_act + 4 * capr);  // bid level words, then D | orders << 21
+  u32* lva = lvb + kWarpLevels;                         // ask level words, then S | orders << 21
+  u32* m_slot = lva + kWarpLevels;                      // [2][kWarpMarginal]
+  u32* m_qty = m_slot + 2 * kWarpMarginal;              // [2][kWarpMarginal]
+  u64* m_key = reinterpret_cast<u64*>(m_qty + 2 * kWarpMarginal);  // [2][kWarpMarginal]
+  const u32 lt_mask = (1u << lane) - 1u;
+  const int gw = blockIdx.x * kWarpsPerBlock + wib, nw = gridDim.x * kWarpsPerBlock;
+  for (int b = gw; b < n_books; b += nw) {
+    const size_t o = (size_t)b * cap;
+    // stage the book (this warp's region only; the last loop iteration ended
+    // with a __syncwarp, so nobody still reads it)
+    if (kVec16) {
+      for (int c = lane; c < (cap >> 2); c += 32) {
+        cp_async16(s_act + 4 * c, active + o + 4 * c);
+        cp_async16(s_sid + 4 * c, side + o + 4 * c);
+        cp_async16(s_px + 4 * c, price + o + 4 * c);
+        cp_async16(s_qt + 4 * c, qty + o + 4 * c);
+      }
+    } else {
+      for (int c = lane; c < cap; c += 32) {
+        cp_async4(s_act + c, active + o + c);
+        cp_async4(s_sid + c, side + o + c);
+        cp_async4(s_px + c, price + o + c);
+        cp_async4(s_qt + c, qty + o + c);
       }
     }
-    const Red4 r1 = block_red4(big, cnt, mn, mx, s_red, par);
-    const int nbid = (int)(r1.b & 0xFFFFu), nask = (int)(r1.b >> 16);
-    const int32_t pmin = (int32_t)(r1.mn ^ 0x80000000u), pmax = (int32_t)(r1.mx ^ 0x80000000u);
-    const bool cross = nbid > 0 && nask > 0 && r1.mx >= r1.mn;
-    const long long L = cross ? (long long)pmax - (long long)pmin + 1 : 0;
-    bool sorted = cross && (r1.a != 0 || L > kLobLevels);
-    u32 V = 0;
-    int32_t pa = 0, pb = 0;
-    u32 Dn = 0, Sp = 0;
-    if (cross && !sorted) {
-      // level path: share histograms of [pmin, pmax]
-      for (int l = threadIdx.x; l < L; l += kLobThreads) {
-        hb[l] = 0u;
-        ha[l] = 0u;
-      }
-      if (threadIdx.x == 0) {
-        s_nm[0] = 0;
-        s_nm[1] = 0;
-      }
-      __syncthreads();
+    cp_async_commit();
+    cp_async_wait_0();
+    __syncwarp();
+
+    // this lane's slots k * 32 + lane into registers: price and live | ask | qty
+    int32_t px[SPL];
+    u32 w[SPL];
+    u32 cnt = 0, mn = 0xFFFFFFFFu, mx = 0u, sb = 0, sa = 0, bad = 0, zq = 0;
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        if (!(fl[r] & 1u)) continue;
-        const bool ask = fl[r] & 2u;
-        if (ask ? px[r] <= pmax : px[r] >= pmin) atomicAdd((ask ? ha : hb) + (px[r] - pmin), qv[r]);
-      }
-      __syncthreads();
-      // D(l) = bid shares at levels >= l, S(l) = ask shares at levels <= l
-      u32 Dl[kLobLevelsPerThread], Sl[kLobLevelsPerThread];
-      u32 sb = 0, sa = 0;
-      const int l0 = threadIdx.x * kLobLevelsPerThread;
-#pragma unroll
-      for (int j = 0; j < kLobLevelsPerThread; ++j) {
-        Dl[j] = l0 + j < L ? hb[l0 + j] : 0u;
-        Sl[j] = l0 + j < L ? ha[l0 + j] : 0u;
-        sb += Dl[j];
-        sa += Sl[j];
-      }
-      // packed exclusive scan (both totals stay below 2^31)
-      const u64 v = ((u64)sb << 32) | sa;
-      u64 incl = v;
-      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-      for (int o2 = 1; o2 < 32; o2 <<= 1) {
-        const u64 t = __shfl_up_sync(0xFFFFFFFFu, incl, o2);
-        if (lane >= o2) incl += t;
-      }
-      if (lane == 31) s_scan[spar][warp] = incl;
-      __syncthreads();
-      u64 ex = incl - v, tot = 0;
-#pragma unroll
-      for (int w = 0; w < kLobWarps; ++w) {
-        const u64 t = s_scan[spar][w];
-        ex += w < warp ? t : 0ull;
-        tot += t;
-      }
-      spar ^= 1;
-      const u32 HB = (u32)(tot >> 32);
-      u32 pre_b = (u32)(ex >> 32), pre_a = (u32)ex, best = 0;
-#pragma unroll
-      for (int j = 0; j < kLobLevelsPerThread; ++j) {
-        const u32 hbj = Dl[j];
-        pre_a += Sl[j];
-        Dl[j] = HB - pre_b;
-        Sl[j] = pre_a;
-        pre_b += hbj;
-        if (l0 + j < L) {
-          hb[l0 + j] = Dl[j];
-          ha[l0 + j] = Sl[j];
-          best = max(best, min(Dl[j], Sl[j]));
+    for (int k = 0; k < SPL; ++k) {
+      const int i = k * 32 + lane;
+      px[k] = 0;
+      w[k] = 0;
+      if (i < cap && s_act[i] != 0) {
+        const int32_t p = s_px[i];
+        const u32 q = (u32)s_qt[i];
+        const bool ask = s_sid[i] != 0;
+        bad |= q > kShareMask;  // too large (or negative) for the level words
+        zq |= q == 0;
+        const u32 qm = q & kShareMask;
+        px[k] = p;
+        w[k] = kLive | (ask ? kAsk : 0u) | qm;
+        if (ask) {
+          cnt += 0x10000u;
+          sa += qm;
+          mn = min(mn, ord32(p));
+        } else {
+          cnt += 1u;
+          sb += qm;
+          mx = max(mx, ord32(p));
         }
       }
-      V = block_red4(0u, 0u, 0xFFFFFFFFu, best, s_red, par).mx;
+    }
+    // share sums saturate per lane, so the warp sums cannot wrap
+    cnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
+    const u32 SB = __reduce_add_sync(0xFFFFFFFFu, min(sb, 1u << kShareBits));
+    const u32 SA = __reduce_add_sync(0xFFFFFFFFu, min(sa, 1u << kShareBits));
+    mn = __reduce_min_sync(0xFFFFFFFFu, mn);
+    mx = __reduce_max_sync(0xFFFFFFFFu, mx);
+    bad = __any_sync(0xFFFFFFFFu, bad);
+    zq = __any_sync(0xFFFFFFFFu, zq);
+    const bool cross = (cnt & 0xFFFFu) != 0 && (cnt >> 16) != 0 && mx >= mn;
+    const int32_t pmin = (int32_t)(mn ^ 0x80000000u), pmax = (int32_t)(mx ^ 0x80000000u);
+    const long long L = cross ? (long long)pmax - (long long)pmin + 1 : 0;
+    if (cross && (bad || SB > kShareMask || SA > kShareMask || L > kWarpLevels)) {
+      if (lane == 0) out_volume[b] = -1;  // the sort path takes it
+      __syncwarp();
+      continue;
+    }
+    u32 V = 0;
+    int32_t pb = 0, pa = 0;
+    u32 Dn = 0, Sp = 0;
+    if (cross) {
+      for (int l = lane; l < L; l += 32) {
+        lvb[l] = 0u;
+        lva[l] = 0u;
+      }
+      __syncwarp();
+#pragma unroll
+      for (int k = 0; k < SPL; ++k) {
+        if (!(w[k] & kLive)) continue;
+        const bool ask = w[k] & kAsk;
+        if (ask ? px[k] <= pmax : px[k] >= pmin)
+          atomicAdd((ask ? lva : lvb) + (px[k] - pmin), (w[k] & kShareMask) | (1u << kShareBits));
+      }
+      __syncwarp();
+      // D(l) = bid shares at levels >= l, S(l) = ask shares at levels <= l;
+      // lane owns levels [LPL * lane, LPL * lane + LPL)
+      u32 hb[LPL], ha[LPL];
+      u32 tb = 0, ta = 0;
+      const int l0 = lane * LPL;
+#pragma unroll
+      for (int j = 0; j < LPL; ++j) {
+        hb[j] = l0 + j < L ? lvb[l0 + j] : 0u;
+        ha[j] = l0 + j < L ? lva[l0 + j] : 0u;
+        tb += hb[j] & kShareMask;
+        ta += ha[j] & kShareMask;
+      }
+      const u32 ib = warp_incl_scan(tb, lane), ia = warp_incl_scan(ta, lane);
+      const u32 BT = __shfl_sync(0xFFFFFFFFu, ib, 31);
+      u32 pre_b = ib - tb, pre_a = ia - ta, best = 0;
+      u32 Dl[LPL], Sl[LPL];
+#pragma unroll
+      for (int j = 0; j < LPL; ++j) {
+        Dl[j] = BT - pre_b;
+        pre_b += hb[j] & kShareMask;
+        pre_a += ha[j] & kShareMask;
+        Sl[j] = pre_a;
+        if (l0 + j < L) best = max(best, min(Dl[j], Sl[j]));
+      }
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < LPL; ++j) {
+        if (l0 + j < L) {
+          lvb[l0 + j] = Dl[j] | (hb[j] & ~kShareMask);
+          lva[l0 + j] = Sl[j] | (ha[j] & ~kShareMask);
+        }
+      }
+      V = __reduce_max_sync(0xFFFFFFFFu, best);
       if (V > 0) {
         // D falls and S rises with the level: count the levels at or above V
         u32 cb = 0, ca = 0;
 #pragma unroll
-        for (int j = 0; j < kLobLevelsPerThread; ++j) {
+        for (int j = 0; j < LPL; ++j) {
           cb += (l0 + j < L) && Dl[j] >= V;
           ca += (l0 + j < L) && Sl[j] >= V;
         }
-        const Red4 r3 = block_red4(cb, ca, 0xFFFFFFFFu, 0u, s_red, par);
-        const int lb = (int)r3.a - 1, la = (int)L - (int)r3.b;
+        const int lb = (int)__reduce_add_sync(0xFFFFFFFFu, cb) - 1;
+        const int la = (int)L - (int)__reduce_add_sync(0xFFFFFFFFu, ca);
+        __syncwarp();
+        if ((lvb[lb] >> kShareBits) > kWarpMarginal || (lva[la] >> kShareBits) > kWarpMarginal) {
+          if (lane == 0) out_volume[b] = -1;  // a crowded marginal level: the sort path takes it
+          __syncwarp();
+          continue;
+        }
         pb = pmin + lb;
         pa = pmin + la;
-        Dn = lb + 1 < L ? hb[lb + 1] : 0u;  // bid shares priced above pb
-        Sp = la > 0 ? ha[la - 1] : 0u;      // ask shares priced below pa
-        // the marginal orders, ranked by (time, slot) below
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          if (!(fl[r] & 1u) || qv[r] == 0) continue;
-          const int s = (fl[r] >> 1) & 1;
-          if (px[r] != (s ? pa : pb)) continue;
-          const int i = threadIdx.x + r * kLobThreads;
-          const int k = atomicAdd(&s_nm[s], 1);
-          if (k < kLobMarginal) {
-            mk[s * kLobMarginal + k] = ((u64)ord32(time[o + i]) << 32) | (u32)i;
-            mq[s * kLobMarginal + k] = qv[r];
-          }
-        }
-        __syncthreads();
-        sorted = s_nm[0] > kLobMarginal || s_nm[1] > kLobMarginal;
+        Dn = lb + 1 < L ? lvb[lb + 1] & kShareMask : 0u;  // bid shares priced above pb
+        Sp = la > 0 ? lva[la - 1] & kShareMask : 0u;      // ask shares priced below pa
       }
     }
-    if (sorted) {
-      lob_match_sorted(d, n, b, cap, nbid, nask, active, qty, time, out_volume, out_price, skey, sord,
-                       s_scan[0], &s_v);
-    } else {
-      if (threadIdx.x == 0) {
-        out_volume[b] = (long long)V;
-        out_price[b] = V > 0 ? pa : -1;
+    if (V == 0 && !zq) {
+      if (lane == 0) {
+        out_volume[b] = 0;
+        out_price[b] = -1;
+      }
+      __syncwarp();
+      continue;
+    }
+    // whole fills (and zero-qty orders) written here; marginal orders listed
+    int nm[2] = {0, 0};
+#pragma unroll
+    for (int k = 0; k < SPL; ++k) {
+      const int i = k * 32 + lane;
+      const bool live = w[k] & kLive, ask = w[k] & kAsk;
+      const u32 q = w[k] & kShareMask;
+      const bool whole = live && (q == 0 || (V > 0 && (ask ? px[k] < pa : px[k] > pb)));
+      const bool marg = live && q > 0 && V > 0 && px[k] == (ask ? pa : pb);
+      if (whole) {
+        qty[o + i] = 0;
+        active[o + i] = 0;
       }
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        if (!(fl[r] & 1u)) continue;
-        const int i = threadIdx.x + r * kLobThreads;
-        const bool ask = fl[r] & 2u;
-        const u32 q = qv[r];
-        u32 fill = 0;
-        if (V > 0 && q > 0) {
-          const int32_t edge = ask ? pa : pb;
-          const bool whole = ask ? px[r] < edge : px[r] > edge;
-          if (whole) {
-            fill = q;
-          } else if (px[r] == edge) {
-            const int s = ask ? 1 : 0;
-            const u64 mine = ((u64)ord32(time[o + i]) << 32) | (u32)i;
-            u32 before = ask ? Sp : Dn;
-            const int m = s_nm[s];
-            for (int e = 0; e < m; ++e) before += mk[s * kLobMarginal + e] < mine ? mq[s * kLobMarginal + e] : 0u;
-            fill = V > before ? min(V - before, q) : 0u;
-          }
+      for (int s = 0; s < 2; ++s) {
+        const bool mine = marg && (ask == (s == 1));
+        const u32 bal = __ballot_sync(0xFFFFFFFFu, mine);
+        if (mine) {
+          const int pos = nm[s] + __popc(bal & lt_mask);
+          m_slot[s * kWarpMarginal + pos] = (u32)i;
+          m_qty[s * kWarpMarginal + pos] = q;
         }
-        if (fill || q == 0) {
-          qty[o + i] = (int32_t)(q - fill);
-          if (q == fill) active[o + i] = 0;
+        nm[s] += __popc(bal);
+      }
+    }
+    __syncwarp();
+    if (V > 0) {
+#pragma unroll
+      for (int s = 0; s < 2; ++s)
+        for (int e = lane; e < nm[s]; e += 32) {
+          const u32 slot = m_slot[s * kWarpMarginal + e];
+          m_key[s * kWarpMarginal + e] = ((u64)ord32(time[o + slot]) << 32) | slot;
+        }
+      __syncwarp();
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const u32* mq = m_qty + s * kWarpMarginal;
+        const u64* mk = m_key + s * kWarpMarginal;
+        for (int e = lane; e < nm[s]; e += 32) {
+          const u64 mine = mk[e];
+          u32 before = s ? Sp : Dn;
+          for (int f = 0; f < nm[s]; ++f) before += mk[f] < mine ? mq[f] : 0u;
+          const u32 q = mq[e];
+          const u32 fill = V > before ? min(V - before, q) : 0u;
+          if (fill) {
+            const u32 slot = (u32)mine;
+            qty[o + slot] = (int32_t)(q - fill);
+            if (fill == q) active[o + slot] = 0;
+          }
         }
       }
     }
-    __syncthreads();  // the staging buffer and work area are reused
+    if (lane == 0) {
+      out_volume[b] = (long long)V;
+      out_price[b] = V > 0 ? pa : -1;
+    }
+    __syncwarp();
   }
-  cp_async_wait_0();
+}
+
+// Sort path for the books the level path deferred (out_volume < 0), one CTA
+// per book; n = R * kLobThreads padded slots. Shared memory: the book's words
+// (4 x n int32), then key u64[n] and ord u32[n].
+template <int R>
+__global__ void __launch_bounds__(kLobThreads)
+    k_lob_deferred(int n_books, int cap, int32_t* active, const int32_t* __restrict__ side,
+                   const int32_t* __restrict__ price, int32_t* qty, const int32_t* __restrict__ time,
+                   long long* out_volume, int32_t* out_price) {
+  constexpr int n = R * kLobThreads;
+  extern __shared__ __align__(16) unsigned char lob_smem[];
+  int32_t* w = reinterpret_cast<int32_t*>(lob_smem);
+  const LobBook d{w, w + n, w + 2 * n, w + 3 * n};
+  u64* key = reinterpret_cast<u64*>(w + 4 * n);
+  u32* ord = reinterpret_cast<u32*>(key + n);
+  __shared__ int s_list[kLobThreads];
+  __shared__ int s_cnt;
+  __shared__ u64 s_scan[kLobWarps + 1];
+  __shared__ unsigned long long s_v;
+  for (int c0 = blockIdx.x * kLobThreads; c0 < n_books; c0 += gridDim.x * kLobThreads) {
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    const int bq = c0 + threadIdx.x;
+    if (bq < n_books && out_volume[bq] < 0) s_list[atomicAdd(&s_cnt, 1)] = bq;
+    __syncthreads();
+    const int m = s_cnt;
+    for (int j = 0; j < m; ++j) {
+      const int b = s_list[j];
+      const size_t o = (size_t)b * cap;
+      int nbid = 0, nask = 0;
+      for (int i = threadIdx.x; i < n; i += kLobThreads) {
+        const bool in = i < cap;
+        const int32_t a = in ? active[o + i] : 0;
+        const int32_t s = in ? side[o + i] : 0;
+        d.act[i] = a;
+        d.sid[i] = s;
+        d.px[i] = in ? price[o + i] : 0;
+        d.qt[i] = in ? qty[o + i] : 0;
+        nbid += __syncthreads_count(a != 0 && s == 0);
+        nask += __syncthreads_count(a != 0 && s != 0);
+      }
+      lob_match_sorted(d, n, b, cap, nbid, nask, active, qty, time, out_volume, out_price, key, ord, s_scan, &s_v);
+      __syncthreads();  // shared arrays are reused by the next book
+    }
+  }
 }
 
 // new orders into each book's lowest free slots: order j < k[b] -> j-th free
@@ -477,40 +523,66 @@ __global__ void __launch_bounds__(kLobThreads) k_lob_add(int n_books, int cap, i
   }
 }
 
+
 static int lob_pad(int cap) {
   int n = kLobThreads;
   while (n < cap) n <<= 1;
   return n;
 }
 
-static size_t lob_smem_bytes(int n) {
-  return 8 * (size_t)n * sizeof(int32_t) + std::max(kLobLevelBytes, (size_t)n * (sizeof(u64) + sizeof(u32)));
-}
-
-template <int R, bool kVec16>
-static abm_status lob_launch(int n_books, int cap, int32_t* active, const int32_t* side, const int32_t* price,
-                             int32_t* qty, const int32_t* time, long long* vol, int32_t* px, cudaStream_t st) {
-  static int grid_per_sm = 0;
-  const size_t smem = lob_smem_bytes(R * kLobThreads);
-  if (!grid_per_sm) {
-    ABM_CUDA_TRY(cudaFuncSetAttribute(k_lob_match<R, kVec16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
+template <int SPL, bool kVec16>
+static abm_status lob_launch_warp(int n_books, int cap, int32_t* active, const int32_t* side, const int32_t* price,
+                                  int32_t* qty, const int32_t* time, long long* vol, int32_t* px, cudaStream_t st) {
+  static int blocks_per_sm = 0, for_capr = -1;
+  const int capr = (cap + 3) & ~3;
+  const size_t smem = kWarpsPerBlock * warp_smem_bytes(capr);
+  if (for_capr != capr) {
+    ABM_CUDA_TRY(cudaFuncSetAttribute(k_lob_match_warp<SPL, kVec16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(kWarpsPerBlock * warp_smem_bytes(32 * SPL))));
     int occ = 0;
-    ABM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lob_match<R, kVec16>, kLobThreads, smem));
-    grid_per_sm = std::max(occ, 1);
+    ABM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lob_match_warp<SPL, kVec16>,
+                                                               kWarpsPerBlock * 32, smem));
+    blocks_per_sm = std::max(occ, 1);
+    for_capr = capr;
   }
-  const int grid = (int)std::min<long long>(n_books, (long long)num_sms() * grid_per_sm);
-  k_lob_match<R, kVec16><<<grid, kLobThreads, smem, st>>>(n_books, cap, active, side, price, qty, time, vol, px);
+  const long long want = ((long long)n_books + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  const int grid = (int)std::min<long long>(want, (long long)num_sms() * blocks_per_sm);
+  k_lob_match_warp<SPL, kVec16><<<grid, kWarpsPerBlock * 32, smem, st>>>(n_books, cap, capr, active, side, price,
+                                                                          qty, time, vol, px);
   ABM_LAUNCH_CHECK();
   return ABM_OK;
 }
 
 template <int R>
-static abm_status lob_launch_r(bool vec16, int n_books, int cap, int32_t* active, const int32_t* side,
-                               const int32_t* price, int32_t* qty, const int32_t* time, long long* vol, int32_t* px,
-                               cudaStream_t st) {
-  return vec16 ? lob_launch<R, true>(n_books, cap, active, side, price, qty, time, vol, px, st)
-               : lob_launch<R, false>(n_books, cap, active, side, price, qty, time, vol, px, st);
+static abm_status lob_launch_deferred(int n_books, int cap, int32_t* active, const int32_t* side,
+                                      const int32_t* price, int32_t* qty, const int32_t* time, long long* vol,
+                                      int32_t* px, cudaStream_t st) {
+  constexpr size_t smem = (size_t)R * kLobThreads * (4 * sizeof(int32_t) + sizeof(u64) + sizeof(u32));
+  static bool attr = false;
+  if (!attr) {
+    ABM_CUDA_TRY(cudaFuncSetAttribute(k_lob_deferred<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  const long long chunks = ((long long)n_books + kLobThreads - 1) / kLobThreads;
+  const int grid = (int)std::min<long long>(chunks, (long long)num_sms() * 2);
+  k_lob_deferred<R><<<grid, kLobThreads, smem, st>>>(n_books, cap, active, side, price, qty, time, vol, px);
+  ABM_LAUNCH_CHECK();
+  return ABM_OK;
+}
+
+template <int SPL>
+static abm_status lob_launch(bool vec16, int n_books, int cap, int32_t* active, const int32_t* side,
+                             const int32_t* price, int32_t* qty, const int32_t* time, long long* vol, int32_t* px,
+                             cudaStream_t st) {
+  abm_status e = vec16 ? lob_launch_warp<SPL, true>(n_books, cap, active, side, price, qty, time, vol, px, st)
+                       : lob_launch_warp<SPL, false>(n_books, cap, active, side, price, qty, time, vol, px, st);
+  if (e != ABM_OK) return e;
+  switch (lob_pad(cap) / kLobThreads) {
+    case 1: return lob_launch_deferred<1>(n_books, cap, active, side, price, qty, time, vol, px, st);
+    case 2: return lob_launch_deferred<2>(n_books, cap, active, side, price, qty, time, vol, px, st);
+    case 4: return lob_launch_deferred<4>(n_books, cap, active, side, price, qty, time, vol, px, st);
+    default: return lob_launch_deferred<8>(n_books, cap, active, side, price, qty, time, vol, px, st);
+  }
 }
 
 }  // namespace abm
@@ -528,12 +600,10 @@ extern "C" abm_status abm_lob_match(int32_t n_books, int32_t cap, int32_t* activ
       cap % 4 == 0 && ((uintptr_t)active | (uintptr_t)side | (uintptr_t)price | (uintptr_t)qty) % 16 == 0;
   long long* vol = reinterpret_cast<long long*>(out_volume);
   const cudaStream_t st = (cudaStream_t)stream;
-  switch (lob_pad(cap) / kLobThreads) {
-    case 1: return lob_launch_r<1>(vec16, n_books, cap, active, side, price, qty, time, vol, out_price, st);
-    case 2: return lob_launch_r<2>(vec16, n_books, cap, active, side, price, qty, time, vol, out_price, st);
-    case 4: return lob_launch_r<4>(vec16, n_books, cap, active, side, price, qty, time, vol, out_price, st);
-    default: return lob_launch_r<8>(vec16, n_books, cap, active, side, price, qty, time, vol, out_price, st);
-  }
+  if (cap <= 256) return lob_launch<8>(vec16, n_books, cap, active, side, price, qty, time, vol, out_price, st);
+  if (cap <= 512) return lob_launch<16>(vec16, n_books, cap, active, side, price, qty, time, vol, out_price, st);
+  if (cap <= 1024) return lob_launch<32>(vec16, n_books, cap, active, side, price, qty, time, vol, out_price, st);
+  return lob_launch<64>(vec16, n_books, cap, active, side, price, qty, time, vol, out_price, st);
 }
 
 extern "C" abm_status abm_lob_add(int32_t n_books, int32_t cap, int32_t* active, int32_t* side, int32_t* price,
