@@ -19,8 +19,8 @@
 // reach V. Only prices in [lowest ask, highest bid] matter.
 //
 // Level path (k_lob_match_warp): one warp per book. The warp stages the book's
-// active, side, price and qty words into shared memory with cp.async, keeps
-// each lane's slots in registers, builds per-price histograms of the range
+// active, side, price and qty words into shared memory with cp.async, moves
+// each lane's slots into registers (and starts staging its next book), builds per-price histograms of the range
 // (shares | orders << 21, one shared atomic per order), scans them into D and
 // S, and takes V, the bid level pb holding share V (largest p with D(p) >= V)
 // and the ask level pa holding it (smallest p with S(p) >= V). Bids above pb
@@ -199,10 +199,10 @@ __device__ void lob_match_sorted(const LobBook& d, int n, int b, int cap, int nb
 }
 
 // Shared memory of one warp of the level path: the staged book (4 arrays of
-// capr = cap rounded up to 4 words), the level words of both sides, and the
-// marginal lists (slot, qty, key) of both sides.
-__host__ __device__ constexpr size_t warp_smem_bytes(int capr) {
-  return 16 * (size_t)capr + 2 * kWarpLevels * sizeof(u32) + 2 * kWarpMarginal * (2 * sizeof(u32) + sizeof(u64));
+// 32 * SPL words; slots >= cap hold active = 0), the level words of both
+// sides, and the marginal lists (slot, qty, key) of both sides.
+__host__ __device__ constexpr size_t warp_smem_bytes(int spl) {
+  return 16 * 32 * (size_t)spl + 2 * kWarpLevels * sizeof(u32) + 2 * kWarpMarginal * (2 * sizeof(u32) + sizeof(u64));
 }
 
 // Inclusive warp scan of a u32.
@@ -215,80 +215,91 @@ __device__ __forceinline__ u32 warp_incl_scan(u32 v, int lane) {
   return v;
 }
 
-// Level path, one warp per book; SPL = slots per lane (cap <= 32 * SPL).
-// Deferred books get out_volume = -1 and are left untouched.
+// Book b's words into the warp's staging arrays (asynchronous; committed).
+template <bool kVec16>
+__device__ __forceinline__ void warp_stage(int32_t* s_act, int n, int b, int cap, int lane, const int32_t* active,
+                                           const int32_t* side, const int32_t* price, const int32_t* qty) {
+  const size_t o = (size_t)b * cap;
+  if (kVec16) {
+    for (int c = lane; c < (cap >> 2); c += 32) {
+      cp_async16(s_act + 4 * c, active + o + 4 * c);
+      cp_async16(s_act + n + 4 * c, side + o + 4 * c);
+      cp_async16(s_act + 2 * n + 4 * c, price + o + 4 * c);
+      cp_async16(s_act + 3 * n + 4 * c, qty + o + 4 * c);
+    }
+  } else {
+    for (int c = lane; c < cap; c += 32) {
+      cp_async4(s_act + c, active + o + c);
+      cp_async4(s_act + n + c, side + o + c);
+      cp_async4(s_act + 2 * n + c, price + o + c);
+      cp_async4(s_act + 3 * n + c, qty + o + c);
+    }
+  }
+  cp_async_commit();
+}
+
+// Level path, one warp per book; SPL = slots per lane (cap <= 32 * SPL), a
+// lane holding slots 4 * (g * 32 + lane) + c. The next book is staged as soon
+// as this one's words are in registers. Deferred books get out_volume = -1
+// and are left untouched.
 template <int SPL, bool kVec16>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
-    k_lob_match_warp(int n_books, int cap, int capr, int32_t* active, const int32_t* __restrict__ side,
+    k_lob_match_warp(int n_books, int cap, int32_t* active, const int32_t* __restrict__ side,
                      const int32_t* __restrict__ price, int32_t* qty, const int32_t* __restrict__ time,
                      long long* out_volume, int32_t* out_price) {
   constexpr int LPL = kWarpLevels / 32;  // levels per lane in the scan
+  constexpr int n = 32 * SPL;            // staged words per array
   extern __shared__ __align__(16) unsigned char lob_smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  unsigned char* base = lob_smem + wib * warp_smem_bytes(capr);
-  int32_t* s_act = reinterpret_cast<int32_t*>(base);
-  int32_t* s_sid = s_act + capr;
-  int32_t* s_px = s_act + 2 * capr;
-  int32_t* s_qt = s_act + 3 * capr;
-  u32* lvb = reinterpret_cast<u32*>(s_act + 4 * capr);  // bid level words, then D | orders << 21
-  u32* lva = lvb + kWarpLevels;                         // ask level words, then S | orders << 21
-  u32* m_slot = lva + kWarpLevels;                      // [2][kWarpMarginal]
-  u32* m_qty = m_slot + 2 * kWarpMarginal;              // [2][kWarpMarginal]
+  unsigned char* base = lob_smem + wib * warp_smem_bytes(SPL);
+  int32_t* s_act = reinterpret_cast<int32_t*>(base);  // then side, price, qty at +n, +2n, +3n
+  u32* lvb = reinterpret_cast<u32*>(s_act + 4 * n);   // bid level words, then D | orders << 21
+  u32* lva = lvb + kWarpLevels;                       // ask level words, then S | orders << 21
+  u32* m_slot = lva + kWarpLevels;                    // [2][kWarpMarginal]
+  u32* m_qty = m_slot + 2 * kWarpMarginal;            // [2][kWarpMarginal]
   u64* m_key = reinterpret_cast<u64*>(m_qty + 2 * kWarpMarginal);  // [2][kWarpMarginal]
   const u32 lt_mask = (1u << lane) - 1u;
   const int gw = blockIdx.x * kWarpsPerBlock + wib, nw = gridDim.x * kWarpsPerBlock;
+  for (int i = cap + lane; i < n; i += 32) s_act[i] = 0;  // padding slots: never copied, never live
+  if (gw < n_books) warp_stage<kVec16>(s_act, n, gw, cap, lane, active, side, price, qty);
   for (int b = gw; b < n_books; b += nw) {
     const size_t o = (size_t)b * cap;
-    // stage the book (this warp's region only; the last loop iteration ended
-    // with a __syncwarp, so nobody still reads it)
-    if (kVec16) {
-      for (int c = lane; c < (cap >> 2); c += 32) {
-        cp_async16(s_act + 4 * c, active + o + 4 * c);
-        cp_async16(s_sid + 4 * c, side + o + 4 * c);
-        cp_async16(s_px + 4 * c, price + o + 4 * c);
-        cp_async16(s_qt + 4 * c, qty + o + 4 * c);
-      }
-    } else {
-      for (int c = lane; c < cap; c += 32) {
-        cp_async4(s_act + c, active + o + c);
-        cp_async4(s_sid + c, side + o + c);
-        cp_async4(s_px + c, price + o + c);
-        cp_async4(s_qt + c, qty + o + c);
-      }
-    }
-    cp_async_commit();
     cp_async_wait_0();
     __syncwarp();
 
-    // this lane's slots k * 32 + lane into registers: price and live | ask | qty
+    // this lane's slots into registers: price and live | ask | qty
     int32_t px[SPL];
     u32 w[SPL];
     u32 cnt = 0, mn = 0xFFFFFFFFu, mx = 0u, sb = 0, sa = 0, bad = 0, zq = 0;
 #pragma unroll
-    for (int k = 0; k < SPL; ++k) {
-      const int i = k * 32 + lane;
-      px[k] = 0;
-      w[k] = 0;
-      if (i < cap && s_act[i] != 0) {
-        const int32_t p = s_px[i];
-        const u32 q = (u32)s_qt[i];
-        const bool ask = s_sid[i] != 0;
-        bad |= q > kShareMask;  // too large (or negative) for the level words
-        zq |= q == 0;
-        const u32 qm = q & kShareMask;
-        px[k] = p;
-        w[k] = kLive | (ask ? kAsk : 0u) | qm;
-        if (ask) {
-          cnt += 0x10000u;
-          sa += qm;
-          mn = min(mn, ord32(p));
-        } else {
-          cnt += 1u;
-          sb += qm;
-          mx = max(mx, ord32(p));
-        }
+    for (int g = 0; g < SPL / 4; ++g) {
+      const int v = g * 32 + lane;
+      const int4 a4 = reinterpret_cast<const int4*>(s_act)[v];
+      const int4 s4 = reinterpret_cast<const int4*>(s_act + n)[v];
+      const int4 p4 = reinterpret_cast<const int4*>(s_act + 2 * n)[v];
+      const int4 q4 = reinterpret_cast<const int4*>(s_act + 3 * n)[v];
+      const int av[4] = {a4.x, a4.y, a4.z, a4.w}, sv[4] = {s4.x, s4.y, s4.z, s4.w};
+      const int pv[4] = {p4.x, p4.y, p4.z, p4.w}, qv[4] = {q4.x, q4.y, q4.z, q4.w};
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int k = 4 * g + c;
+        const bool live = av[c] != 0, ask = sv[c] != 0;
+        const bool lbid = live && !ask, lask = live && ask;
+        const u32 q = (u32)qv[c], qm = q & kShareMask;
+        bad |= (u32)(live && q > kShareMask);  // too large (or negative) for the level words
+        zq |= (u32)(live && q == 0);
+        px[k] = pv[c];
+        w[k] = live ? (kLive | (ask ? kAsk : 0u) | qm) : 0u;
+        cnt += lask ? 0x10000u : (lbid ? 1u : 0u);
+        sa += lask ? qm : 0u;
+        sb += lbid ? qm : 0u;
+        mn = min(mn, lask ? ord32(pv[c]) : 0xFFFFFFFFu);
+        mx = max(mx, lbid ? ord32(pv[c]) : 0u);
       }
     }
+    __syncwarp();  // the staging arrays are free: stage the next book
+    if (b + nw < n_books) warp_stage<kVec16>(s_act, n, b + nw, cap, lane, active, side, price, qty);
+
     // share sums saturate per lane, so the warp sums cannot wrap
     cnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
     const u32 SB = __reduce_add_sync(0xFFFFFFFFu, min(sb, 1u << kShareBits));
@@ -302,7 +313,6 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     const long long L = cross ? (long long)pmax - (long long)pmin + 1 : 0;
     if (cross && (bad || SB > kShareMask || SA > kShareMask || L > kWarpLevels)) {
       if (lane == 0) out_volume[b] = -1;  // the sort path takes it
-      __syncwarp();
       continue;
     }
     u32 V = 0;
@@ -316,10 +326,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
       __syncwarp();
 #pragma unroll
       for (int k = 0; k < SPL; ++k) {
-        if (!(w[k] & kLive)) continue;
         const bool ask = w[k] & kAsk;
-        if (ask ? px[k] <= pmax : px[k] >= pmin)
-          atomicAdd((ask ? lva : lvb) + (px[k] - pmin), (w[k] & kShareMask) | (1u << kShareBits));
+        const bool in = (w[k] & kLive) && (ask ? px[k] <= pmax : px[k] >= pmin);
+        if (in) atomicAdd((ask ? lva : lvb) + (px[k] - pmin), (w[k] & kShareMask) | (1u << kShareBits));
       }
       __syncwarp();
       // D(l) = bid shares at levels >= l, S(l) = ask shares at levels <= l;
@@ -368,7 +377,6 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
         __syncwarp();
         if ((lvb[lb] >> kShareBits) > kWarpMarginal || (lva[la] >> kShareBits) > kWarpMarginal) {
           if (lane == 0) out_volume[b] = -1;  // a crowded marginal level: the sort path takes it
-          __syncwarp();
           continue;
         }
         pb = pmin + lb;
@@ -382,14 +390,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
         out_volume[b] = 0;
         out_price[b] = -1;
       }
-      __syncwarp();
       continue;
     }
     // whole fills (and zero-qty orders) written here; marginal orders listed
-    int nm[2] = {0, 0};
+    int nm0 = 0, nm1 = 0;
 #pragma unroll
     for (int k = 0; k < SPL; ++k) {
-      const int i = k * 32 + lane;
+      const int i = 4 * ((k >> 2) * 32 + lane) + (k & 3);
       const bool live = w[k] & kLive, ask = w[k] & kAsk;
       const u32 q = w[k] & kShareMask;
       const bool whole = live && (q == 0 || (V > 0 && (ask ? px[k] < pa : px[k] > pb)));
@@ -398,42 +405,39 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
         qty[o + i] = 0;
         active[o + i] = 0;
       }
-#pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        const bool mine = marg && (ask == (s == 1));
-        const u32 bal = __ballot_sync(0xFFFFFFFFu, mine);
-        if (mine) {
-          const int pos = nm[s] + __popc(bal & lt_mask);
+      if (__any_sync(0xFFFFFFFFu, marg)) {
+        const u32 bal_b = __ballot_sync(0xFFFFFFFFu, marg && !ask), bal_a = __ballot_sync(0xFFFFFFFFu, marg && ask);
+        if (marg) {
+          const int s = ask ? 1 : 0;
+          const int pos = (ask ? nm1 + __popc(bal_a & lt_mask) : nm0 + __popc(bal_b & lt_mask));
           m_slot[s * kWarpMarginal + pos] = (u32)i;
           m_qty[s * kWarpMarginal + pos] = q;
         }
-        nm[s] += __popc(bal);
+        nm0 += __popc(bal_b);
+        nm1 += __popc(bal_a);
       }
     }
     __syncwarp();
     if (V > 0) {
-#pragma unroll
-      for (int s = 0; s < 2; ++s)
-        for (int e = lane; e < nm[s]; e += 32) {
-          const u32 slot = m_slot[s * kWarpMarginal + e];
-          m_key[s * kWarpMarginal + e] = ((u64)ord32(time[o + slot]) << 32) | slot;
-        }
+      for (int e = lane; e < nm0 + nm1; e += 32) {
+        const int s = e >= nm0, f = e - (s ? nm0 : 0);
+        const u32 slot = m_slot[s * kWarpMarginal + f];
+        m_key[s * kWarpMarginal + f] = ((u64)ord32(time[o + slot]) << 32) | slot;
+      }
       __syncwarp();
-#pragma unroll
-      for (int s = 0; s < 2; ++s) {
+      for (int e = lane; e < nm0 + nm1; e += 32) {
+        const int s = e >= nm0, f = e - (s ? nm0 : 0), m = s ? nm1 : nm0;
         const u32* mq = m_qty + s * kWarpMarginal;
         const u64* mk = m_key + s * kWarpMarginal;
-        for (int e = lane; e < nm[s]; e += 32) {
-          const u64 mine = mk[e];
-          u32 before = s ? Sp : Dn;
-          for (int f = 0; f < nm[s]; ++f) before += mk[f] < mine ? mq[f] : 0u;
-          const u32 q = mq[e];
-          const u32 fill = V > before ? min(V - before, q) : 0u;
-          if (fill) {
-            const u32 slot = (u32)mine;
-            qty[o + slot] = (int32_t)(q - fill);
-            if (fill == q) active[o + slot] = 0;
-          }
+        const u64 mine = mk[f];
+        u32 before = s ? Sp : Dn;
+        for (int h = 0; h < m; ++h) before += mk[h] < mine ? mq[h] : 0u;
+        const u32 q = mq[f];
+        const u32 fill = V > before ? min(V - before, q) : 0u;
+        if (fill) {
+          const u32 slot = (u32)mine;
+          qty[o + slot] = (int32_t)(q - fill);
+          if (fill == q) active[o + slot] = 0;
         }
       }
     }
@@ -441,8 +445,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
       out_volume[b] = (long long)V;
       out_price[b] = V > 0 ? pa : -1;
     }
-    __syncwarp();
   }
+  cp_async_wait_0();
 }
 
 // Sort path for the books the level path deferred (out_volume < 0), one CTA
@@ -533,22 +537,20 @@ static int lob_pad(int cap) {
 template <int SPL, bool kVec16>
 static abm_status lob_launch_warp(int n_books, int cap, int32_t* active, const int32_t* side, const int32_t* price,
                                   int32_t* qty, const int32_t* time, long long* vol, int32_t* px, cudaStream_t st) {
-  static int blocks_per_sm = 0, for_capr = -1;
-  const int capr = (cap + 3) & ~3;
-  const size_t smem = kWarpsPerBlock * warp_smem_bytes(capr);
-  if (for_capr != capr) {
+  static int blocks_per_sm = 0;
+  const size_t smem = kWarpsPerBlock * warp_smem_bytes(SPL);
+  if (!blocks_per_sm) {
     ABM_CUDA_TRY(cudaFuncSetAttribute(k_lob_match_warp<SPL, kVec16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(kWarpsPerBlock * warp_smem_bytes(32 * SPL))));
+                                      (int)smem));
     int occ = 0;
     ABM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lob_match_warp<SPL, kVec16>,
                                                                kWarpsPerBlock * 32, smem));
     blocks_per_sm = std::max(occ, 1);
-    for_capr = capr;
   }
   const long long want = ((long long)n_books + kWarpsPerBlock - 1) / kWarpsPerBlock;
   const int grid = (int)std::min<long long>(want, (long long)num_sms() * blocks_per_sm);
-  k_lob_match_warp<SPL, kVec16><<<grid, kWarpsPerBlock * 32, smem, st>>>(n_books, cap, capr, active, side, price,
-                                                                          qty, time, vol, px);
+  k_lob_match_warp<SPL, kVec16><<<grid, kWarpsPerBlock * 32, smem, st>>>(n_books, cap, active, side, price, qty,
+                                                                          time, vol, px);
   ABM_LAUNCH_CHECK();
   return ABM_OK;
 }
