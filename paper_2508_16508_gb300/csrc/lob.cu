@@ -33,6 +33,7 @@
 // to -1) and matched by a second kernel, one CTA per book: bitonic sort of the
 // whole book in shared memory, cumulative sums, a binary search per bid.
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -200,10 +201,15 @@ __device__ void lob_match_sorted(const LobBook& d, int n, int b, int cap, int nb
 
 // Shared memory of one warp of the level path: the staged book (4 arrays of
 // 32 * SPL words; slots >= cap hold active = 0), the level words of both
-// sides, and the marginal lists (slot, qty, key) of both sides.
+// sides, and the marginal lists (qty, key = time | slot) of both sides.
 __host__ __device__ constexpr size_t warp_smem_bytes(int spl) {
-  return 16 * 32 * (size_t)spl + 2 * kWarpLevels * sizeof(u32) + 2 * kWarpMarginal * (2 * sizeof(u32) + sizeof(u64));
+  return 16 * 32 * (size_t)spl + 2 * kWarpLevels * sizeof(u32) + 2 * kWarpMarginal * (sizeof(u32) + sizeof(u64));
 }
+
+__device__ __forceinline__ int popc_mask(u32 m) { return __popc(m); }
+__device__ __forceinline__ int popc_mask(u64 m) { return __popcll(m); }
+__device__ __forceinline__ int ffs_mask(u32 m) { return __ffs(m); }
+__device__ __forceinline__ int ffs_mask(u64 m) { return __ffsll((long long)m); }
 
 // Inclusive warp scan of a u32.
 __device__ __forceinline__ u32 warp_incl_scan(u32 v, int lane) {
@@ -255,10 +261,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   int32_t* s_act = reinterpret_cast<int32_t*>(base);  // then side, price, qty at +n, +2n, +3n
   u32* lvb = reinterpret_cast<u32*>(s_act + 4 * n);   // bid level words, then D | orders << 21
   u32* lva = lvb + kWarpLevels;                       // ask level words, then S | orders << 21
-  u32* m_slot = lva + kWarpLevels;                    // [2][kWarpMarginal]
-  u32* m_qty = m_slot + 2 * kWarpMarginal;            // [2][kWarpMarginal]
+  u32* m_qty = lva + kWarpLevels;                     // [2][kWarpMarginal]
   u64* m_key = reinterpret_cast<u64*>(m_qty + 2 * kWarpMarginal);  // [2][kWarpMarginal]
-  const u32 lt_mask = (1u << lane) - 1u;
   const int gw = blockIdx.x * kWarpsPerBlock + wib, nw = gridDim.x * kWarpsPerBlock;
   for (int i = cap + lane; i < n; i += 32) s_act[i] = 0;  // padding slots: never copied, never live
   if (gw < n_books) warp_stage<kVec16>(s_act, n, gw, cap, lane, active, side, price, qty);
@@ -392,8 +396,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
       }
       continue;
     }
-    // whole fills (and zero-qty orders) written here; marginal orders listed
-    int nm0 = 0, nm1 = 0;
+    // whole fills (and zero-qty orders) written here; marginal orders marked
+    // in per-lane bit masks (bit k = this lane's slot k), listed below
+    using Mask = typename std::conditional<(SPL > 32), u64, u32>::type;
+    Mask mmb = 0, mma = 0;
 #pragma unroll
     for (int k = 0; k < SPL; ++k) {
       const int i = 4 * ((k >> 2) * 32 + lane) + (k & 3);
@@ -405,26 +411,33 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
         qty[o + i] = 0;
         active[o + i] = 0;
       }
-      if (__any_sync(0xFFFFFFFFu, marg)) {
-        const u32 bal_b = __ballot_sync(0xFFFFFFFFu, marg && !ask), bal_a = __ballot_sync(0xFFFFFFFFu, marg && ask);
-        if (marg) {
-          const int s = ask ? 1 : 0;
-          const int pos = (ask ? nm1 + __popc(bal_a & lt_mask) : nm0 + __popc(bal_b & lt_mask));
-          m_slot[s * kWarpMarginal + pos] = (u32)i;
-          m_qty[s * kWarpMarginal + pos] = q;
+      mmb |= (Mask)(marg && !ask) << k;
+      mma |= (Mask)(marg && ask) << k;
+    }
+    int nm0 = 0, nm1 = 0;
+    if (V > 0) {
+      // list positions: warp scan of the per-lane counts; qty and time of the
+      // marginal orders from global memory (neither written by this kernel)
+      const int cb = popc_mask(mmb), ca = popc_mask(mma);
+      const int ib = (int)warp_incl_scan((u32)cb, lane), ia = (int)warp_incl_scan((u32)ca, lane);
+      nm0 = __shfl_sync(0xFFFFFFFFu, ib, 31);
+      nm1 = __shfl_sync(0xFFFFFFFFu, ia, 31);
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        Mask m = s ? mma : mmb;
+        int pos = s ? ia - ca : ib - cb;
+        while (m) {
+          const int k = ffs_mask(m) - 1;
+          m &= m - 1;
+          const u32 i = 4u * (u32)((k >> 2) * 32 + lane) + (u32)(k & 3);
+          m_qty[s * kWarpMarginal + pos] = (u32)qty[o + i];
+          m_key[s * kWarpMarginal + pos] = ((u64)ord32(time[o + i]) << 32) | i;
+          ++pos;
         }
-        nm0 += __popc(bal_b);
-        nm1 += __popc(bal_a);
       }
     }
     __syncwarp();
     if (V > 0) {
-      for (int e = lane; e < nm0 + nm1; e += 32) {
-        const int s = e >= nm0, f = e - (s ? nm0 : 0);
-        const u32 slot = m_slot[s * kWarpMarginal + f];
-        m_key[s * kWarpMarginal + f] = ((u64)ord32(time[o + slot]) << 32) | slot;
-      }
-      __syncwarp();
       for (int e = lane; e < nm0 + nm1; e += 32) {
         const int s = e >= nm0, f = e - (s ? nm0 : 0), m = s ? nm1 : nm0;
         const u32* mq = m_qty + s * kWarpMarginal;
