@@ -18,15 +18,14 @@
 // holding it <= p, while at p = the price of the ask holding share V both sums
 // reach V. Only prices in [lowest ask, highest bid] matter.
 //
-// Level path (k_lob_match_warp): one warp per book, three coalesced passes
-// over its active, side, price and qty words (the first from DRAM, the others
-// mostly from L1 / L2): lowest ask and highest bid, then per-price histograms
-// of that range (shares | orders << 21, one shared atomic per order), then
-// fills. The histograms are scanned into D and S, which give V, the bid level
-// pb holding share V (largest p with D(p) >= V) and the ask level pa holding
-// it (smallest p with S(p) >= V). Bids above pb and asks below pa fill whole,
-// those beyond fill nothing, and only the orders on the two marginal levels
-// are ranked by (time, slot), by counting.
+// Level path (k_lob_match_warp): one warp per book. The warp stages the book's
+// active, side, price and qty words into shared memory with cp.async, moves
+// each lane's slots into registers (and starts staging its next book), builds per-price histograms of the range
+// (shares | orders << 21, one shared atomic per order), scans them into D and
+// S, and takes V, the bid level pb holding share V (largest p with D(p) >= V)
+// and the ask level pa holding it (smallest p with S(p) >= V). Bids above pb
+// and asks below pa fill whole, those beyond fill nothing, and only the orders
+// on the two marginal levels are ranked by (time, slot), by counting.
 //
 // Sort path (k_lob_deferred): a book whose range is wider than kWarpLevels
 // prices, whose marginal level holds more than kWarpMarginal orders, or whose
@@ -34,6 +33,7 @@
 // to -1) and matched by a second kernel, one CTA per book: bitonic sort of the
 // whole book in shared memory, cumulative sums, a binary search per bid.
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -41,11 +41,23 @@ namespace abm {
 
 constexpr int kLobThreads = 256;        // sort path: threads per book
 constexpr int kLobWarps = kLobThreads / 32;
-constexpr int kWarpsPerBlock = 4;       // level path: books in flight per CTA
+constexpr int kWarpsPerBlock = 2;       // level path: books in flight per CTA
 constexpr int kWarpLevels = 256;        // level path: prices in [lowest ask, highest bid], at most
 constexpr int kWarpMarginal = 64;       // level path: orders on one marginal level, at most
 constexpr u32 kShareBits = 21;          // level words: shares in the low 21 bits, orders above
 constexpr u32 kShareMask = (1u << kShareBits) - 1u;
+constexpr u32 kLive = 1u << 31, kAsk = 1u << 30;  // packed slot word: live | ask | qty
+
+__device__ __forceinline__ u32 smem_u32(const void* p) { return (u32)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // order-preserving map of int32 onto u32
 __device__ __forceinline__ u32 ord32(int32_t p) { return (u32)p ^ 0x80000000u; }
@@ -187,11 +199,17 @@ __device__ void lob_match_sorted(const LobBook& d, int n, int b, int cap, int nb
   }
 }
 
-// Shared memory of one warp of the level path: the level words of both sides
-// and the marginal lists (qty, key = time | slot) of both sides.
-constexpr size_t kWarpSmemBytes = 2 * kWarpLevels * sizeof(u32) + 2 * kWarpMarginal * (sizeof(u32) + sizeof(u64));
+// Shared memory of one warp of the level path: the staged book (4 arrays of
+// 32 * SPL words; slots >= cap hold active = 0), the level words of both
+// sides, and the marginal lists (qty, key = time | slot) of both sides.
+__host__ __device__ constexpr size_t warp_smem_bytes(int spl) {
+  return 16 * 32 * (size_t)spl + 2 * kWarpLevels * sizeof(u32) + 2 * kWarpMarginal * (sizeof(u32) + sizeof(u64));
+}
 
-__device__ __forceinline__ int ffs64(u64 m) { return __ffsll((long long)m); }
+__device__ __forceinline__ int popc_mask(u32 m) { return __popc(m); }
+__device__ __forceinline__ int popc_mask(u64 m) { return __popcll(m); }
+__device__ __forceinline__ int ffs_mask(u32 m) { return __ffs(m); }
+__device__ __forceinline__ int ffs_mask(u64 m) { return __ffsll((long long)m); }
 
 // Inclusive warp scan of a u32.
 __device__ __forceinline__ u32 warp_incl_scan(u32 v, int lane) {
@@ -203,49 +221,89 @@ __device__ __forceinline__ u32 warp_incl_scan(u32 v, int lane) {
   return v;
 }
 
-// Level path, one warp per book, lane holding slots k * 32 + lane. Three
-// passes over the book's words: the first from DRAM, the other two mostly
-// from L1 / L2; no staging, few registers, many warps per SM. Deferred books
-// get out_volume = -1 and are left untouched.
+// Book b's words into the warp's staging arrays (asynchronous; committed).
+template <bool kVec16>
+__device__ __forceinline__ void warp_stage(int32_t* s_act, int n, int b, int cap, int lane, const int32_t* active,
+                                           const int32_t* side, const int32_t* price, const int32_t* qty) {
+  const size_t o = (size_t)b * cap;
+  if (kVec16) {
+    for (int c = lane; c < (cap >> 2); c += 32) {
+      cp_async16(s_act + 4 * c, active + o + 4 * c);
+      cp_async16(s_act + n + 4 * c, side + o + 4 * c);
+      cp_async16(s_act + 2 * n + 4 * c, price + o + 4 * c);
+      cp_async16(s_act + 3 * n + 4 * c, qty + o + 4 * c);
+    }
+  } else {
+    for (int c = lane; c < cap; c += 32) {
+      cp_async4(s_act + c, active + o + c);
+      cp_async4(s_act + n + c, side + o + c);
+      cp_async4(s_act + 2 * n + c, price + o + c);
+      cp_async4(s_act + 3 * n + c, qty + o + c);
+    }
+  }
+  cp_async_commit();
+}
+
+// Level path, one warp per book; SPL = slots per lane (cap <= 32 * SPL), a
+// lane holding slots 4 * (g * 32 + lane) + c. The next book is staged as soon
+// as this one's words are in registers. Deferred books get out_volume = -1
+// and are left untouched.
+template <int SPL, bool kVec16>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     k_lob_match_warp(int n_books, int cap, int32_t* active, const int32_t* __restrict__ side,
                      const int32_t* __restrict__ price, int32_t* qty, const int32_t* __restrict__ time,
                      long long* out_volume, int32_t* out_price) {
   constexpr int LPL = kWarpLevels / 32;  // levels per lane in the scan
+  constexpr int n = 32 * SPL;            // staged words per array
   extern __shared__ __align__(16) unsigned char lob_smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  u32* lvb = reinterpret_cast<u32*>(lob_smem + wib * kWarpSmemBytes);  // bid level words, then D | orders << 21
-  u32* lva = lvb + kWarpLevels;                                         // ask level words, then S | orders << 21
-  u32* m_qty = lva + kWarpLevels;                                       // [2][kWarpMarginal]
-  u64* m_key = reinterpret_cast<u64*>(m_qty + 2 * kWarpMarginal);       // [2][kWarpMarginal]
+  unsigned char* base = lob_smem + wib * warp_smem_bytes(SPL);
+  int32_t* s_act = reinterpret_cast<int32_t*>(base);  // then side, price, qty at +n, +2n, +3n
+  u32* lvb = reinterpret_cast<u32*>(s_act + 4 * n);   // bid level words, then D | orders << 21
+  u32* lva = lvb + kWarpLevels;                       // ask level words, then S | orders << 21
+  u32* m_qty = lva + kWarpLevels;                     // [2][kWarpMarginal]
+  u64* m_key = reinterpret_cast<u64*>(m_qty + 2 * kWarpMarginal);  // [2][kWarpMarginal]
   const int gw = blockIdx.x * kWarpsPerBlock + wib, nw = gridDim.x * kWarpsPerBlock;
-  const int kmax = (cap + 31) >> 5;  // slots per lane
+  for (int i = cap + lane; i < n; i += 32) s_act[i] = 0;  // padding slots: never copied, never live
+  if (gw < n_books) warp_stage<kVec16>(s_act, n, gw, cap, lane, active, side, price, qty);
   for (int b = gw; b < n_books; b += nw) {
     const size_t o = (size_t)b * cap;
-    const int32_t* a_b = active + o;
-    const int32_t* s_b = side + o;
-    const int32_t* p_b = price + o;
-    const int32_t* q_b = qty + o;
+    cp_async_wait_0();
+    __syncwarp();
 
-    // pass 1: sides' counts, lowest ask, highest bid, share sums, flags
+    // this lane's slots into registers: price and live | ask | qty
+    int32_t px[SPL];
+    u32 w[SPL];
     u32 cnt = 0, mn = 0xFFFFFFFFu, mx = 0u, sb = 0, sa = 0, bad = 0, zq = 0;
-#pragma unroll 4
-    for (int k = 0; k < kmax; ++k) {
-      const int i = k * 32 + lane;
-      if (i < cap) {
-        const bool live = a_b[i] != 0, ask = __ldg(s_b + i) != 0;
-        const int32_t p = __ldg(p_b + i);
-        const u32 q = (u32)q_b[i], qm = q & kShareMask;
+#pragma unroll
+    for (int g = 0; g < SPL / 4; ++g) {
+      const int v = g * 32 + lane;
+      const int4 a4 = reinterpret_cast<const int4*>(s_act)[v];
+      const int4 s4 = reinterpret_cast<const int4*>(s_act + n)[v];
+      const int4 p4 = reinterpret_cast<const int4*>(s_act + 2 * n)[v];
+      const int4 q4 = reinterpret_cast<const int4*>(s_act + 3 * n)[v];
+      const int av[4] = {a4.x, a4.y, a4.z, a4.w}, sv[4] = {s4.x, s4.y, s4.z, s4.w};
+      const int pv[4] = {p4.x, p4.y, p4.z, p4.w}, qv[4] = {q4.x, q4.y, q4.z, q4.w};
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int k = 4 * g + c;
+        const bool live = av[c] != 0, ask = sv[c] != 0;
         const bool lbid = live && !ask, lask = live && ask;
+        const u32 q = (u32)qv[c], qm = q & kShareMask;
         bad |= (u32)(live && q > kShareMask);  // too large (or negative) for the level words
         zq |= (u32)(live && q == 0);
+        px[k] = pv[c];
+        w[k] = live ? (kLive | (ask ? kAsk : 0u) | qm) : 0u;
         cnt += lask ? 0x10000u : (lbid ? 1u : 0u);
         sa += lask ? qm : 0u;
         sb += lbid ? qm : 0u;
-        mn = min(mn, lask ? ord32(p) : 0xFFFFFFFFu);
-        mx = max(mx, lbid ? ord32(p) : 0u);
+        mn = min(mn, lask ? ord32(pv[c]) : 0xFFFFFFFFu);
+        mx = max(mx, lbid ? ord32(pv[c]) : 0u);
       }
     }
+    __syncwarp();  // the staging arrays are free: stage the next book
+    if (b + nw < n_books) warp_stage<kVec16>(s_act, n, b + nw, cap, lane, active, side, price, qty);
+
     // share sums saturate per lane, so the warp sums cannot wrap
     cnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
     const u32 SB = __reduce_add_sync(0xFFFFFFFFu, min(sb, 1u << kShareBits));
@@ -265,22 +323,16 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     int32_t pb = 0, pa = 0;
     u32 Dn = 0, Sp = 0;
     if (cross) {
-      __syncwarp();  // the previous book's readers of the level words are done
       for (int l = lane; l < L; l += 32) {
         lvb[l] = 0u;
         lva[l] = 0u;
       }
       __syncwarp();
-      // pass 2: per-price histograms of [pmin, pmax]
-#pragma unroll 4
-      for (int k = 0; k < kmax; ++k) {
-        const int i = k * 32 + lane;
-        if (i < cap && a_b[i] != 0) {
-          const bool ask = __ldg(s_b + i) != 0;
-          const int32_t p = __ldg(p_b + i);
-          if (ask ? p <= pmax : p >= pmin)
-            atomicAdd((ask ? lva : lvb) + (p - pmin), ((u32)q_b[i] & kShareMask) | (1u << kShareBits));
-        }
+#pragma unroll
+      for (int k = 0; k < SPL; ++k) {
+        const bool ask = w[k] & kAsk;
+        const bool in = (w[k] & kLive) && (ask ? px[k] <= pmax : px[k] >= pmin);
+        if (in) atomicAdd((ask ? lva : lvb) + (px[k] - pmin), (w[k] & kShareMask) | (1u << kShareBits));
       }
       __syncwarp();
       // D(l) = bid shares at levels >= l, S(l) = ask shares at levels <= l;
@@ -344,46 +396,48 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
       }
       continue;
     }
-    // pass 3: whole fills (and zero-qty orders) written; marginal orders
-    // marked in per-lane bit masks (bit k = slot k * 32 + lane)
-    u64 mmb = 0, mma = 0;
-#pragma unroll 4
-    for (int k = 0; k < kmax; ++k) {
-      const int i = k * 32 + lane;
-      if (i < cap && a_b[i] != 0) {
-        const bool ask = __ldg(s_b + i) != 0;
-        const int32_t p = __ldg(p_b + i);
-        const u32 q = (u32)q_b[i];
-        const bool whole = q == 0 || (V > 0 && (ask ? p < pa : p > pb));
-        const bool marg = q > 0 && V > 0 && p == (ask ? pa : pb);
-        if (whole) {
-          qty[o + i] = 0;
-          active[o + i] = 0;
-        }
-        mmb |= (u64)(marg && !ask) << k;
-        mma |= (u64)(marg && ask) << k;
+    // whole fills (and zero-qty orders) written here; marginal orders marked
+    // in per-lane bit masks (bit k = this lane's slot k), listed below
+    using Mask = typename std::conditional<(SPL > 32), u64, u32>::type;
+    Mask mmb = 0, mma = 0;
+#pragma unroll
+    for (int k = 0; k < SPL; ++k) {
+      const int i = 4 * ((k >> 2) * 32 + lane) + (k & 3);
+      const bool live = w[k] & kLive, ask = w[k] & kAsk;
+      const u32 q = w[k] & kShareMask;
+      const bool whole = live && (q == 0 || (V > 0 && (ask ? px[k] < pa : px[k] > pb)));
+      const bool marg = live && q > 0 && V > 0 && px[k] == (ask ? pa : pb);
+      if (whole) {
+        qty[o + i] = 0;
+        active[o + i] = 0;
       }
+      mmb |= (Mask)(marg && !ask) << k;
+      mma |= (Mask)(marg && ask) << k;
     }
+    int nm0 = 0, nm1 = 0;
     if (V > 0) {
       // list positions: warp scan of the per-lane counts; qty and time of the
-      // marginal orders (neither written by this kernel)
-      const int cb = __popcll(mmb), ca = __popcll(mma);
+      // marginal orders from global memory (neither written by this kernel)
+      const int cb = popc_mask(mmb), ca = popc_mask(mma);
       const int ib = (int)warp_incl_scan((u32)cb, lane), ia = (int)warp_incl_scan((u32)ca, lane);
-      const int nm0 = __shfl_sync(0xFFFFFFFFu, ib, 31), nm1 = __shfl_sync(0xFFFFFFFFu, ia, 31);
+      nm0 = __shfl_sync(0xFFFFFFFFu, ib, 31);
+      nm1 = __shfl_sync(0xFFFFFFFFu, ia, 31);
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
-        u64 m = s ? mma : mmb;
+        Mask m = s ? mma : mmb;
         int pos = s ? ia - ca : ib - cb;
         while (m) {
-          const int k = ffs64(m) - 1;
+          const int k = ffs_mask(m) - 1;
           m &= m - 1;
-          const u32 i = (u32)(k * 32 + lane);
-          m_qty[s * kWarpMarginal + pos] = (u32)q_b[i];
+          const u32 i = 4u * (u32)((k >> 2) * 32 + lane) + (u32)(k & 3);
+          m_qty[s * kWarpMarginal + pos] = (u32)qty[o + i];
           m_key[s * kWarpMarginal + pos] = ((u64)ord32(time[o + i]) << 32) | i;
           ++pos;
         }
       }
-      __syncwarp();
+    }
+    __syncwarp();
+    if (V > 0) {
       for (int e = lane; e < nm0 + nm1; e += 32) {
         const int s = e >= nm0, f = e - (s ? nm0 : 0), m = s ? nm1 : nm0;
         const u32* mq = m_qty + s * kWarpMarginal;
@@ -399,13 +453,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
           if (fill == q) active[o + slot] = 0;
         }
       }
-      __syncwarp();  // the lists are reused by the next book
     }
     if (lane == 0) {
       out_volume[b] = (long long)V;
       out_price[b] = V > 0 ? pa : -1;
     }
   }
+  cp_async_wait_0();
 }
 
 // Sort path for the books the level path deferred (out_volume < 0), one CTA
@@ -493,18 +547,23 @@ static int lob_pad(int cap) {
   return n;
 }
 
+template <int SPL, bool kVec16>
 static abm_status lob_launch_warp(int n_books, int cap, int32_t* active, const int32_t* side, const int32_t* price,
                                   int32_t* qty, const int32_t* time, long long* vol, int32_t* px, cudaStream_t st) {
   static int blocks_per_sm = 0;
-  const size_t smem = kWarpsPerBlock * kWarpSmemBytes;
+  const size_t smem = kWarpsPerBlock * warp_smem_bytes(SPL);
   if (!blocks_per_sm) {
+    ABM_CUDA_TRY(cudaFuncSetAttribute(k_lob_match_warp<SPL, kVec16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
     int occ = 0;
-    ABM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lob_match_warp, kWarpsPerBlock * 32, smem));
+    ABM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lob_match_warp<SPL, kVec16>,
+                                                               kWarpsPerBlock * 32, smem));
     blocks_per_sm = std::max(occ, 1);
   }
   const long long want = ((long long)n_books + kWarpsPerBlock - 1) / kWarpsPerBlock;
   const int grid = (int)std::min<long long>(want, (long long)num_sms() * blocks_per_sm);
-  k_lob_match_warp<<<grid, kWarpsPerBlock * 32, smem, st>>>(n_books, cap, active, side, price, qty, time, vol, px);
+  k_lob_match_warp<SPL, kVec16><<<grid, kWarpsPerBlock * 32, smem, st>>>(n_books, cap, active, side, price, qty,
+                                                                          time, vol, px);
   ABM_LAUNCH_CHECK();
   return ABM_OK;
 }
@@ -526,9 +585,12 @@ static abm_status lob_launch_deferred(int n_books, int cap, int32_t* active, con
   return ABM_OK;
 }
 
-static abm_status lob_launch(int n_books, int cap, int32_t* active, const int32_t* side, const int32_t* price,
-                             int32_t* qty, const int32_t* time, long long* vol, int32_t* px, cudaStream_t st) {
-  const abm_status e = lob_launch_warp(n_books, cap, active, side, price, qty, time, vol, px, st);
+template <int SPL>
+static abm_status lob_launch(bool vec16, int n_books, int cap, int32_t* active, const int32_t* side,
+                             const int32_t* price, int32_t* qty, const int32_t* time, long long* vol, int32_t* px,
+                             cudaStream_t st) {
+  abm_status e = vec16 ? lob_launch_warp<SPL, true>(n_books, cap, active, side, price, qty, time, vol, px, st)
+                       : lob_launch_warp<SPL, false>(n_books, cap, active, side, price, qty, time, vol, px, st);
   if (e != ABM_OK) return e;
   switch (lob_pad(cap) / kLobThreads) {
     case 1: return lob_launch_deferred<1>(n_books, cap, active, side, price, qty, time, vol, px, st);
@@ -548,8 +610,15 @@ extern "C" abm_status abm_lob_match(int32_t n_books, int32_t cap, int32_t* activ
   if (n_books < 0 || cap < 1 || cap > ABM_LOB_MAX_CAP) return ABM_ERR_ARG;
   if (n_books == 0) return ABM_OK;
   if (!active || !side || !price || !qty || !time || !out_volume || !out_price) return ABM_ERR_ARG;
-  return lob_launch(n_books, cap, active, side, price, qty, time, reinterpret_cast<long long*>(out_volume), out_price,
-                    (cudaStream_t)stream);
+  // 16-byte copies need every book's rows 16-byte aligned
+  const bool vec16 =
+      cap % 4 == 0 && ((uintptr_t)active | (uintptr_t)side | (uintptr_t)price | (uintptr_t)qty) % 16 == 0;
+  long long* vol = reinterpret_cast<long long*>(out_volume);
+  const cudaStream_t st = (cudaStream_t)stream;
+  if (cap <= 256) return lob_launch<8>(vec16, n_books, cap, active, side, price, qty, time, vol, out_price, st);
+  if (cap <= 512) return lob_launch<16>(vec16, n_books, cap, active, side, price, qty, time, vol, out_price, st);
+  if (cap <= 1024) return lob_launch<32>(vec16, n_books, cap, active, side, price, qty, time, vol, out_price, st);
+  return lob_launch<64>(vec16, n_books, cap, active, side, price, qty, time, vol, out_price, st);
 }
 
 extern "C" abm_status abm_lob_add(int32_t n_books, int32_t cap, int32_t* active, int32_t* side, int32_t* price,
