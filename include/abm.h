@@ -166,6 +166,10 @@ abm_status abm_sort(abm_slab* s, int32_t field, int32_t* out_perm, void* stream)
  * orders placed.
  */
 #define ABM_LOB_MAX_CAP 2048
+/* Launch shape of abm_lob_match's price-level path for the rest of the
+ * process: warps matching one book (1, 2 or 4; 0 = the default, 2). Results
+ * never depend on it. ABM_ERR_ARG for other values. Host only. */
+abm_status abm_lob_tune(int32_t warps_per_book);
 abm_status abm_lob_match(int32_t n_books, int32_t cap, int32_t* active, const int32_t* side, const int32_t* price,
                          int32_t* qty, const int32_t* time, int64_t* out_volume, int32_t* out_price, void* stream);
 abm_status abm_lob_add(int32_t n_books, int32_t cap, int32_t* active, int32_t* side, int32_t* price, int32_t* qty,

@@ -158,6 +158,7 @@ def _sig(L):
         "abm_capacity_from_prediction": ([vp, i32, C.c_float, i32, vp, vp, vp, vp], st),
         "abm_lob_match": ([i32, i32, vp, vp, vp, vp, vp, vp, vp, vp], st),
         "abm_lob_add": ([i32, i32, vp, vp, vp, vp, vp, vp, vp, i32, vp, vp], st),
+        "abm_lob_tune": ([i32], st),
     }
     global EXPORTED
     for name, (args, res) in sigs.items():

@@ -18,20 +18,22 @@
 // holding it <= p, while at p = the price of the ask holding share V both sums
 // reach V. Only prices in [lowest ask, highest bid] matter.
 //
-// Level path (k_lob_match_warp): one warp per book. The warp stages the book's
-// active, side, price and qty words into shared memory with cp.async, moves
-// each lane's slots into registers (and starts staging its next book), builds per-price histograms of the range
-// (shares | orders << 21, one shared atomic per order), scans them into D and
-// S, and takes V, the bid level pb holding share V (largest p with D(p) >= V)
-// and the ask level pa holding it (smallest p with S(p) >= V). Bids above pb
-// and asks below pa fill whole, those beyond fill nothing, and only the orders
-// on the two marginal levels are ranked by (time, slot), by counting.
+// Level path (k_lob_match_levels): a CTA of G warps matches one book at a
+// time. It stages the book's active, side, price and qty words into shared
+// memory with cp.async, moves each thread's slots into registers (and starts
+// staging its next book), builds per-price histograms of the range (shares |
+// orders << 21, one shared atomic per order), scans them into D and S, and
+// takes V, the bid level pb holding share V (largest p with D(p) >= V) and the
+// ask level pa holding it (smallest p with S(p) >= V). Bids above pb and asks
+// below pa fill whole, those beyond fill nothing, and only the orders on the
+// two marginal levels are ranked by (time, slot), by counting.
 //
 // Sort path (k_lob_deferred): a book whose range is wider than kWarpLevels
 // prices, whose marginal level holds more than kWarpMarginal orders, or whose
-// bid or ask shares reach 2^21 is left untouched by the warp (its volume set
-// to -1) and matched by a second kernel, one CTA per book: bitonic sort of the
-// whole book in shared memory, cumulative sums, a binary search per bid.
+// bid or ask shares reach 2^21 is left untouched by the level path (its
+// volume set to -1) and matched by a second kernel, one CTA per book: bitonic
+// sort of the whole book in shared memory, cumulative sums, a binary search
+// per bid.
 #include <algorithm>
 #include <type_traits>
 
@@ -41,7 +43,6 @@ namespace abm {
 
 constexpr int kLobThreads = 256;        // sort path: threads per book
 constexpr int kLobWarps = kLobThreads / 32;
-constexpr int kWarpsPerBlock = 2;       // level path: books in flight per CTA
 constexpr int kWarpLevels = 256;        // level path: prices in [lowest ask, highest bid], at most
 constexpr int kWarpMarginal = 64;       // level path: orders on one marginal level, at most
 constexpr u32 kShareBits = 21;          // level words: shares in the low 21 bits, orders above
@@ -199,11 +200,11 @@ __device__ void lob_match_sorted(const LobBook& d, int n, int b, int cap, int nb
   }
 }
 
-// Shared memory of one warp of the level path: the staged book (4 arrays of
-// 32 * SPL words; slots >= cap hold active = 0), the level words of both
-// sides, and the marginal lists (qty, key = time | slot) of both sides.
-__host__ __device__ constexpr size_t warp_smem_bytes(int spl) {
-  return 16 * 32 * (size_t)spl + 2 * kWarpLevels * sizeof(u32) + 2 * kWarpMarginal * (sizeof(u32) + sizeof(u64));
+// Shared memory of one CTA of the level path (one book at a time): the staged
+// book (4 arrays of n words; slots >= cap hold active = 0), the level words of
+// both sides, and the marginal lists (qty, key = time | slot) of both sides.
+__host__ __device__ constexpr size_t grp_smem_bytes(int n) {
+  return 16 * (size_t)n + 2 * kWarpLevels * sizeof(u32) + 2 * kWarpMarginal * (sizeof(u32) + sizeof(u64));
 }
 
 __device__ __forceinline__ int popc_mask(u32 m) { return __popc(m); }
@@ -221,20 +222,101 @@ __device__ __forceinline__ u32 warp_incl_scan(u32 v, int lane) {
   return v;
 }
 
-// Book b's words into the warp's staging arrays (asynchronous; committed).
-template <bool kVec16>
-__device__ __forceinline__ void warp_stage(int32_t* s_act, int n, int b, int cap, int lane, const int32_t* active,
-                                           const int32_t* side, const int32_t* price, const int32_t* qty) {
+// Barrier of the G warps matching one book.
+template <int G>
+__device__ __forceinline__ void grp_sync() {
+  if (G == 1) __syncwarp();
+  else __syncthreads();
+}
+
+// Three sums, a min, a max and an or over the G warps (every thread gets
+// them). One barrier; the exchange buffer alternates between calls.
+struct Agg6 {
+  u32 s0, s1, s2, mn, mx, orr;
+};
+template <int G>
+__device__ __forceinline__ Agg6 grp_agg6(Agg6 a, u32 (*x)[G][8], int& par) {
+  a.s0 = __reduce_add_sync(0xFFFFFFFFu, a.s0);
+  a.s1 = __reduce_add_sync(0xFFFFFFFFu, a.s1);
+  a.s2 = __reduce_add_sync(0xFFFFFFFFu, a.s2);
+  a.mn = __reduce_min_sync(0xFFFFFFFFu, a.mn);
+  a.mx = __reduce_max_sync(0xFFFFFFFFu, a.mx);
+  a.orr = __reduce_or_sync(0xFFFFFFFFu, a.orr);
+  if (G == 1) return a;
+  if ((threadIdx.x & 31) == 0) {
+    u32* d = x[par][threadIdx.x >> 5];
+    d[0] = a.s0;
+    d[1] = a.s1;
+    d[2] = a.s2;
+    d[3] = a.mn;
+    d[4] = a.mx;
+    d[5] = a.orr;
+  }
+  __syncthreads();
+  Agg6 r{0u, 0u, 0u, 0xFFFFFFFFu, 0u, 0u};
+#pragma unroll
+  for (int w = 0; w < G; ++w) {
+    const u32* d = x[par][w];
+    r.s0 += d[0];
+    r.s1 += d[1];
+    r.s2 += d[2];
+    r.mn = min(r.mn, d[3]);
+    r.mx = max(r.mx, d[4]);
+    r.orr |= d[5];
+  }
+  par ^= 1;
+  return r;
+}
+
+// Exclusive scan of two u32 over the G warps' threads, with the totals.
+template <int G>
+__device__ __forceinline__ void grp_scan2(u32 a, u32 b, u32& ex_a, u32& ex_b, u32& tot_a, u32& tot_b,
+                                          u32 (*x)[G][8], int& par) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const u32 ia = warp_incl_scan(a, lane), ib = warp_incl_scan(b, lane);
+  if (G == 1) {
+    ex_a = ia - a;
+    ex_b = ib - b;
+    tot_a = __shfl_sync(0xFFFFFFFFu, ia, 31);
+    tot_b = __shfl_sync(0xFFFFFFFFu, ib, 31);
+    return;
+  }
+  if (lane == 31) {
+    x[par][warp][0] = ia;
+    x[par][warp][1] = ib;
+  }
+  __syncthreads();
+  u32 pa = 0, pb = 0, ta = 0, tb = 0;
+#pragma unroll
+  for (int w = 0; w < G; ++w) {
+    const u32 wa = x[par][w][0], wb = x[par][w][1];
+    pa += w < warp ? wa : 0u;
+    pb += w < warp ? wb : 0u;
+    ta += wa;
+    tb += wb;
+  }
+  ex_a = pa + ia - a;
+  ex_b = pb + ib - b;
+  tot_a = ta;
+  tot_b = tb;
+  par ^= 1;
+}
+
+// Book b's words into the staging arrays (asynchronous; committed). T
+// threads copy.
+template <int T, bool kVec16>
+__device__ __forceinline__ void grp_stage(int32_t* s_act, int n, int b, int cap, const int32_t* active,
+                                          const int32_t* side, const int32_t* price, const int32_t* qty) {
   const size_t o = (size_t)b * cap;
   if (kVec16) {
-    for (int c = lane; c < (cap >> 2); c += 32) {
+    for (int c = threadIdx.x; c < (cap >> 2); c += T) {
       cp_async16(s_act + 4 * c, active + o + 4 * c);
       cp_async16(s_act + n + 4 * c, side + o + 4 * c);
       cp_async16(s_act + 2 * n + 4 * c, price + o + 4 * c);
       cp_async16(s_act + 3 * n + 4 * c, qty + o + 4 * c);
     }
   } else {
-    for (int c = lane; c < cap; c += 32) {
+    for (int c = threadIdx.x; c < cap; c += T) {
       cp_async4(s_act + c, active + o + c);
       cp_async4(s_act + n + c, side + o + c);
       cp_async4(s_act + 2 * n + c, price + o + c);
@@ -244,40 +326,42 @@ __device__ __forceinline__ void warp_stage(int32_t* s_act, int n, int b, int cap
   cp_async_commit();
 }
 
-// Level path, one warp per book; SPL = slots per lane (cap <= 32 * SPL), a
-// lane holding slots 4 * (g * 32 + lane) + c. The next book is staged as soon
-// as this one's words are in registers. Deferred books get out_volume = -1
-// and are left untouched.
-template <int SPL, bool kVec16>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
-    k_lob_match_warp(int n_books, int cap, int32_t* active, const int32_t* __restrict__ side,
-                     const int32_t* __restrict__ price, int32_t* qty, const int32_t* __restrict__ time,
-                     long long* out_volume, int32_t* out_price) {
-  constexpr int LPL = kWarpLevels / 32;  // levels per lane in the scan
-  constexpr int n = 32 * SPL;            // staged words per array
+// Level path: a CTA of G warps (T = 32 G threads) matches one book at a time;
+// SPL = slots per thread (cap <= T * SPL), thread t holding slots
+// 4 * (g * T + t) + c. The book's words move from the staging arrays into
+// registers, and the next book is staged at once. Deferred books get
+// out_volume = -1 and are left untouched.
+template <int G, int SPL, bool kVec16>
+__global__ void __launch_bounds__(G * 32)
+    k_lob_match_levels(int n_books, int cap, int32_t* active, const int32_t* __restrict__ side,
+                       const int32_t* __restrict__ price, int32_t* qty, const int32_t* __restrict__ time,
+                       long long* out_volume, int32_t* out_price) {
+  constexpr int T = G * 32;
+  constexpr int LPT = kWarpLevels / T;  // levels per thread in the scan
+  constexpr int n = T * SPL;            // staged words per array
   extern __shared__ __align__(16) unsigned char lob_smem[];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  unsigned char* base = lob_smem + wib * warp_smem_bytes(SPL);
-  int32_t* s_act = reinterpret_cast<int32_t*>(base);  // then side, price, qty at +n, +2n, +3n
-  u32* lvb = reinterpret_cast<u32*>(s_act + 4 * n);   // bid level words, then D | orders << 21
-  u32* lva = lvb + kWarpLevels;                       // ask level words, then S | orders << 21
-  u32* m_qty = lva + kWarpLevels;                     // [2][kWarpMarginal]
+  __shared__ u32 s_x[2][G][8];
+  int32_t* s_act = reinterpret_cast<int32_t*>(lob_smem);  // then side, price, qty at +n, +2n, +3n
+  u32* lvb = reinterpret_cast<u32*>(s_act + 4 * n);        // bid level words, then D | orders << 21
+  u32* lva = lvb + kWarpLevels;                            // ask level words, then S | orders << 21
+  u32* m_qty = lva + kWarpLevels;                          // [2][kWarpMarginal]
   u64* m_key = reinterpret_cast<u64*>(m_qty + 2 * kWarpMarginal);  // [2][kWarpMarginal]
-  const int gw = blockIdx.x * kWarpsPerBlock + wib, nw = gridDim.x * kWarpsPerBlock;
-  for (int i = cap + lane; i < n; i += 32) s_act[i] = 0;  // padding slots: never copied, never live
-  if (gw < n_books) warp_stage<kVec16>(s_act, n, gw, cap, lane, active, side, price, qty);
-  for (int b = gw; b < n_books; b += nw) {
+  const int t = threadIdx.x;
+  int par = 0;
+  for (int i = cap + t; i < n; i += T) s_act[i] = 0;  // padding slots: never copied, never live
+  if ((int)blockIdx.x < n_books) grp_stage<T, kVec16>(s_act, n, blockIdx.x, cap, active, side, price, qty);
+  for (int b = blockIdx.x; b < n_books; b += gridDim.x) {
     const size_t o = (size_t)b * cap;
     cp_async_wait_0();
-    __syncwarp();
+    grp_sync<G>();
 
-    // this lane's slots into registers: price and live | ask | qty
+    // this thread's slots into registers: price and live | ask | qty
     int32_t px[SPL];
     u32 w[SPL];
-    u32 cnt = 0, mn = 0xFFFFFFFFu, mx = 0u, sb = 0, sa = 0, bad = 0, zq = 0;
+    u32 cnt = 0, mn = 0xFFFFFFFFu, mx = 0u, sb = 0, sa = 0, flags = 0;
 #pragma unroll
     for (int g = 0; g < SPL / 4; ++g) {
-      const int v = g * 32 + lane;
+      const int v = g * T + t;
       const int4 a4 = reinterpret_cast<const int4*>(s_act)[v];
       const int4 s4 = reinterpret_cast<const int4*>(s_act + n)[v];
       const int4 p4 = reinterpret_cast<const int4*>(s_act + 2 * n)[v];
@@ -290,8 +374,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
         const bool live = av[c] != 0, ask = sv[c] != 0;
         const bool lbid = live && !ask, lask = live && ask;
         const u32 q = (u32)qv[c], qm = q & kShareMask;
-        bad |= (u32)(live && q > kShareMask);  // too large (or negative) for the level words
-        zq |= (u32)(live && q == 0);
+        flags |= (live && q > kShareMask) ? 1u : 0u;  // too large (or negative) for the level words
+        flags |= (live && q == 0) ? 2u : 0u;
         px[k] = pv[c];
         w[k] = live ? (kLive | (ask ? kAsk : 0u) | qm) : 0u;
         cnt += lask ? 0x10000u : (lbid ? 1u : 0u);
@@ -301,86 +385,83 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
         mx = max(mx, lbid ? ord32(pv[c]) : 0u);
       }
     }
-    __syncwarp();  // the staging arrays are free: stage the next book
-    if (b + nw < n_books) warp_stage<kVec16>(s_act, n, b + nw, cap, lane, active, side, price, qty);
-
-    // share sums saturate per lane, so the warp sums cannot wrap
-    cnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
-    const u32 SB = __reduce_add_sync(0xFFFFFFFFu, min(sb, 1u << kShareBits));
-    const u32 SA = __reduce_add_sync(0xFFFFFFFFu, min(sa, 1u << kShareBits));
-    mn = __reduce_min_sync(0xFFFFFFFFu, mn);
-    mx = __reduce_max_sync(0xFFFFFFFFu, mx);
-    bad = __any_sync(0xFFFFFFFFu, bad);
-    zq = __any_sync(0xFFFFFFFFu, zq);
-    const bool cross = (cnt & 0xFFFFu) != 0 && (cnt >> 16) != 0 && mx >= mn;
-    const int32_t pmin = (int32_t)(mn ^ 0x80000000u), pmax = (int32_t)(mx ^ 0x80000000u);
+    // share sums saturate per thread, so the sums cannot wrap; for G > 1 the
+    // barrier inside also frees the staging arrays
+    const Agg6 r1 = grp_agg6<G>(Agg6{cnt, min(sb, 1u << kShareBits), min(sa, 1u << kShareBits), mn, mx, flags}, s_x,
+                                par);
+    if (G == 1) __syncwarp();
+    if (b + (int)gridDim.x < n_books)
+      grp_stage<T, kVec16>(s_act, n, b + gridDim.x, cap, active, side, price, qty);
+    const bool zq = r1.orr & 2u;
+    const bool cross = (r1.s0 & 0xFFFFu) != 0 && (r1.s0 >> 16) != 0 && r1.mx >= r1.mn;
+    const int32_t pmin = (int32_t)(r1.mn ^ 0x80000000u), pmax = (int32_t)(r1.mx ^ 0x80000000u);
     const long long L = cross ? (long long)pmax - (long long)pmin + 1 : 0;
-    if (cross && (bad || SB > kShareMask || SA > kShareMask || L > kWarpLevels)) {
-      if (lane == 0) out_volume[b] = -1;  // the sort path takes it
+    if (cross && ((r1.orr & 1u) || r1.s1 > kShareMask || r1.s2 > kShareMask || L > kWarpLevels)) {
+      if (t == 0) out_volume[b] = -1;  // the sort path takes it
       continue;
     }
     u32 V = 0;
     int32_t pb = 0, pa = 0;
     u32 Dn = 0, Sp = 0;
     if (cross) {
-      for (int l = lane; l < L; l += 32) {
+      for (int l = t; l < L; l += T) {
         lvb[l] = 0u;
         lva[l] = 0u;
       }
-      __syncwarp();
+      grp_sync<G>();
 #pragma unroll
       for (int k = 0; k < SPL; ++k) {
         const bool ask = w[k] & kAsk;
         const bool in = (w[k] & kLive) && (ask ? px[k] <= pmax : px[k] >= pmin);
         if (in) atomicAdd((ask ? lva : lvb) + (px[k] - pmin), (w[k] & kShareMask) | (1u << kShareBits));
       }
-      __syncwarp();
+      grp_sync<G>();
       // D(l) = bid shares at levels >= l, S(l) = ask shares at levels <= l;
-      // lane owns levels [LPL * lane, LPL * lane + LPL)
-      u32 hb[LPL], ha[LPL];
+      // thread t owns levels [LPT * t, LPT * t + LPT)
+      u32 hb[LPT], ha[LPT];
       u32 tb = 0, ta = 0;
-      const int l0 = lane * LPL;
+      const int l0 = t * LPT;
 #pragma unroll
-      for (int j = 0; j < LPL; ++j) {
+      for (int j = 0; j < LPT; ++j) {
         hb[j] = l0 + j < L ? lvb[l0 + j] : 0u;
         ha[j] = l0 + j < L ? lva[l0 + j] : 0u;
         tb += hb[j] & kShareMask;
         ta += ha[j] & kShareMask;
       }
-      const u32 ib = warp_incl_scan(tb, lane), ia = warp_incl_scan(ta, lane);
-      const u32 BT = __shfl_sync(0xFFFFFFFFu, ib, 31);
-      u32 pre_b = ib - tb, pre_a = ia - ta, best = 0;
-      u32 Dl[LPL], Sl[LPL];
+      u32 pre_b, pre_a, BT, AT;
+      grp_scan2<G>(tb, ta, pre_b, pre_a, BT, AT, s_x, par);
+      u32 best = 0;
+      u32 Dl[LPT], Sl[LPT];
 #pragma unroll
-      for (int j = 0; j < LPL; ++j) {
+      for (int j = 0; j < LPT; ++j) {
         Dl[j] = BT - pre_b;
         pre_b += hb[j] & kShareMask;
         pre_a += ha[j] & kShareMask;
         Sl[j] = pre_a;
         if (l0 + j < L) best = max(best, min(Dl[j], Sl[j]));
       }
-      __syncwarp();
+      if (G == 1) __syncwarp();  // (G > 1: the scan's barrier came after every read)
 #pragma unroll
-      for (int j = 0; j < LPL; ++j) {
+      for (int j = 0; j < LPT; ++j) {
         if (l0 + j < L) {
           lvb[l0 + j] = Dl[j] | (hb[j] & ~kShareMask);
           lva[l0 + j] = Sl[j] | (ha[j] & ~kShareMask);
         }
       }
-      V = __reduce_max_sync(0xFFFFFFFFu, best);
+      V = grp_agg6<G>(Agg6{0u, 0u, 0u, 0xFFFFFFFFu, best, 0u}, s_x, par).mx;
       if (V > 0) {
         // D falls and S rises with the level: count the levels at or above V
         u32 cb = 0, ca = 0;
 #pragma unroll
-        for (int j = 0; j < LPL; ++j) {
+        for (int j = 0; j < LPT; ++j) {
           cb += (l0 + j < L) && Dl[j] >= V;
           ca += (l0 + j < L) && Sl[j] >= V;
         }
-        const int lb = (int)__reduce_add_sync(0xFFFFFFFFu, cb) - 1;
-        const int la = (int)L - (int)__reduce_add_sync(0xFFFFFFFFu, ca);
-        __syncwarp();
+        const Agg6 r3 = grp_agg6<G>(Agg6{cb, ca, 0u, 0xFFFFFFFFu, 0u, 0u}, s_x, par);
+        const int lb = (int)r3.s0 - 1, la = (int)L - (int)r3.s1;
+        grp_sync<G>();
         if ((lvb[lb] >> kShareBits) > kWarpMarginal || (lva[la] >> kShareBits) > kWarpMarginal) {
-          if (lane == 0) out_volume[b] = -1;  // a crowded marginal level: the sort path takes it
+          if (t == 0) out_volume[b] = -1;  // a crowded marginal level: the sort path takes it
           continue;
         }
         pb = pmin + lb;
@@ -390,19 +471,19 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
       }
     }
     if (V == 0 && !zq) {
-      if (lane == 0) {
+      if (t == 0) {
         out_volume[b] = 0;
         out_price[b] = -1;
       }
       continue;
     }
     // whole fills (and zero-qty orders) written here; marginal orders marked
-    // in per-lane bit masks (bit k = this lane's slot k), listed below
+    // in per-thread bit masks (bit k = this thread's slot k), listed below
     using Mask = typename std::conditional<(SPL > 32), u64, u32>::type;
     Mask mmb = 0, mma = 0;
 #pragma unroll
     for (int k = 0; k < SPL; ++k) {
-      const int i = 4 * ((k >> 2) * 32 + lane) + (k & 3);
+      const int i = 4 * ((k >> 2) * T + t) + (k & 3);
       const bool live = w[k] & kLive, ask = w[k] & kAsk;
       const u32 q = w[k] & kShareMask;
       const bool whole = live && (q == 0 || (V > 0 && (ask ? px[k] < pa : px[k] > pb)));
@@ -414,32 +495,28 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
       mmb |= (Mask)(marg && !ask) << k;
       mma |= (Mask)(marg && ask) << k;
     }
-    int nm0 = 0, nm1 = 0;
     if (V > 0) {
-      // list positions: warp scan of the per-lane counts; qty and time of the
+      // list positions: scan of the per-thread counts; qty and time of the
       // marginal orders from global memory (neither written by this kernel)
-      const int cb = popc_mask(mmb), ca = popc_mask(mma);
-      const int ib = (int)warp_incl_scan((u32)cb, lane), ia = (int)warp_incl_scan((u32)ca, lane);
-      nm0 = __shfl_sync(0xFFFFFFFFu, ib, 31);
-      nm1 = __shfl_sync(0xFFFFFFFFu, ia, 31);
+      const u32 cb = (u32)popc_mask(mmb), ca = (u32)popc_mask(mma);
+      u32 eb, ea, nm0, nm1;
+      grp_scan2<G>(cb, ca, eb, ea, nm0, nm1, s_x, par);
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
         Mask m = s ? mma : mmb;
-        int pos = s ? ia - ca : ib - cb;
+        u32 pos = s ? ea : eb;
         while (m) {
           const int k = ffs_mask(m) - 1;
           m &= m - 1;
-          const u32 i = 4u * (u32)((k >> 2) * 32 + lane) + (u32)(k & 3);
+          const u32 i = 4u * (u32)((k >> 2) * T + t) + (u32)(k & 3);
           m_qty[s * kWarpMarginal + pos] = (u32)qty[o + i];
           m_key[s * kWarpMarginal + pos] = ((u64)ord32(time[o + i]) << 32) | i;
           ++pos;
         }
       }
-    }
-    __syncwarp();
-    if (V > 0) {
-      for (int e = lane; e < nm0 + nm1; e += 32) {
-        const int s = e >= nm0, f = e - (s ? nm0 : 0), m = s ? nm1 : nm0;
+      grp_sync<G>();
+      for (int e = t; e < (int)(nm0 + nm1); e += T) {
+        const int s = e >= (int)nm0, f = e - (s ? (int)nm0 : 0), m = s ? (int)nm1 : (int)nm0;
         const u32* mq = m_qty + s * kWarpMarginal;
         const u64* mk = m_key + s * kWarpMarginal;
         const u64 mine = mk[f];
@@ -454,7 +531,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
         }
       }
     }
-    if (lane == 0) {
+    if (t == 0) {
       out_volume[b] = (long long)V;
       out_price[b] = V > 0 ? pa : -1;
     }
@@ -547,25 +624,42 @@ static int lob_pad(int cap) {
   return n;
 }
 
-template <int SPL, bool kVec16>
-static abm_status lob_launch_warp(int n_books, int cap, int32_t* active, const int32_t* side, const int32_t* price,
-                                  int32_t* qty, const int32_t* time, long long* vol, int32_t* px, cudaStream_t st) {
+static int g_lob_warps_per_book = 2;  // level path: warps per book (1, 2 or 4)
+
+template <int G, int SPL, bool kVec16>
+static abm_status lob_launch_levels(int n_books, int cap, int32_t* active, const int32_t* side, const int32_t* price,
+                                    int32_t* qty, const int32_t* time, long long* vol, int32_t* px, cudaStream_t st) {
   static int blocks_per_sm = 0;
-  const size_t smem = kWarpsPerBlock * warp_smem_bytes(SPL);
+  const size_t smem = grp_smem_bytes(G * 32 * SPL);
   if (!blocks_per_sm) {
-    ABM_CUDA_TRY(cudaFuncSetAttribute(k_lob_match_warp<SPL, kVec16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
+    ABM_CUDA_TRY(cudaFuncSetAttribute(k_lob_match_levels<G, SPL, kVec16>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
-    ABM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lob_match_warp<SPL, kVec16>,
-                                                               kWarpsPerBlock * 32, smem));
+    ABM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lob_match_levels<G, SPL, kVec16>, G * 32,
+                                                               smem));
     blocks_per_sm = std::max(occ, 1);
   }
-  const long long want = ((long long)n_books + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  const int grid = (int)std::min<long long>(want, (long long)num_sms() * blocks_per_sm);
-  k_lob_match_warp<SPL, kVec16><<<grid, kWarpsPerBlock * 32, smem, st>>>(n_books, cap, active, side, price, qty,
-                                                                          time, vol, px);
+  const int grid = (int)std::min<long long>(n_books, (long long)num_sms() * blocks_per_sm);
+  k_lob_match_levels<G, SPL, kVec16><<<grid, G * 32, smem, st>>>(n_books, cap, active, side, price, qty, time, vol,
+                                                                  px);
   ABM_LAUNCH_CHECK();
   return ABM_OK;
+}
+
+// the smallest slots-per-thread (a multiple of 4) that covers cap
+template <int G, bool kVec16>
+static abm_status lob_launch_g(int n_books, int cap, int32_t* active, const int32_t* side, const int32_t* price,
+                               int32_t* qty, const int32_t* time, long long* vol, int32_t* px, cudaStream_t st) {
+  constexpr int T = G * 32;
+  if (cap <= 4 * T) return lob_launch_levels<G, 4, kVec16>(n_books, cap, active, side, price, qty, time, vol, px, st);
+  if (cap <= 8 * T) return lob_launch_levels<G, 8, kVec16>(n_books, cap, active, side, price, qty, time, vol, px, st);
+  if (cap <= 16 * T)
+    return lob_launch_levels<G, 16, kVec16>(n_books, cap, active, side, price, qty, time, vol, px, st);
+  if (G <= 2 && cap <= 32 * T)
+    return lob_launch_levels<G, (G <= 2 ? 32 : 16), kVec16>(n_books, cap, active, side, price, qty, time, vol, px,
+                                                             st);
+  return lob_launch_levels<G, (G == 1 ? 64 : 16), kVec16>(n_books, cap, active, side, price, qty, time, vol, px,
+                                                           st);
 }
 
 template <int R>
@@ -585,12 +679,23 @@ static abm_status lob_launch_deferred(int n_books, int cap, int32_t* active, con
   return ABM_OK;
 }
 
-template <int SPL>
 static abm_status lob_launch(bool vec16, int n_books, int cap, int32_t* active, const int32_t* side,
                              const int32_t* price, int32_t* qty, const int32_t* time, long long* vol, int32_t* px,
                              cudaStream_t st) {
-  abm_status e = vec16 ? lob_launch_warp<SPL, true>(n_books, cap, active, side, price, qty, time, vol, px, st)
-                       : lob_launch_warp<SPL, false>(n_books, cap, active, side, price, qty, time, vol, px, st);
+  abm_status e;
+  switch (g_lob_warps_per_book) {
+    case 1:
+      e = vec16 ? lob_launch_g<1, true>(n_books, cap, active, side, price, qty, time, vol, px, st)
+                : lob_launch_g<1, false>(n_books, cap, active, side, price, qty, time, vol, px, st);
+      break;
+    case 4:
+      e = vec16 ? lob_launch_g<4, true>(n_books, cap, active, side, price, qty, time, vol, px, st)
+                : lob_launch_g<4, false>(n_books, cap, active, side, price, qty, time, vol, px, st);
+      break;
+    default:
+      e = vec16 ? lob_launch_g<2, true>(n_books, cap, active, side, price, qty, time, vol, px, st)
+                : lob_launch_g<2, false>(n_books, cap, active, side, price, qty, time, vol, px, st);
+  }
   if (e != ABM_OK) return e;
   switch (lob_pad(cap) / kLobThreads) {
     case 1: return lob_launch_deferred<1>(n_books, cap, active, side, price, qty, time, vol, px, st);
@@ -615,10 +720,13 @@ extern "C" abm_status abm_lob_match(int32_t n_books, int32_t cap, int32_t* activ
       cap % 4 == 0 && ((uintptr_t)active | (uintptr_t)side | (uintptr_t)price | (uintptr_t)qty) % 16 == 0;
   long long* vol = reinterpret_cast<long long*>(out_volume);
   const cudaStream_t st = (cudaStream_t)stream;
-  if (cap <= 256) return lob_launch<8>(vec16, n_books, cap, active, side, price, qty, time, vol, out_price, st);
-  if (cap <= 512) return lob_launch<16>(vec16, n_books, cap, active, side, price, qty, time, vol, out_price, st);
-  if (cap <= 1024) return lob_launch<32>(vec16, n_books, cap, active, side, price, qty, time, vol, out_price, st);
-  return lob_launch<64>(vec16, n_books, cap, active, side, price, qty, time, vol, out_price, st);
+  return lob_launch(vec16, n_books, cap, active, side, price, qty, time, vol, out_price, st);
+}
+
+extern "C" abm_status abm_lob_tune(int32_t warps_per_book) {
+  if (warps_per_book != 0 && warps_per_book != 1 && warps_per_book != 2 && warps_per_book != 4) return ABM_ERR_ARG;
+  g_lob_warps_per_book = warps_per_book ? warps_per_book : 2;
+  return ABM_OK;
 }
 
 extern "C" abm_status abm_lob_add(int32_t n_books, int32_t cap, int32_t* active, int32_t* side, int32_t* price,

@@ -278,6 +278,11 @@ class OrderBooks:
     def numpy(self) -> dict:
         return {f: self.t[f].cpu().numpy() for f in self.FIELDS}
 
+    @staticmethod
+    def tune(warps_per_book: int = 0):
+        """Warps matching one book on the price-level path (process-wide)."""
+        call("abm_lob_tune", int(warps_per_book))
+
 
 def decode_stats(t: torch.Tensor) -> list[dict]:
     """Device stats rows (int32 words) -> list of dicts."""

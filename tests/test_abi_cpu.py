@@ -58,3 +58,4 @@ def test_host_only_calls(lib_path):
     assert L.abm_lob_match(0, 8, None, None, None, None, None, None, None, None) == abm.OK
     assert L.abm_lob_add(1, 8, None, None, None, None, None, None, None, -1, None, None) == abm.ERR_ARG
     assert L.abm_lob_add(1, 8, None, None, None, None, None, None, None, 0, None, None) == abm.ERR_ARG
+    assert L.abm_lob_tune(3) == abm.ERR_ARG and L.abm_lob_tune(0) == abm.OK

@@ -209,3 +209,18 @@ def test_market_paper_scale(eng):
     for f in ref:
         np.testing.assert_array_equal(got[f], ref[f], err_msg=f)
     assert traded > 0
+
+
+@pytest.mark.parametrize("warps", [1, 2, 4])
+@pytest.mark.parametrize("cap", [7, 128, 257, 1000, 1024, 2048])
+def test_match_every_launch_shape(eng, warps, cap):
+    """The price-level path with 1, 2 or 4 warps per book (results must not
+    depend on it), ragged and full caps, crowded and wide books mixed in."""
+    eng.OrderBooks.tune(warps)
+    try:
+        book = workloads.random_books(97, cap, 0.7, seed=cap * 3 + warps)
+        book["price"][5::7] = 100  # some books on one price level
+        book["price"][3::11] = np.where(book["side"][3::11] == 0, 10**6, 10)  # some with a wide range
+        check_match(eng, book)
+    finally:
+        eng.OrderBooks.tune(0)
