@@ -151,32 +151,43 @@ def kernel_bytes(k: int, st: dict) -> int:
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_persistent_large_predation_traffic.txt")
 TRAFFIC_SOURCES = ("pred_persistent.cu", "pred_world.cuh", "pred_rules.cuh", "common.cuh")
+LOB_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_lob_match_levels_65536x1024.md")
+LOB_TRAFFIC_SOURCES = ("lob.cu", "common.cuh")
 
 
-def persistent_sources_sha256() -> str:
+def sources_sha256(names) -> str:
     import hashlib
     h = hashlib.sha256()
-    for name in TRAFFIC_SOURCES:
+    for name in names:
         with open(os.path.join(ROOT, "paper_2508_16508_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
 
 
-def persistent_traffic(K: int, W: int, ctas_per_sm: int):
-    """DRAM bytes (read + write) of the timed k_persistent launch from the
-    stored ncu capture, or None when the capture covers another step range or
-    the kernel's sources changed since it was taken."""
+def persistent_sources_sha256() -> str:
+    return sources_sha256(TRAFFIC_SOURCES)
+
+
+def stored_traffic(path: str, sources, **must):
+    """DRAM bytes (read + write) of one launch from a stored single-pass ncu
+    capture (key = value lines), or None when the capture was of another
+    launch (any `must` key differs) or the kernel's sources changed since."""
     try:
-        with open(TRAFFIC_FILE) as f:
+        with open(path) as f:
             kv = dict(ln.split("=", 1) for ln in (x.strip() for x in f) if "=" in ln and not ln.startswith("#"))
         kv = {k.strip(): v.strip() for k, v in kv.items()}
-        if kv.get("sources_sha256") != persistent_sources_sha256():
+        if kv.get("sources_sha256") != sources_sha256(sources):
             return None
-        if int(kv["steps"]) != K or int(kv["warmup"]) != W or int(kv["ctas_per_sm"]) != ctas_per_sm:
+        if any(int(kv[k]) != int(v) for k, v in must.items()):
             return None
         return int(kv["dram_bytes_read"]) + int(kv["dram_bytes_write"])
     except (OSError, KeyError, ValueError):
         return None
+
+
+def persistent_traffic(K: int, W: int, ctas_per_sm: int):
+    """DRAM bytes of the timed k_persistent launch (see stored_traffic)."""
+    return stored_traffic(TRAFFIC_FILE, TRAFFIC_SOURCES, steps=K, warmup=W, ctas_per_sm=ctas_per_sm)
 
 
 # ----------------------------------------------------------------------------
@@ -585,6 +596,8 @@ def lob_leg(torch, engine, hbm_peak, reps=10, n_books=None):
            "live_orders_per_s": live / (ms * 1e-3), "live_orders": live, "traded_shares": want[0],
            "books_crossed": int((vol > 0).sum()), "same_result_every_rep": same,
            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                        "traffic": stored_traffic(LOB_TRAFFIC_FILE, LOB_TRAFFIC_SOURCES, n_books=nb_, cap=W["cap"],
+                                                  warps_per_book=best_g),
                         "algorithmic_bytes_per_launch": alg,
                         "bytes_per_slot": {"algorithmic": alg / slots, "sector_min": None},
                         "note": "algorithmic words: active of every slot, side/price/qty of live slots, the "
