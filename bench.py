@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--batch-models", type=int, default=None)
     ap.add_argument("--batch-steps", type=int, default=None)
     ap.add_argument("--lob-books", type=int, default=None, help="lob leg: books in the matching round")
+    ap.add_argument("--lob-warps", type=int, default=None, choices=[1, 2, 4],
+                    help="lob leg: warps per book instead of the sweep (fixed launch sequence for ncu)")
     a = ap.parse_args()
     if a.leg == "predation":
         a.no_extras = True
@@ -536,7 +538,7 @@ def many_wolves_leg(torch, engine, abm, K, W, ctas_per_sm):
             "eaten": sum(r["eaten"] for r in rows), "end_counters": gw.counters()}
 
 
-def lob_leg(torch, engine, hbm_peak, reps=10, n_books=None):
+def lob_leg(torch, engine, hbm_peak, reps=10, n_books=None, warps=None):
     """Order-book matching (Section 5.3): one matching round of 65536 books x
     1024 slots (half live), timed kernel-only on a freshly restored book each
     rep (inputs 1.3 GB, larger than L2; L2 also flushed); plus the finance
@@ -579,12 +581,13 @@ def lob_leg(torch, engine, hbm_peak, reps=10, n_books=None):
             ts.append(e0.elapsed_time(e1))
         return ts
 
-    # launch shape: warps per book on the price-level path (results identical)
+    # launch shape: warps per book on the price-level path (results identical);
+    # a fixed shape skips the sweep (a fixed launch sequence for ncu)
     trials = {}
-    for g in (1, 2, 4):
+    for g in ((warps,) if warps else (1, 2, 4)):
         engine.OrderBooks.tune(g)
-        trials[g] = statistics.median(timed(4))
-    best_g = min(trials, key=trials.get)
+        trials[g] = statistics.median(timed(4)) if not warps else None
+    best_g = warps or min(trials, key=trials.get)
     engine.OrderBooks.tune(best_g)
     ts = timed(reps)
     same = (int(vol.sum()), int(px.sum())) == want
@@ -719,7 +722,7 @@ def run_ours(args, rank, world, local):
                     out = selective_update_leg(torch, engine, abm, autotune, hbm_peak, tune=not args.no_tune,
                                                ps=args.p)
                 elif args.leg == "lob":
-                    out = lob_leg(torch, engine, hbm_peak, n_books=args.lob_books)
+                    out = lob_leg(torch, engine, hbm_peak, n_books=args.lob_books, warps=args.lob_warps)
                 else:
                     out = batched_leg(torch, engine, capacity, autotune, abm, hbm_peak, n_models=args.batch_models,
                                       steps=args.batch_steps, tune=not args.no_tune)
