@@ -637,10 +637,40 @@ def lob_leg(torch, engine, hbm_peak, reps=10, n_books=None, warps=None):
         e1.record()
         e1.synchronize()
         mts.append(e0.elapsed_time(e1))
+    eager = (int(mv.sum()), int(ma.sum()), int(mp.sum()))
+    # the same 100 steps captured once in a CUDA graph (no host launch cost),
+    # replayed from a restored book each time
+    mb = engine.OrderBooks(mbook)
+    start = {f: mb.t[f].clone() for f in engine.OrderBooks.FIELDS}
+    gs = torch.cuda.Stream()
+    gs.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(gs):
+        with torch.cuda.graph(graph, stream=gs):
+            for st in range(M["steps"]):
+                mb.add(d_orders[st], d_k[st], out=ma[st])
+                mb.match(mv[st], mp[st])
+    torch.cuda.current_stream().wait_stream(gs)
+    gts, same_graph = [], True
+    for _ in range(5):
+        for f in engine.OrderBooks.FIELDS:
+            mb.t[f].copy_(start[f])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        graph.replay()
+        e1.record()
+        e1.synchronize()
+        gts.append(e0.elapsed_time(e1))
+        same_graph &= (int(mv.sum()), int(ma.sum()), int(mp.sum())) == eager
+    del graph
     out["market"] = {"workload": M["name"], "ms_100_steps": statistics.median(mts), "ms_all": mts,
                      "us_per_step": 1e3 * statistics.median(mts) / M["steps"],
-                     "traded_shares": int(mv.sum()), "orders_placed": int(ma.sum()),
-                     "launches": 2 * M["steps"],
+                     "graph_ms_100_steps": statistics.median(gts), "graph_ms_all": gts,
+                     "graph_us_per_step": 1e3 * statistics.median(gts) / M["steps"],
+                     "graph_same_result": same_graph,
+                     "traded_shares": eager[0], "orders_placed": eager[1],
+                     "launches": 3 * M["steps"],
                      "paper_ms_100_steps_500_books": 2212.47,
                      "note": "paper figure: Table 4 (JAX, its own hardware): context, not a target"}
     return out

@@ -35,6 +35,7 @@
 // sort of the whole book in shared memory, cumulative sums, a binary search
 // per bid.
 #include <algorithm>
+#include <atomic>
 #include <type_traits>
 
 #include "common.cuh"
@@ -624,7 +625,7 @@ static int lob_pad(int cap) {
   return n;
 }
 
-static int g_lob_warps_per_book = 2;  // level path: warps per book (1, 2 or 4)
+static std::atomic<int> g_lob_warps_per_book{2};  // level path: warps per book (1, 2 or 4)
 
 template <int G, int SPL, bool kVec16>
 static abm_status lob_launch_levels(int n_books, int cap, int32_t* active, const int32_t* side, const int32_t* price,
@@ -683,7 +684,7 @@ static abm_status lob_launch(bool vec16, int n_books, int cap, int32_t* active, 
                              const int32_t* price, int32_t* qty, const int32_t* time, long long* vol, int32_t* px,
                              cudaStream_t st) {
   abm_status e;
-  switch (g_lob_warps_per_book) {
+  switch (g_lob_warps_per_book.load(std::memory_order_relaxed)) {
     case 1:
       e = vec16 ? lob_launch_g<1, true>(n_books, cap, active, side, price, qty, time, vol, px, st)
                 : lob_launch_g<1, false>(n_books, cap, active, side, price, qty, time, vol, px, st);
@@ -725,7 +726,7 @@ extern "C" abm_status abm_lob_match(int32_t n_books, int32_t cap, int32_t* activ
 
 extern "C" abm_status abm_lob_tune(int32_t warps_per_book) {
   if (warps_per_book != 0 && warps_per_book != 1 && warps_per_book != 2 && warps_per_book != 4) return ABM_ERR_ARG;
-  g_lob_warps_per_book = warps_per_book ? warps_per_book : 2;
+  g_lob_warps_per_book.store(warps_per_book ? warps_per_book : 2, std::memory_order_relaxed);
   return ABM_OK;
 }
 

@@ -224,3 +224,41 @@ def test_match_every_launch_shape(eng, warps, cap):
         check_match(eng, book)
     finally:
         eng.OrderBooks.tune(0)
+
+
+def test_market_graph_replay_equals_eager(eng):
+    """Placement + matching steps captured in a CUDA graph and replayed give
+    the eager calls' results (every call enqueues on the capturing stream)."""
+    n_books, cap, kmax, steps = 200, 500, 10, 12
+    orders, ks = workloads.market_orders(n_books, kmax, steps, seed=77)
+    book = workloads.random_books(n_books, cap, 0.3, seed=78)
+    d_orders, d_k = torch.from_numpy(orders).cuda(), torch.from_numpy(ks).cuda()
+    outs = [torch.empty(steps, n_books, dtype=t, device="cuda") for t in (torch.int32, torch.int64, torch.int32)]
+    eager = eng.OrderBooks(book)
+    for st in range(steps):
+        eager.add(d_orders[st], d_k[st], out=outs[0][st])
+        eager.match(outs[1][st], outs[2][st])
+    torch.cuda.synchronize()
+    want = [o.clone() for o in outs]
+    replay = eng.OrderBooks(book)
+    start = {f: replay.t[f].clone() for f in replay.FIELDS}
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            for st in range(steps):
+                replay.add(d_orders[st], d_k[st], out=outs[0][st])
+                replay.match(outs[1][st], outs[2][st])
+    torch.cuda.current_stream().wait_stream(s)
+    for _ in range(2):
+        for f in replay.FIELDS:
+            replay.t[f].copy_(start[f])
+        for o in outs:
+            o.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        for o, w in zip(outs, want):
+            assert torch.equal(o, w)
+        for f in replay.FIELDS:
+            assert torch.equal(replay.t[f], eager.t[f]), f
