@@ -333,7 +333,7 @@ __device__ __forceinline__ void grp_stage(int32_t* s_act, int n, int b, int cap,
 // registers, and the next book is staged at once. Deferred books get
 // out_volume = -1 and are left untouched.
 template <int G, int SPL, bool kVec16>
-__global__ void __launch_bounds__(G * 32, (G == 2 && SPL <= 16) ? 11 : 0)
+__global__ void __launch_bounds__(G * 32)
     k_lob_match_levels(int n_books, int cap, int32_t* active, const int32_t* __restrict__ side,
                        const int32_t* __restrict__ price, int32_t* qty, const int32_t* __restrict__ time,
                        long long* out_volume, int32_t* out_price) {
