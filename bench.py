@@ -12,8 +12,10 @@ the start of the step, divided by the device time.
 The same JSON line carries the selective-update microbenchmark (2^24 slots x 8
 int32 fields, p in {0.001, 0.05, 0.5}, plus the Zipf conflict pass) in HBM
 GB/s; the batched legs (4096 models, 500 steps: plain fixed capacity vs
-learned capacity); the roofline of the timed kernel; the oracle's CPU timing;
-and the end-to-end (host API) rate.
+learned capacity); the order-book leg (one matching round of 65536 books x 1024
+slots, and the 500-book, 100-step market run eager and from a CUDA graph); the
+roofline of the timed kernel; the oracle's CPU timing; and the end-to-end
+(host API) rate. ``--leg selective|batched|lob|predation`` runs one leg alone.
 
 ``--impl reference`` times the sequential CPU oracle on the same workload.
 """
