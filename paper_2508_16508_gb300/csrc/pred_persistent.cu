@@ -22,8 +22,8 @@ namespace abm {
 
 constexpr int kPT = 512;                  // threads per CTA
 constexpr int kPWarps = kPT / 32;
-constexpr int kBarSpin = 1 << 24;
-constexpr int kPhases = 5;                // grid barriers per step (plus one closing a launch)         // bounded barrier wait (~2 s with the back-off)
+constexpr int kBarSpin = 1 << 24;         // bounded barrier wait (polls; a few seconds)
+constexpr int kPhases = 5;                // grid barriers per step (plus one closing a launch)
 
 // Grid barrier (all CTAs co-resident: cooperative launch) over a monotonic
 // arrival counter: the k-th barrier of a launch is passed once the counter
@@ -49,15 +49,16 @@ __device__ __forceinline__ void grid_sync(u32* bar, int* err, u32& target, u32 e
   if (threadIdx.x == 0) {
     red_release_add(bar, 1u);
     int spins = 0;
-    u32 backoff = 16;
+    u32 backoff = 8;
     while ((int)(ld_acquire32(bar) - target) < 0) {
       if (++spins > limit) {
         atomicExch(err, kErrTimeout);
         break;
       }
-      if (ld_relaxed32(reinterpret_cast<const u32*>(err)) != 0u) break;  // another CTA gave up
+      // another CTA gave up (checked now and then: one round trip per poll)
+      if ((spins & 63) == 0 && ld_relaxed32(reinterpret_cast<const u32*>(err)) != 0u) break;
       __nanosleep(backoff);
-      if (backoff < 128) backoff <<= 1;
+      if (backoff < 32) backoff <<= 1;
     }
   }
   __syncthreads();
