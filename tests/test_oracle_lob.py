@@ -100,11 +100,13 @@ def test_add_into_lowest_free_slots():
     rng = np.random.default_rng(5)
     book = workloads.random_books(30, 40, 0.5, 9)
     new, k = workloads.random_new_orders(30, 25, 10)
+    k[0], k[1], k[2] = -4, 25 + 7, 0  # counts outside [0, kmax] are clamped to it
+    book["active"][1] = 0  # 40 free slots: only kmax = 25 orders exist to place
     before = copy(book)
     added = oracle.lob_add(book, new, k)
     for b in range(30):
         free = [i for i in range(40) if not before["active"][b, i]]  # ascending
-        r = min(int(k[b]), len(free))
+        r = min(max(int(k[b]), 0), 25, len(free))
         assert added[b] == r
         for j, slot in enumerate(free[:r]):
             assert book["active"][b, slot] == 1
@@ -113,6 +115,7 @@ def test_add_into_lowest_free_slots():
         for f in ("active", "side", "price", "qty", "time"):
             np.testing.assert_array_equal(book[f][b, untouched], before[f][b, untouched])
     del rng
+    assert added[0] == 0 and added[1] == 25 and added[2] == 0
 
 
 @pytest.mark.parametrize("seed", range(8))
