@@ -132,7 +132,8 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------
-# algorithmic bytes per kernel launch (units and per-unit bytes listed in the design doc)
+# algorithmic bytes per kernel launch: each access of a phase counted once at its
+# natural size, from the step's statistics (agents moved, winners, parents, ...)
 
 def kernel_bytes(k: int, st: dict) -> int:
     s = 0 if k < 3 else 1

@@ -3,7 +3,7 @@
  *
  * Every function cites the passage of the ABMax paper (arXiv 2508.16508) it
  * restates. Where the paper is silent, the reading used is written beside the
- * code; the same readings are listed in the design doc.
+ * code.
  */
 #include "oracle.h"
 #include <stdlib.h>
