@@ -270,13 +270,18 @@ abm_status abm_resolve(const int32_t* claim_res, const uint32_t* claim_prio, int
  * embedding that forbids the CUDA allocator outright. This entry point
  * allocates nothing -- no cudaMalloc, cudaFree or allocating library call --
  * and takes no scratch argument: its per-resource table is a file-scope
- * device array of ABM_RESOLVE_STATIC_MAX_R 64-bit entries (2 MiB), which
- * every GPU that loads the library holds until the process exits. The caller
+ * device array of ABM_RESOLVE_STATIC_MAX_R 64-bit entries (2 MiB). The caller
  * still passes the inputs and outputs (same meaning as abm_resolve).
  *  - R above ABM_RESOLVE_STATIC_MAX_R returns ABM_ERR_TOO_LARGE.
- *  - The first call on a device looks the array's device address up
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *  - The array belongs to the library's device code, which CUDA loads onto a
+ *    device lazily (by default) the first time the library touches that
+ *    device: from then on the device holds the 2 MiB until the process exits.
+ *  - The first call on a device also looks the array's device address up
+ *    (cudaGetSymbolAddress) with that device current, and may be the moment
+ *    the module is loaded (one driver allocation). So make one call on each
+ *    device -- a warm-up with M = 0 will do -- before any stream capture and
+ *    before the period in which the host forbids allocation; later calls
+ *    allocate nothing.
  *  - All calls share the one array. Each call empties the entries it uses
  *    before claiming, so nothing carries over between calls, but calls that
  *    overlap on the GPU (different streams, or different host threads on the

@@ -10,6 +10,7 @@
 //    which keeps the kernels CUDA-graph replayable without memset nodes.
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -262,5 +263,21 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, cudaStream
   } while (0)
 
 namespace abm {
-int num_sms();  // cached multiprocessor count of the current device
+int num_sms();  // multiprocessor count of the current device (cached per device)
+
+// A kernel's dynamic shared-memory limit is a per-device setting: set it once
+// for each device a process uses (bit d of `done` records device d; devices
+// beyond 63 set it on every call). Two threads that race on a device's first
+// call both set it, which is harmless.
+template <typename K>
+inline cudaError_t smem_attr_once(K* kernel, int bytes, std::atomic<unsigned long long>& done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = (dev >= 0 && dev < 64) ? 1ull << dev : 0ull;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_release);
+  return e;
+}
 }

@@ -630,15 +630,20 @@ static std::atomic<int> g_lob_warps_per_book{2};  // level path: warps per book 
 template <int G, int SPL, bool kVec16>
 static abm_status lob_launch_levels(int n_books, int cap, int32_t* active, const int32_t* side, const int32_t* price,
                                     int32_t* qty, const int32_t* time, long long* vol, int32_t* px, cudaStream_t st) {
-  static int blocks_per_sm = 0;
+  // the shared-memory limit and the occupancy are per device: looked up once for each
+  static std::atomic<unsigned long long> attr{0};
+  static std::atomic<int> occ_dev[64];
   const size_t smem = grp_smem_bytes(G * 32 * SPL);
+  ABM_CUDA_TRY(smem_attr_once(k_lob_match_levels<G, SPL, kVec16>, (int)smem, attr));
+  int dev = 0;
+  ABM_CUDA_TRY(cudaGetDevice(&dev));
+  int blocks_per_sm = (dev >= 0 && dev < 64) ? occ_dev[dev].load(std::memory_order_relaxed) : 0;
   if (!blocks_per_sm) {
-    ABM_CUDA_TRY(cudaFuncSetAttribute(k_lob_match_levels<G, SPL, kVec16>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
     ABM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lob_match_levels<G, SPL, kVec16>, G * 32,
                                                                smem));
     blocks_per_sm = std::max(occ, 1);
+    if (dev >= 0 && dev < 64) occ_dev[dev].store(blocks_per_sm, std::memory_order_relaxed);
   }
   const int grid = (int)std::min<long long>(n_books, (long long)num_sms() * blocks_per_sm);
   k_lob_match_levels<G, SPL, kVec16><<<grid, G * 32, smem, st>>>(n_books, cap, active, side, price, qty, time, vol,
@@ -668,11 +673,8 @@ static abm_status lob_launch_deferred(int n_books, int cap, int32_t* active, con
                                       const int32_t* price, int32_t* qty, const int32_t* time, long long* vol,
                                       int32_t* px, cudaStream_t st) {
   constexpr size_t smem = (size_t)R * kLobThreads * (4 * sizeof(int32_t) + sizeof(u64) + sizeof(u32));
-  static bool attr = false;
-  if (!attr) {
-    ABM_CUDA_TRY(cudaFuncSetAttribute(k_lob_deferred<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr{0};
+  ABM_CUDA_TRY(smem_attr_once(k_lob_deferred<R>, (int)smem, attr));
   const long long chunks = ((long long)n_books + kLobThreads - 1) / kLobThreads;
   const int grid = (int)std::min<long long>(chunks, (long long)num_sms() * 2);
   k_lob_deferred<R><<<grid, kLobThreads, smem, st>>>(n_books, cap, active, side, price, qty, time, vol, px);

@@ -124,15 +124,12 @@ __global__ void k_is_winner_scalar(const int32_t* __restrict__ res, int M, int R
   }
 }
 
-static bool g_res_attr = false;
+static std::atomic<unsigned long long> g_res_attr{0};  // devices whose k_claims has its smem limit
 
 abm_status resolve_launch(const int32_t* claim_res, const uint32_t* claim_prio, int32_t M, int32_t R,
                           uint64_t* table, int32_t* out_winner, uint8_t* out_is_winner, cudaStream_t st) {
   const size_t smem = (size_t)kHash * (sizeof(u64) + sizeof(int));
-  if (!g_res_attr) {
-    ABM_CUDA_TRY(cudaFuncSetAttribute(k_claims, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    g_res_attr = true;
-  }
+  ABM_CUDA_TRY(smem_attr_once(k_claims, (int)smem, g_res_attr));
   const int sms = num_sms();
   if (M > 0) {
     const int nchunks = (M + kResChunk - 1) / kResChunk;

@@ -11,6 +11,7 @@
 // equal nonzero ranks), computed in O(n + k) instead of O(n * k). The passes
 // are chained with programmatic dependent launch; no pass spins on another CTA.
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -19,15 +20,20 @@
 
 namespace abm {
 
-static int g_num_sms = 0;
+// SM count per device, looked up once per device (a process may drive
+// several GPUs from several host threads: relaxed atomics, idempotent writes)
+constexpr int kSmCacheDevices = 64;
+static std::atomic<int> g_num_sms[kSmCacheDevices];
 int num_sms() {
-  if (g_num_sms == 0) {
-    int dev = 0, n = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
-    g_num_sms = n > 0 ? n : 1;
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (dev >= 0 && dev < kSmCacheDevices) {
+    n = g_num_sms[dev].load(std::memory_order_relaxed);
+    if (n > 0) return n;
   }
-  return g_num_sms;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) return 1;
+  if (dev >= 0 && dev < kSmCacheDevices) g_num_sms[dev].store(n, std::memory_order_relaxed);
+  return n;
 }
 
 constexpr int kSlabThreads = 256;    // default CTA size of the slab passes

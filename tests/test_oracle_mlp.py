@@ -61,3 +61,32 @@ def test_capacity_rounding():
     yhat = np.log(np.array([[100.0, 5.0], [1e9, 1.0]]))
     cap = mlp.capacity(yhat, 0.1, 128, np.array([[4096, 4096], [4096, 4096]]), np.array([[10, 200], [0, 0]]))
     assert cap.tolist() == [[128, 256], [4096, 128]]
+
+
+def test_features_by_hand():
+    """The twelve inputs of the capacity network, computed by hand for three
+    models: log1p of the side and of the two initial populations, each rule
+    parameter over its nominal value with both read as unsigned 32-bit words
+    (thresholds of 2^31 and above are stored as negative int32), and the
+    horizon over 500."""
+    T_s, T_w, T_g = 171798691, 214748364, 2**31  # floor(0.04 2^32), floor(0.05 2^32), 0.5
+    as_i32 = lambda v: v - 2**32 if v >= 2**31 else v  # noqa: E731
+    nominal = [4, 20, T_s, T_w, 30, 1, 1, as_i32(T_g)]
+    table = np.array([
+        # side, n0 sheep, n0 wolves, 8 params, horizon
+        [16, 100, 25, 4, 20, T_s, T_w, 30, 1, 1, as_i32(T_g), 200],
+        [256, 0, 13106, 5, 15, as_i32(0xC0000000), T_w // 2, 38, 1, 1, as_i32(0xFFFFFFFF), 500],
+        [40, 1, 2, 3, 25, 0, 2**31 - 1, 22, 2, 1, 0, 1],
+    ], dtype=np.int64)
+    x = mlp.features(table.astype(np.int32), np.array(nominal, dtype=np.int32))
+    want = np.array([
+        [np.log(17.0), np.log(101.0), np.log(26.0), 1, 1, 1, 1, 1, 1, 1, 1, 0.4],
+        # 0xC0000000 / T_s: T_s * 18.75 = 3221225456.25, so 18.75 + 15.75 / T_s;
+        # T_w // 2 / T_w = 107374182 / 214748364 = 0.5; 0xFFFFFFFF / 2^31 = 2 - 2^-31
+        [np.log(257.0), 0.0, np.log(13107.0), 1.25, 0.75, 18.75 + 15.75 / T_s, 0.5, 38 / 30, 1, 1,
+         2.0 - 2.0**-31, 1.0],
+        # (2^31 - 1) / T_w = 10 + 7 / T_w  (T_w * 10 = 2147483640)
+        [np.log(41.0), np.log(2.0), np.log(3.0), 0.75, 1.25, 0.0, 10 + 7 / T_w, 22 / 30, 2, 1, 0.0, 0.002],
+    ])
+    assert x.shape == (3, 12)
+    np.testing.assert_allclose(x, want, rtol=1e-14, atol=0)

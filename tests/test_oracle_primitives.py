@@ -201,13 +201,69 @@ def test_update_wraps_int32():
     np.testing.assert_array_equal(s.fields[0], [-2**31, 2**31 - 1])
 
 
+def philox_rows(seed, model, step, purpose, species, n):
+    """Words [n][4] of the Philox block at counters (step, j, purpose, species),
+    j < n, one generator call per counter (the generator itself is pinned to
+    Triton's philox in test_oracle_philox.py)."""
+    out = np.zeros((n, 4), dtype=np.uint32)
+    for j in range(n):
+        out[j] = oracle.philox([step & 0xFFFFFFFF, j, purpose, species], [seed, model])
+    return out
+
+
+def records_by_philox(seed, model, step, p0, p1, k, F):
+    """Record j, field f = word f % 4 of the block of counter (step, j, p0 or p1, 0)."""
+    lo, hi = philox_rows(seed, model, step, p0, 0, k), philox_rows(seed, model, step, p1, 0, k)
+    rec = np.zeros((k, F), dtype=np.uint32)
+    for f in range(F):
+        rec[:, f] = (lo if f < 4 else hi)[:, f % 4]
+    return rec.view(np.int32)
+
+
+@pytest.mark.parametrize("seed,model,step,k,F", [(2, 0, 0, 5, 8), (7, 3, 11, 1, 4), (0, 1, 0xFFFFFFFF, 9, 6),
+                                                 (5, 0, 2, 3, 1)])
+def test_c1_records_word_by_word(seed, model, step, k, F):
+    """The microbenchmark's records against the generator, word by word: field
+    f of record j is word f % 4 of counter (step, j, NEWREC0 / NEWREC1 for the
+    upper four fields, 0) under key (seed, model)."""
+    got = oracle.c1_records(seed, model, step, oracle.P_NEWREC0, oracle.P_NEWREC1, k, F)
+    assert got.shape == (k, F)
+    for j in range(k):
+        w0 = oracle.philox([step, j, oracle.P_NEWREC0, 0], [seed, model])
+        w1 = oracle.philox([step, j, oracle.P_NEWREC1, 0], [seed, model])
+        for f in range(F):
+            assert np.uint32(got[j, f]) == (w0 if f < 4 else w1)[f % 4], (j, f)
+    # the delta records take the other two purposes
+    d = oracle.c1_records(seed, model, step, oracle.P_DELTA0, oracle.P_DELTA1, k, F)
+    np.testing.assert_array_equal(d, records_by_philox(seed, model, step, oracle.P_DELTA0, oracle.P_DELTA1, k, F))
+    assert oracle.c1_records(seed, model, step, oracle.P_NEWREC0, oracle.P_NEWREC1, 0, F).shape == (0, F)
+
+
+@pytest.mark.parametrize("n,F,seed,model", [(37, 8, 2, 0), (10, 5, 9, 4), (1, 1, 0, 0)])
+def test_c1_init_word_by_word(n, F, seed, model):
+    """Initial microbenchmark slab: slot i is live iff word 0 of counter
+    (INIT_STEP, i, INIT_ACTIVE, 0) is below 2^31 (compared as unsigned), and
+    its field f is word f % 4 of counter (INIT_STEP, i, NEWREC0 or NEWREC1, 0)."""
+    s = oracle.Slab(n, F)
+    s.c1_init(seed=seed, model=model)
+    for i in range(n):
+        a = oracle.philox([oracle.INIT_STEP, i, oracle.P_INIT_ACTIVE, 0], [seed, model])
+        assert s.active[i] == (1 if int(a[0]) < 2**31 else 0), i
+        w0 = oracle.philox([oracle.INIT_STEP, i, oracle.P_NEWREC0, 0], [seed, model])
+        w1 = oracle.philox([oracle.INIT_STEP, i, oracle.P_NEWREC1, 0], [seed, model])
+        for f in range(F):
+            assert np.uint32(s.fields[f, i]) == (w0 if f < 4 else w1)[f % 4], (i, f)
+    if n >= 10:
+        assert 0 < s.active.sum() < n  # both outcomes occur: the comparison is not constant
+
+
 def c1_call_brute(active, fields, seed, step, T, k):
     """Microbenchmark call restated with numpy on Philox draws."""
     n, F = fields.shape[1], fields.shape[0]
     active = active.copy(); fields = fields.copy().astype(np.int64)
     # slots 2j and 2j+1 share draw j: words (0, 1) and (2, 3) = (remove, choose)
     half = (n + 1) // 2
-    w = np.stack([oracle.philox_words(seed, 0, step, oracle.P_MASK, 0, 0, half, word=q) for q in range(4)])
+    w = philox_rows(seed, 0, step, oracle.P_MASK, 0, half).T
     slot = np.arange(n)
     mask = w[2 * (slot & 1), slot >> 1] < T
     removed = int(np.sum(active.astype(bool) & mask))
@@ -215,8 +271,8 @@ def c1_call_brute(active, fields, seed, step, T, k):
     choose = w[2 * (slot & 1) + 1, slot >> 1] < T
     chosen = np.flatnonzero(active.astype(bool) & choose)
     free = np.flatnonzero(active == 0)
-    d = oracle.c1_records(seed, 0, step, oracle.P_DELTA0, oracle.P_DELTA1, k, F)
-    rec = oracle.c1_records(seed, 0, step, oracle.P_NEWREC0, oracle.P_NEWREC1, k, F)
+    d = records_by_philox(seed, 0, step, oracle.P_DELTA0, oracle.P_DELTA1, k, F)
+    rec = records_by_philox(seed, 0, step, oracle.P_NEWREC0, oracle.P_NEWREC1, k, F)
     ru = min(k, chosen.size); ra = min(k, free.size)
     fields[:, chosen[:ru]] += d[:ru].T
     fields = ((fields + 2**31) % 2**32 - 2**31)

@@ -56,6 +56,58 @@ def test_static_resolve_matches_resolve_twice(lib, M, R, seed):
         assert torch.equal(f, f_ref)
 
 
+def test_static_resolve_edge_cases(lib):
+    """No claims; no per-claim flags wanted; claim arrays that start one element
+    past a 16-byte boundary (the flags then take the unaligned path)."""
+    abm = lib
+    rng = np.random.default_rng(5)
+    R = 1000
+    st = abm.stream_handle()
+    # M = 0: every resource reports no winner, whatever the array held before
+    w = torch.full((R,), 77, dtype=torch.int32, device="cuda")
+    abm.check(abm.lib().abm_resolve_static(None, None, 0, R, abm.ptr(w), None, st))
+    torch.cuda.synchronize()
+    assert bool((w == -1).all())
+    M = 50_001
+    res = torch.from_numpy(rng.integers(-2, R + 2, size=M + 1).astype(np.int32)).cuda()
+    prio = torch.from_numpy(rng.integers(0, 1 << 32, size=M + 1, dtype=np.uint64).astype(np.uint32).view(np.int32)).cuda()
+    for off in (0, 1):
+        r_, p_ = res[off:off + M], prio[off:off + M]
+        w_ref, f_ref, w, f = call_pair(abm, r_, p_, R)
+        assert torch.equal(w, w_ref) and torch.equal(f, f_ref)
+        # the same call without the per-claim flags
+        w2 = torch.full((R,), 5, dtype=torch.int32, device="cuda")
+        abm.check(abm.lib().abm_resolve_static(abm.ptr(r_), abm.ptr(p_), M, R, abm.ptr(w2), None, st))
+        torch.cuda.synchronize()
+        assert torch.equal(w2, w_ref)
+    # flags written from an odd address as well
+    fb = torch.zeros(M + 1, dtype=torch.uint8, device="cuda")
+    abm.check(abm.lib().abm_resolve_static(abm.ptr(res[1:]), abm.ptr(prio[1:]), M, R, abm.ptr(w2),
+                                           abm.ptr(fb[1:]), st))
+    torch.cuda.synchronize()
+    assert torch.equal(fb[1:], f_ref)
+
+
+def test_static_resolve_allocates_nothing(lib):
+    """Once a device has run the call, further calls leave the device's free
+    memory unchanged: the scratch table is the library's own fixed array."""
+    abm = lib
+    M, R = 1 << 20, 1 << 16
+    res = torch.from_numpy(workloads.zipf_claims(M, R, seed=9)).cuda()
+    prio = torch.from_numpy(np.random.default_rng(9).integers(0, 1 << 31, size=M).astype(np.int32)).cuda()
+    w = torch.empty(R, dtype=torch.int32, device="cuda")
+    f = torch.empty(M, dtype=torch.uint8, device="cuda")
+    st = abm.stream_handle()
+    abm.check(abm.lib().abm_resolve_static(abm.ptr(res), abm.ptr(prio), M, R, abm.ptr(w), abm.ptr(f), st))
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        abm.check(abm.lib().abm_resolve_static(abm.ptr(res), abm.ptr(prio), M, R, abm.ptr(w), abm.ptr(f), st))
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+
+
 def test_static_resolve_rejects_oversize(lib):
     abm = lib
     R = abm.RESOLVE_STATIC_MAX_R + 1
