@@ -392,6 +392,7 @@ def batched_leg(torch, engine, capacity, autotune, abm, hbm_peak, n_models=None,
     e1.synchronize()
     t_fixed = e0.elapsed_time(e1)
     want = b.digest().cpu().numpy()
+    out["_digest_fixed"] = want
     cnt = b.counters()
     b.check()
     info = b.info()
@@ -430,22 +431,34 @@ def batched_leg(torch, engine, capacity, autotune, abm, hbm_peak, n_models=None,
     out["tune_trials_learned_ms"] = trials(tl)
     res = capacity.run_learned(models, learned, fixed, steps, threads=tl["threads"], ctas_per_sm=tl["ctas_per_sm"])
     t_learned = res["ms_learned"] + res["ms_rerun"] + t_mlp
+    out["_digest_learned"] = res["digest"]
+    n_over = np.array([max(c["overflow"]) for c in res["counters"]])
     out["learned"] = {"ms": t_learned, "ms_run": res["ms_learned"], "ms_rerun": res["ms_rerun"], "ms_mlp": t_mlp,
                       "agent_steps_per_s": agents / (t_learned * 1e-3),
                       "speedup_vs_fixed": t_fixed / t_learned,
-                      "overflowed_models": len(res["overflowed"]), "unrecovered_overflows": 0,
+                      "overflowed_models": len(res["overflowed"]), "rerun_models": res["rerun"],
+                      # models whose reported result is still truncated after the rerun
+                      "unrecovered_overflows": int(res["unrecovered"]),
+                      "truncated_after_rerun": int(n_over.sum()),
                       "bit_exact_vs_fixed": bool(np.array_equal(res["digest"], want)),
                       "capacity_sum_fixed": int(fixed.sum()), "capacity_sum_learned": int(learned.sum()),
                       "peak_sum": int(hw.sum()),
                       "wasted_capacity": (int(learned.sum()) - int(hw.sum())) / int(hw.sum())}
-    # learned capacities (memory) with extent sweeps (work): both savings at once
+    # learned capacities (memory) with extent sweeps (work): compared with the
+    # extent-sweep fixed run, the fair plain baseline for it
     res = capacity.run_learned(models, learned, fixed, steps, sweep=abm.SWEEP_EXTENT, threads=tl["threads"],
                                ctas_per_sm=tl["ctas_per_sm"])
     t_le = res["ms_learned"] + res["ms_rerun"] + t_mlp
     out["learned_extent_sweep"] = {"ms": t_le, "ms_run": res["ms_learned"], "ms_rerun": res["ms_rerun"],
-                                   "agent_steps_per_s": agents / (t_le * 1e-3), "speedup_vs_fixed": t_fixed / t_le,
+                                   "agent_steps_per_s": agents / (t_le * 1e-3),
+                                   "speedup_vs_fixed_extent_sweep": t_ext / t_le,
+                                   "speedup_vs_fixed": t_fixed / t_le,
                                    "overflowed_models": len(res["overflowed"]),
+                                   "unrecovered_overflows": int(res["unrecovered"]),
                                    "bit_exact_vs_fixed": bool(np.array_equal(res["digest"], want))}
+    out["note"] = ("speedup_vs_fixed compares with the paper's static shapes (every slot swept every step); "
+                   "learned_extent_sweep.speedup_vs_fixed_extent_sweep compares two runs that both stop at the "
+                   "extent, where capacity only saves memory")
     return out
 
 
@@ -709,14 +722,16 @@ def lob_cpu_baseline(n_sample=4096, budget_s=15.0):
 
 
 def _oracle_model_run(args):
-    """One batched-workload model on the sequential oracle (process-pool worker)."""
+    """One batched-workload model on the sequential oracle (process-pool
+    worker): agent-steps, seconds, and the digest of its final state."""
     side, seed, model, params, cap, n0, steps = args
     import oracle
+    from oracle import digest
     w = oracle.World(side, seed, model, params, cap, n0)
     t0 = time.perf_counter()
     st = w.step(steps)
     dt = time.perf_counter() - t0
-    return sum(r["n_start"][0] + r["n_start"][1] for r in st), dt
+    return sum(r["n_start"][0] + r["n_start"][1] for r in st), dt, digest.state_digest(w)
 
 
 def batched_cpu_baseline(n_sample=48, sample_seed=7):
@@ -734,11 +749,12 @@ def batched_cpu_baseline(n_sample=48, sample_seed=7):
     with mp.get_context("spawn").Pool(cores) as pool:
         res = pool.map(_oracle_model_run, jobs, chunksize=1)
     wall = time.perf_counter() - t0
-    agents = sum(a for a, _ in res)
+    agents = sum(a for a, _, _ in res)
     return {"value": agents / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n_sample} random models (numpy seed {sample_seed}) of the 4096, all {B['steps']} steps, "
                       f"one model per core, {wall:.1f} s wall",
-            "cpu_seconds": sum(d for _, d in res)}
+            "cpu_seconds": sum(d for _, d, _ in res),
+            "_models": [int(i) for i in pick], "_digests": [int(d) for _, _, d in res]}
 
 
 def run_ours(args, rank, world, local):
@@ -774,49 +790,64 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
     clk = ClockSampler(local)
     clk.__enter__()
-    # one persistent launch for all K steps; CUDA events around it on the
-    # launching stream, block 0's global-timer laps between the grid barriers
-    phase = gw.step_profiled(K, stats)
-    torch.cuda.synchronize()
+    # the product call: one abm_step for all K steps (one cooperative launch on
+    # the persistent engine), CUDA events around it on the launching stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    gw.step(K, stats)
+    e1.record()
+    e1.synchronize()
     barrier(world)
     gw.check()
-    ms_total = phase[7]
+    ms_total = e0.elapsed_time(e1)
     st_rows = engine.decode_stats(stats[:K])
     agents = sum(r["n_start"][0] + r["n_start"][1] for r in st_rows)
     t_max = max_over_ranks(ms_total, world, device="cuda")
     total_agents = sum_over_ranks(agents, world, device="cuda")
     value = total_agents / (t_max * 1e-3)
+    persistent = tw["engine"] == abm.ENGINE_PERSISTENT
 
     # roofline of the (only) kernel of the timed region: algorithmic bytes of
     # every phase of every step over the launch's duration
     step_bytes = sum(kernel_bytes(k, r) for r in st_rows for k in range(6))
     achieved = step_bytes / (ms_total * 1e-3) / 1e9
-    roofline = {"kernel": "k_persistent (all phases of all timed steps, one cooperative launch)",
+    roofline = {"kernel": "k_persistent (all phases of all timed steps, one cooperative launch)" if persistent
+                else "six per-phase kernels per step",
                 "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "peak_kind": peak_kind,
-                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": persistent_traffic(K, W, tw["ctas_per_sm"])
-                if tw["engine"] == abm.ENGINE_PERSISTENT else None,
+                "unit": "GB/s", "frac": achieved / hbm_peak,
+                "traffic": persistent_traffic(K, W, tw["ctas_per_sm"]) if persistent else None,
                 "launch_ms": ms_total, "algorithmic_bytes_per_launch": step_bytes,
                 "frac_of_nominal_8tbs": achieved / NOMINAL_HBM_GBS,
                 "bytes_per_agent_step": {"algorithmic": step_bytes / max(agents, 1)},
-                "note": "latency-bound: dependent random cell accesses and 5 grid barriers per step"}
+                "note": "latency-bound: dependent random cell accesses and the grid barriers of each step"}
     if roofline["traffic"]:
         roofline["bytes_per_agent_step"]["dram"] = roofline["traffic"] / max(agents, 1)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": t_max / max(K, 1), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic (Philox-seeded initial state)",
-            "config": dict(config_block(), engine=("persistent" if tw["engine"] == abm.ENGINE_PERSISTENT
-                                                    else "kernels"), ctas_per_sm=tw["ctas_per_sm"],
-                           launch="default" if args.no_tune else "autotuned",
+            "config": dict(config_block(), engine=("persistent" if persistent else "kernels"),
+                           ctas_per_sm=tw["ctas_per_sm"], launch="default" if args.no_tune else "autotuned",
+                           timed_call="abm_step(K steps)",
                            tune_trials_ms=[[("persistent" if x["engine"] == abm.ENGINE_PERSISTENT else "kernels"),
                                             x["ctas_per_sm"], round(x["ms"], 3)] for x in tw.get("trials", [])]),
-            "roofline": roofline, "gpu_launches": 1 if tw["engine"] == abm.ENGINE_PERSISTENT else 6 * K,
-            "phases_us_per_step": {n: 1e3 * phase[i] / max(K, 1) for i, n in enumerate(
-                ("P1_prev_wolf_ranks_sheep_move", "P2_prev_wolf_births_sheep_eat_select", "P3_sheep_ranks_wolf_move",
-                 "P4_sheep_births", "P5_wolf_eat_select", "closing_wolf_ranks"))},
-            "end_counters": gw.counters()}
+            "gpu_launches": 1 if persistent else 6 * K,
+            "end_counters": gw.counters(), "roofline": roofline}
 
-    if rank == 0 and not args.no_extras:
+    extras = rank == 0 and not args.no_extras
+    if extras:
+        # where the time of a step goes: the same K steps again on a second world,
+        # through abm_step_profiled (block 0's global-timer laps between the grid
+        # barriers); not the timed call
+        pw = engine.World(c["side"], c["seed"], c["model"] + rank, c["params"], c["cap"], c["n0"])
+        pw.tune(tw["engine"], tw["ctas_per_sm"])
+        pw.step(W)
+        phase = pw.step_profiled(K)
+        line["phases_us_per_step"] = {n: 1e3 * phase[i] / max(K, 1) for i, n in enumerate(
+            ("P1_prev_wolf_ranks_sheep_move", "P2_prev_wolf_births_sheep_eat_select", "P3_sheep_ranks_wolf_move",
+             "P4_sheep_births", "P5_wolf_eat_select", "closing_wolf_ranks"))}
+        line["phases_us_per_step"]["same_trajectory"] = pw.counters() == gw.counters()
+        del pw
         # end to end through the public API: one abm_step per step, then the
         # step's statistics read back to pinned host memory
         ew = engine.World(c["side"], c["seed"], c["model"] + rank, c["params"], c["cap"], c["n0"])
@@ -866,20 +897,51 @@ def run_ours(args, rank, world, local):
         line["lob"] = lob_leg(torch, engine, hbm_peak)
     clk.__exit__(None, None, None)
     line["clocks"] = clk.summary()
-    if rank == 0 and not args.no_extras:
-        # the oracle on the machine's host cores, bounded sample
-        rate, n, dt = oracle_predation_rate(10**9, 0, budget_s=15.0)
+    if extras:
+        # the oracle on the machine's host cores, on the timed window's steps (bounded)
+        rate, n, dt = oracle_predation_rate(K, W, budget_s=20.0)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"first {n} steps of the large predation run "
-                                          f"({dt:.1f} s, sequential C oracle, 1 thread)",
+                                "sample": f"steps {W}..{W + n - 1} of the large predation run (the timed window"
+                                          f"{'' if n == K else ', cut at 20 s'}; {dt:.1f} s, sequential C oracle, "
+                                          f"1 thread)",
                                 "host_cores": os.cpu_count()}
+        bt = line["batched"]
         cb = batched_cpu_baseline()
-        line["batched"]["cpu_baseline"] = cb
+        picks, odig = cb.pop("_models"), cb.pop("_digests")
+        dfix, dlearn = bt.pop("_digest_fixed"), bt.pop("_digest_learned")
+        ok_fixed = [int(dfix[m]) & (2**64 - 1) == d for m, d in zip(picks, odig)]
+        ok_learned = [int(dlearn[m]) & (2**64 - 1) == d for m, d in zip(picks, odig)]
+        bt["oracle_subset"] = {"models": len(picks), "steps": workloads.BATCH["steps"],
+                               "fixed_bit_exact": sum(ok_fixed), "learned_bit_exact": sum(ok_learned),
+                               "how": "digest of each sampled model's final state: oracle vs GPU batch"}
+        bt["cpu_baseline"] = cb
+        cb["full_batch_s_estimate"] = bt["fixed"]["agent_steps_per_s"] * bt["fixed"]["ms"] * 1e-3 / cb["value"]
         line["lob"]["cpu_baseline"] = lob_cpu_baseline()
-        line["batched"]["cpu_baseline"]["full_batch_s_estimate"] = \
-            line["batched"]["fixed"]["agent_steps_per_s"] * line["batched"]["fixed"]["ms"] * 1e-3 / cb["value"]
+        line["summary"] = summary(line)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def summary(line: dict) -> dict:
+    """The three headline measurements in a few hundred bytes (printed last)."""
+    su, bt, lob = line["selective_update"], line["batched"], line["lob"]
+    r3 = lambda x: round(float(x), 3)  # noqa: E731
+    return {
+        "predation": {"agent_steps_per_s": r3(line["value"]), "us_per_step": r3(1e3 * line["ms_per_step"]),
+                      "hbm_frac": r3(line["roofline"]["frac"]), "cpu_oracle": r3(line["cpu_baseline"]["value"]),
+                      "e2e": r3(line["e2e"]["value"])},
+        "selective_update_hbm_frac": {p: r3(su[p]["frac"]) for p in ("0.001", "0.05", "0.5") if p in su},
+        "selective_update_gbs": {p: round(su[p]["gbs"]) for p in ("0.001", "0.05", "0.5") if p in su},
+        "batched_ms": {"fixed": r3(bt["fixed"]["ms"]), "fixed_extent": r3(bt["fixed_extent_sweep"]["ms"]),
+                       "learned": r3(bt["learned"]["ms"]), "learned_extent": r3(bt["learned_extent_sweep"]["ms"])},
+        "learned_speedup": {"vs_fixed": r3(bt["learned"]["speedup_vs_fixed"]),
+                            "extent_vs_fixed_extent": r3(bt["learned_extent_sweep"]["speedup_vs_fixed_extent_sweep"])},
+        "learned_unrecovered": bt["learned"]["unrecovered_overflows"],
+        "learned_bit_exact": bt["learned"]["bit_exact_vs_fixed"] and bt["learned_extent_sweep"]["bit_exact_vs_fixed"],
+        "batched_oracle_subset": [bt["oracle_subset"]["fixed_bit_exact"], bt["oracle_subset"]["learned_bit_exact"],
+                                  bt["oracle_subset"]["models"]],
+        "lob_hbm_frac": r3(lob["roofline"]["frac"]),
+    }
 
 
 def main():

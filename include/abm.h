@@ -400,6 +400,35 @@ abm_status abm_diag_barrier_timeout(int32_t spin_limit, void* stream);
 /* Synchronises `stream`; reports a recorded device error (e.g. a timed-out wait). */
 abm_status abm_world_check(abm_world* w, void* stream);
 
+/* Digest of the world's observable state (the checkpoint/digest call of the
+ * Section 2 API list): the wrapping 64-bit sum of one hash per live agent
+ * (species, slot, cell, energy, id, age), per cell (steps until its grass is
+ * edible) and per species counter (live agents, next id, high-water mark).
+ * Independent of the capacity and of the engine; a batch model run with the
+ * same configuration has the same digest (abm_batch_digest). out: device
+ * uint64 (required), written asynchronously on `stream`. */
+abm_status abm_digest(abm_world* w, uint64_t* out, void* stream);
+
+/* A species of the world as a Set (Section 2), so that the Set calls --
+ * abm_select, abm_select_permutation, abm_remove, abm_add,
+ * abm_update_distinct, abm_slab_read / write -- edit the world's agents
+ * between steps. The slab has F = 4 fields (0 cell, 1 energy, 2 id, 3 age)
+ * over the world's own arrays; its Bernoulli draws use the world's key. The
+ * first call for a species allocates the view's scratch (about 12 bytes a
+ * slot, kept until abm_destroy); every call copies the world's live count,
+ * next id and overflow flag into the view (asynchronously on `stream`). The
+ * view belongs to the world: abm_slab_destroy and abm_sort refuse it
+ * (ABM_ERR_STATE). Cells must stay in [0, side^2) and ids are the caller's
+ * business. After editing, call abm_world_slab_commit before the next step. */
+abm_status abm_world_slab(abm_world* w, int32_t species, abm_slab** out, void* stream);
+/* Fold a species' edits back into the world: live count recounted from the
+ * live flags, next id and overflow taken from the view, the high-water mark
+ * raised to the live count, the extent raised to the highest live slot + 1,
+ * and the per-cell claim tables emptied (they are rebuilt by the next step,
+ * as after abm_load). ABM_ERR_STATE if abm_world_slab was never called for
+ * the species. Asynchronous on `stream`. */
+abm_status abm_world_slab_commit(abm_world* w, int32_t species, void* stream);
+
 /* State export into device int32 buffers of the slab capacity (agents) or
  * side^2 (grass). which: 0 active, 1 cell, 2 energy, 3 id, 4 age. Grass:
  * 0 grown (0/1), 1 wait = steps until the cell is edible (0 when grown). */
@@ -473,8 +502,32 @@ abm_status abm_batch_overflowed(abm_batch* b, int32_t* list, int32_t* count, voi
  * observable states are equal (up to hash collisions). */
 abm_status abm_batch_digest(abm_batch* b, uint64_t* out, void* stream);
 abm_status abm_batch_check(abm_batch* b, void* stream);
-/* Total slots per species and total cells allocated by the batch. */
+/* Total slots per species and total cells allocated by the batch (its own
+ * slabs; a rerun's are not counted). */
 abm_status abm_batch_info(abm_batch* b, int64_t* slots_sheep, int64_t* slots_wolf, int64_t* cells);
+/* Current capacities of model m (host int32[2]): its own, or the fixed
+ * capacities of its rerun. */
+abm_status abm_batch_capacity(abm_batch* b, int32_t m, int32_t* cap);
+
+/* Recovery of a learned-capacity batch (Section 4: the maximum number of
+ * agents must be known in advance; a predicted capacity can be too small).
+ * Every model whose births were ever truncated by its slab (overflow flag,
+ * as listed by abm_batch_overflowed) is run again from its initial state, to
+ * the step the batch has reached, at the capacities cap_fixed[m] (host
+ * int32[n][2]; cap_fixed[m][s] >= n0[s], entries of models that did not
+ * overflow are not read beyond that check) with `sweep` and the batch's
+ * launch shape, in a second batch that `b` keeps. From then on
+ * abm_batch_counters_get, abm_batch_digest, abm_batch_read_agents,
+ * abm_batch_read_grass and abm_batch_capacity report the rerun for those
+ * models, abm_batch_run advances both, and abm_batch_check checks both;
+ * abm_batch_overflowed and abm_batch_info still describe b's own slabs.
+ * *out_rerun (host, nullable) = models rerun; *out_unrecovered (host,
+ * nullable) = rerun models whose births were truncated again (cap_fixed too
+ * small as well; their counters say so). Synchronises `stream` (the overflow
+ * flags are read on the host to size the rerun). ABM_ERR_STATE on a second
+ * call. */
+abm_status abm_batch_rerun_overflowed(abm_batch* b, const int32_t* cap_fixed, int32_t sweep, int32_t* out_rerun,
+                                      int32_t* out_unrecovered, void* stream);
 
 /* ========================================================================== */
 /* Learned capacity: an FP32 MLP predicting a high quantile of a model's peak */

@@ -104,6 +104,7 @@ def lib():
             L.orc_pred_grass.argtypes = [C.c_void_p, C.c_int]
             L.orc_pred_grass.restype = i32p
             L.orc_pred_counters.argtypes = [C.c_void_p, i32p]
+            L.orc_pred_set_counters.argtypes = [C.c_void_p, C.c_int] + [C.c_int32] * 4
             _lib = L
     return _lib
 
@@ -304,6 +305,14 @@ class World:
     def agents(self, species: int, which: str) -> np.ndarray:
         ptr = lib().orc_pred_agents(self._w, species, AGENT_FIELDS.index(which))
         return np.ctypeslib.as_array(ptr, shape=(self.cap[species],)).copy()
+
+    def agents_view(self, species: int, which: str) -> np.ndarray:
+        """Writable view of one of the species' arrays (for edits between steps)."""
+        ptr = lib().orc_pred_agents(self._w, species, AGENT_FIELDS.index(which))
+        return np.ctypeslib.as_array(ptr, shape=(self.cap[species],))
+
+    def set_counters(self, species: int, n_active: int, next_id: int, hw: int, overflow: int):
+        lib().orc_pred_set_counters(self._w, species, int(n_active), int(next_id), int(hw), int(overflow))
 
     def grass(self, which: str) -> np.ndarray:
         ptr = lib().orc_pred_grass(self._w, 0 if which == "grown" else 1)

@@ -444,6 +444,16 @@ void orc_pred_free(orc_world* w) {
 }
 
 int32_t* orc_pred_agents(orc_world* w, int species, int which) { return w->agent[species][which]; }
+
+/* Counters of a species whose arrays were edited between steps with the Set
+ * operations of Section 2 (select, remove, add, distinct update). */
+void orc_pred_set_counters(orc_world* w, int species, int32_t n_active, int32_t next_id, int32_t hw,
+                           int32_t overflow) {
+  w->n_active[species] = n_active;
+  w->next_id[species] = next_id;
+  w->hw[species] = hw;
+  w->overflow[species] = overflow;
+}
 int32_t* orc_pred_grass(orc_world* w, int which) { return which == 0 ? w->grown : w->countdown; }
 void orc_pred_counters(const orc_world* w, int32_t out[9]) {
   for (int s = 0; s < 2; s++) {

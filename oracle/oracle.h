@@ -107,5 +107,7 @@ int32_t* orc_pred_agents(orc_world* w, int species, int which);
 int32_t* orc_pred_grass(orc_world* w, int which);
 /* out: n_active[2], next_id[2], hw[2], overflow[2], step */
 void orc_pred_counters(const orc_world* w, int32_t out[9]);
+void orc_pred_set_counters(orc_world* w, int species, int32_t n_active, int32_t next_id, int32_t hw,
+                           int32_t overflow);
 
 #endif

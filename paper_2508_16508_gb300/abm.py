@@ -154,6 +154,11 @@ def _sig(L):
         "abm_mlp_get_params": ([vp, vp, i64, vp], st),
         "abm_mlp_get_grads": ([vp, vp, i64, vp], st),
         "abm_batch_digest": ([vp, vp, vp], st),
+        "abm_batch_capacity": ([vp, i32, vp], st),
+        "abm_batch_rerun_overflowed": ([vp, vp, i32, vp, vp, vp], st),
+        "abm_digest": ([vp, vp, vp], st),
+        "abm_world_slab": ([vp, i32, pp, vp], st),
+        "abm_world_slab_commit": ([vp, i32, vp], st),
         "abm_capacity_features": ([vp, i32, vp, vp, vp], st),
         "abm_capacity_from_prediction": ([vp, i32, C.c_float, i32, vp, vp, vp, vp], st),
         "abm_lob_match": ([i32, i32, vp, vp, vp, vp, vp, vp, vp, vp], st),

@@ -172,39 +172,27 @@ def peak_counts(models: list, horizon: int, sweep: int = abm.SWEEP_EXTENT, chunk
 
 def run_learned(models: list, learned_caps: np.ndarray, fixed_caps: np.ndarray, steps: int,
                 sweep: int = abm.SWEEP_CAPACITY, threads: int = 512, ctas_per_sm: int = 2) -> dict:
-    """Learned-capacity batch run with device-side overflow detection and a
-    fixed-capacity rerun of the overflowed models. Returns the per-model
-    digests and counters of the final result, and the GPU times."""
+    """Learned-capacity batch run: one launch at the learned capacities, then
+    abm_batch_rerun_overflowed reruns every model whose slab overflowed at its
+    fixed capacity and reports through the same batch. Returns the per-model
+    digests and counters of the final result, the rerun counts and the GPU
+    times (the rerun's includes setting up its batch)."""
     lm = [dict(m, cap=(int(c[0]), int(c[1]))) for m, c in zip(models, learned_caps)]
     b = engine.Batch(lm)
     b.tune(threads, ctas_per_sm)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
     e0.record()
     b.run(steps, sweep=sweep)
     e1.record()
     ov = b.overflowed()
-    e1.synchronize()
-    t_learned = e0.elapsed_time(e1)
+    n_rerun, n_unrec = b.rerun_overflowed(np.asarray(fixed_caps, dtype=np.int32), sweep=sweep)
+    e2.record()
+    e2.synchronize()
     dig = b.digest().cpu().numpy()
     cnt = b.counters()
     b.check()
+    out = {"digest": dig, "counters": cnt, "overflowed": ov, "rerun": n_rerun, "unrecovered": n_unrec,
+           "ms_learned": e0.elapsed_time(e1), "ms_rerun": e1.elapsed_time(e2) if n_rerun else 0.0}
     del b
-    t_rerun = 0.0
-    if ov:
-        rm = [dict(models[i], cap=(int(fixed_caps[i][0]), int(fixed_caps[i][1]))) for i in ov]
-        rb = engine.Batch(rm)
-        rb.tune(threads, ctas_per_sm)
-        e0.record()
-        rb.run(steps, sweep=sweep)
-        e1.record()
-        e1.synchronize()
-        t_rerun = e0.elapsed_time(e1)
-        rd = rb.digest().cpu().numpy()
-        rc = rb.counters()
-        rb.check()
-        for j, i in enumerate(ov):
-            dig[i] = rd[j]
-            cnt[i] = rc[j]
-        del rb
     torch.cuda.empty_cache()
-    return {"digest": dig, "counters": cnt, "overflowed": ov, "ms_learned": t_learned, "ms_rerun": t_rerun}
+    return out

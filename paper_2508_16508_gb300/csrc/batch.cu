@@ -467,16 +467,7 @@ __global__ void k_batch_overflowed(BatchDev b, int32_t* list, int32_t* count) {
   if (threadIdx.x == 0) *count = n;
 }
 
-// splitmix64 finaliser (Steele, Lea, Flood, "Fast splittable pseudorandom
-// number generators", OOPSLA 2014)
-__device__ __forceinline__ u64 mix64(u64 z) {
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-
-// order-independent digest of one model's observable state: live agents
-// (species, slot, cell, energy, id, age), grass (grown, wait) and counters
+// order-independent digest of one model's observable state (digest_* terms)
 __global__ void k_batch_digest(BatchDev b, u64* out) {
   __shared__ u64 s[32];
   const int mi = blockIdx.x;
@@ -486,30 +477,17 @@ __global__ void k_batch_digest(BatchDev b, u64* out) {
   for (int sp = 0; sp < 2; ++sp) {
     for (int i = threadIdx.x; i < k.extent[sp]; i += blockDim.x) {
       if (!b.active[sp][m.oa[sp] + i]) continue;
-      const int4 a = b.agent[sp][m.oa[sp] + i];
-      u64 z = mix64(((u64)sp << 40) ^ (u64)(u32)i);
-      z = mix64(z ^ (((u64)(u32)a.x << 32) | (u32)a.y));
-      z = mix64(z ^ (((u64)(u32)a.z << 32) | (u32)a.w));
-      h += z;
+      h += digest_agent(sp, i, b.agent[sp][m.oa[sp] + i]);
     }
   }
-  for (int c = threadIdx.x; c < m.ncells; c += blockDim.x) {
-    const int r = b.regrow[m.oc + c];
-    const u32 wait = r <= k.step ? 0u : (u32)(r - k.step);
-    h += mix64((2ull << 40) ^ ((u64)(u32)c << 8) ^ ((u64)wait << 40));
-  }
+  for (int c = threadIdx.x; c < m.ncells; c += blockDim.x) h += digest_cell(c, b.regrow[m.oc + c], k.step);
   for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xFFFFFFFFu, h, o);
   if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = h;
   __syncthreads();
   if (threadIdx.x == 0) {
     u64 t = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s[w];
-    for (int sp = 0; sp < 2; ++sp) {
-      t += mix64(0xC0FFEEull + sp * 7 + ((u64)(u32)k.n_active[sp] << 20));
-      t += mix64(0xBADull + sp * 11 + ((u64)(u32)k.next_id[sp] << 20));
-      t += mix64(0xF00Dull + sp * 13 + ((u64)(u32)k.hw[sp] << 20));
-    }
-    out[mi] = t;
+    out[mi] = t + digest_counters(k.n_active, k.next_id, k.hw);
   }
 }
 
@@ -524,7 +502,17 @@ struct abm_batch {
   std::vector<BModel> models;
   long long slots[2], cells;
   int threads, ctas_per_sm, steps_per_launch;
+  // fixed-capacity rerun of the models whose slabs overflowed (abm_batch_rerun_overflowed)
+  abm_batch* rerun;
+  std::vector<int> rerun_of;  // per model: its index in `rerun`, or -1
+  int32_t* rerun_idx;         // device [rerun->n]: model index in this batch of rerun model j
+  u64* rerun_dig;             // device [rerun->n]: digests of the rerun models
 };
+
+// digest j of the rerun batch -> entry idx[j] of this batch's digests
+__global__ void k_scatter_u64(const u64* src, const int32_t* idx, int n, u64* dst) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) dst[idx[j]] = src[j];
+}
 
 static void batch_free(abm_batch* b) {
   for (int s = 0; s < 2; ++s) {
@@ -542,6 +530,9 @@ static void batch_free(abm_batch* b) {
   cudaFree((void*)b->d.order);
   cudaFree(b->d.ctrl);
   cudaFree(b->d.err);
+  if (b->rerun) batch_free(b->rerun);
+  cudaFree(b->rerun_idx);
+  cudaFree(b->rerun_dig);
   delete b;
 }
 
@@ -668,6 +659,8 @@ extern "C" abm_status abm_batch_run(abm_batch* b, int32_t nsteps, int32_t sweep,
     ABM_LAUNCH_CHECK();
     done += s;
   }
+  // rerun models continue at their fixed capacities
+  if (b->rerun) return abm_batch_run(b->rerun, nsteps, sweep, stream);
   return ABM_OK;
 }
 
@@ -690,6 +683,13 @@ extern "C" abm_status abm_batch_counters_get(abm_batch* b, abm_batch_counters* o
     o.reserved = 0;
     o.agent_steps = h[i].agent_steps;
   }
+  if (b->rerun) {
+    std::vector<abm_batch_counters> r((size_t)b->rerun->d.nmodels);
+    const abm_status e = abm_batch_counters_get(b->rerun, r.data(), stream);
+    if (e != ABM_OK) return e;
+    for (size_t i = 0; i < h.size(); ++i)
+      if (b->rerun_of[i] >= 0) out[i] = r[(size_t)b->rerun_of[i]];
+  }
   return ABM_OK;
 }
 
@@ -697,6 +697,8 @@ extern "C" abm_status abm_batch_read_agents(abm_batch* b, int32_t m, int32_t spe
                                             void* stream) {
   if (!b || !dst || m < 0 || m >= b->d.nmodels || species < 0 || species > 1 || which < 0 || which > 4)
     return ABM_ERR_ARG;
+  if (b->rerun && b->rerun_of[(size_t)m] >= 0)
+    return abm_batch_read_agents(b->rerun, b->rerun_of[(size_t)m], species, which, dst, stream);
   const BModel& mm = b->models[(size_t)m];
   cudaStream_t st = (cudaStream_t)stream;
   const size_t n = (size_t)mm.cap[species];
@@ -713,6 +715,8 @@ extern "C" abm_status abm_batch_read_agents(abm_batch* b, int32_t m, int32_t spe
 
 extern "C" abm_status abm_batch_read_grass(abm_batch* b, int32_t m, int32_t which, int32_t* dst, void* stream) {
   if (!b || !dst || m < 0 || m >= b->d.nmodels || which < 0 || which > 1) return ABM_ERR_ARG;
+  if (b->rerun && b->rerun_of[(size_t)m] >= 0)
+    return abm_batch_read_grass(b->rerun, b->rerun_of[(size_t)m], which, dst, stream);
   k_batch_grass<<<std::max(1, std::min(num_sms() * 4, (b->models[(size_t)m].ncells + 255) / 256)), 256, 0,
                   (cudaStream_t)stream>>>(b->d, m, which, dst);
   ABM_LAUNCH_CHECK();
@@ -730,6 +734,14 @@ extern "C" abm_status abm_batch_digest(abm_batch* b, uint64_t* out, void* stream
   if (!b || !out) return ABM_ERR_ARG;
   k_batch_digest<<<b->d.nmodels, 256, 0, (cudaStream_t)stream>>>(b->d, (u64*)out);
   ABM_LAUNCH_CHECK();
+  if (b->rerun) {
+    const int nr = b->rerun->d.nmodels;
+    k_batch_digest<<<nr, 256, 0, (cudaStream_t)stream>>>(b->rerun->d, b->rerun_dig);
+    ABM_LAUNCH_CHECK();
+    k_scatter_u64<<<std::max(1, std::min((nr + 255) / 256, num_sms() * 4)), 256, 0, (cudaStream_t)stream>>>(
+        b->rerun_dig, b->rerun_idx, nr, (u64*)out);
+    ABM_LAUNCH_CHECK();
+  }
   return ABM_OK;
 }
 
@@ -738,7 +750,96 @@ extern "C" abm_status abm_batch_check(abm_batch* b, void* stream) {
   ABM_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
   int err = 0;
   ABM_CUDA_TRY(cudaMemcpy(&err, b->d.err, sizeof(int), cudaMemcpyDeviceToHost));
-  return err ? ABM_ERR_DEVICE_TIMEOUT : ABM_OK;
+  if (err) return ABM_ERR_DEVICE_TIMEOUT;
+  return b->rerun ? abm_batch_check(b->rerun, stream) : ABM_OK;
+}
+
+extern "C" abm_status abm_batch_capacity(abm_batch* b, int32_t m, int32_t* cap) {
+  if (!b || !cap || m < 0 || m >= b->d.nmodels) return ABM_ERR_ARG;
+  if (b->rerun && b->rerun_of[(size_t)m] >= 0) return abm_batch_capacity(b->rerun, b->rerun_of[(size_t)m], cap);
+  cap[0] = b->models[(size_t)m].cap[0];
+  cap[1] = b->models[(size_t)m].cap[1];
+  return ABM_OK;
+}
+
+// The learned-capacity recovery path: the models whose births were truncated
+// are run again from their initial state, at their fixed capacities, in a
+// second batch that this one keeps and reports through.
+extern "C" abm_status abm_batch_rerun_overflowed(abm_batch* b, const int32_t* cap_fixed, int32_t sweep,
+                                                 int32_t* out_rerun, int32_t* out_unrecovered, void* stream) {
+  if (!b || !cap_fixed || (sweep != ABM_SWEEP_CAPACITY && sweep != ABM_SWEEP_EXTENT)) return ABM_ERR_ARG;
+  if (b->rerun) return ABM_ERR_STATE;
+  const int n = b->d.nmodels;
+  for (int i = 0; i < n; ++i)
+    if (cap_fixed[2 * i] < b->models[(size_t)i].n0[0] || cap_fixed[2 * i + 1] < b->models[(size_t)i].n0[1] ||
+        cap_fixed[2 * i] > (1 << 28) - 1 || cap_fixed[2 * i + 1] > (1 << 28) - 1)
+      return ABM_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  // the overflow flags and the steps run so far, read on the host to size the rerun
+  std::vector<BCtr> h((size_t)n);
+  ABM_CUDA_TRY(cudaMemcpyAsync(h.data(), b->d.ctr, sizeof(BCtr) * (size_t)n, cudaMemcpyDeviceToHost, st));
+  ABM_CUDA_TRY(cudaStreamSynchronize(st));
+  std::vector<abm_batch_model> rm;
+  std::vector<int32_t> idx;
+  int steps = -1;
+  for (int i = 0; i < n; ++i) {
+    if (!(h[(size_t)i].overflow[0] | h[(size_t)i].overflow[1])) continue;
+    if (steps >= 0 && h[(size_t)i].step != steps) return ABM_ERR_STATE;  // models are always advanced together
+    steps = h[(size_t)i].step;
+    const BModel& m = b->models[(size_t)i];
+    abm_batch_model x;
+    std::memset(&x, 0, sizeof(x));
+    x.side = m.side;
+    x.seed = m.seed;
+    x.model = m.model;
+    std::memcpy(x.params, m.prm, sizeof(x.params));
+    for (int s = 0; s < 2; ++s) {
+      x.cap[s] = cap_fixed[2 * i + s];
+      x.n0[s] = m.n0[s];
+    }
+    rm.push_back(x);
+    idx.push_back(i);
+  }
+  if (out_rerun) *out_rerun = (int32_t)rm.size();
+  if (out_unrecovered) *out_unrecovered = 0;
+  if (rm.empty()) return ABM_OK;
+  abm_batch* r = nullptr;
+  abm_status e = abm_batch_create(rm.data(), (int32_t)rm.size(), stream, &r);
+  if (e != ABM_OK) return e;
+  r->threads = b->threads;
+  r->ctas_per_sm = b->ctas_per_sm;
+  r->steps_per_launch = b->steps_per_launch;
+  e = abm_batch_run(r, steps, sweep, stream);
+  const int nr = (int)rm.size();
+  if (e == ABM_OK && (cudaMalloc(&b->rerun_idx, sizeof(int32_t) * (size_t)nr) != cudaSuccess ||
+                      cudaMalloc(&b->rerun_dig, sizeof(u64) * (size_t)nr) != cudaSuccess)) {
+    cudaGetLastError();
+    e = ABM_ERR_OOM;
+  }
+  if (e == ABM_OK &&
+      cudaMemcpyAsync(b->rerun_idx, idx.data(), sizeof(int32_t) * (size_t)nr, cudaMemcpyHostToDevice, st) !=
+          cudaSuccess)
+    e = ABM_ERR_CUDA;
+  std::vector<BCtr> hr((size_t)nr);
+  if (e == ABM_OK &&
+      (cudaMemcpyAsync(hr.data(), r->d.ctr, sizeof(BCtr) * (size_t)nr, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+       cudaStreamSynchronize(st) != cudaSuccess))
+    e = ABM_ERR_CUDA;
+  if (e != ABM_OK) {
+    batch_free(r);
+    cudaFree(b->rerun_idx);
+    cudaFree(b->rerun_dig);
+    b->rerun_idx = nullptr;
+    b->rerun_dig = nullptr;
+    return e;
+  }
+  b->rerun = r;
+  b->rerun_of.assign((size_t)n, -1);
+  for (int j = 0; j < nr; ++j) b->rerun_of[(size_t)idx[(size_t)j]] = j;
+  int unrec = 0;
+  for (int j = 0; j < nr; ++j) unrec += (hr[(size_t)j].overflow[0] | hr[(size_t)j].overflow[1]) != 0;
+  if (out_unrecovered) *out_unrecovered = unrec;
+  return ABM_OK;
 }
 
 extern "C" abm_status abm_batch_info(abm_batch* b, int64_t* slots_sheep, int64_t* slots_wolf, int64_t* cells) {

@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "pred_world.cuh"
+#include "slab.cuh"
 
 namespace abm {
 
@@ -274,6 +275,72 @@ __global__ void k_read_grass(WorldDev w, int which, int32_t* dst) {
   }
 }
 
+// digest of the whole world (digest_* terms): per-CTA sums added atomically
+// into *out (zeroed by the caller), the counters' term by CTA 0
+__global__ void k_world_digest(WorldDev w, u64* out) {
+  __shared__ u64 s[kPredThreads / 32];
+  const WorldCtr* c = w.ctr;
+  const int step = c->step;
+  u64 h = 0;
+  const int stride = gridDim.x * blockDim.x;
+  for (int sp = 0; sp < 2; ++sp) {
+    const int ext = c->extent[sp];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ext; i += stride)
+      if (w.sp[sp].active[i]) h += digest_agent(sp, i, w.sp[sp].agent[i]);
+  }
+  for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < w.ncells; cell += stride)
+    h += digest_cell(cell, w.regrow[cell], step);
+  for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xFFFFFFFFu, h, o);
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = h;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    u64 t = 0;
+    for (int k = 0; k < kPredThreads / 32; ++k) t += s[k];
+    if (blockIdx.x == 0) {
+      const int na[2] = {c->n_active[0], c->n_active[1]}, ni[2] = {c->next_id[0], c->next_id[1]};
+      const int hw[2] = {c->hw[0], c->hw[1]};
+      t += digest_counters(na, ni, hw);
+    }
+    atomicAdd(reinterpret_cast<unsigned long long*>(out), (unsigned long long)t);
+  }
+}
+
+// a species' slab view takes the world's live count, next id and overflow flag
+__global__ void k_view_open(const WorldCtr* c, int sp, int32_t* counters) {
+  counters[0] = c->n_active[sp];
+  counters[1] = c->next_id[sp];
+  counters[2] = c->overflow[sp];
+  counters[3] = 0;
+}
+
+// live slots and the highest live slot + 1 of a species, into scan[0], scan[1] (zeroed)
+__global__ void k_view_scan(const int32_t* active, int cap, int* scan) {
+  int n = 0, top = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += gridDim.x * blockDim.x)
+    if (active[i]) {
+      ++n;
+      top = i + 1;
+    }
+  for (int o = 16; o > 0; o >>= 1) {
+    n += __shfl_xor_sync(0xFFFFFFFFu, n, o);
+    top = max(top, __shfl_xor_sync(0xFFFFFFFFu, top, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (n) atomicAdd(&scan[0], n);
+    if (top) atomicMax(&scan[1], top);
+  }
+}
+
+// fold an edited species back into the world's counters
+__global__ void k_view_commit(WorldCtr* c, int sp, const int32_t* counters, const int* scan) {
+  const int n = scan[0];
+  c->n_active[sp] = n;
+  c->next_id[sp] = counters[1];
+  if (counters[2]) c->overflow[sp] = 1;
+  if (n > c->hw[sp]) c->hw[sp] = n;
+  if (scan[1] > c->extent[sp]) c->extent[sp] = scan[1];
+}
+
 }  // namespace abm
 
 // ============================================================================
@@ -292,6 +359,7 @@ struct abm_world {
   cudaGraphExec_t gexec;
   int g_nsteps;
   abm_step_stats* g_stats;
+  abm_slab* view[2];  // per species, made by the first abm_world_slab call
 };
 
 static void world_free(abm_world* w) {
@@ -322,6 +390,8 @@ static void world_free(abm_world* w) {
   cudaFree(w->d.wkey);
   cudaFree(w->d.wnext);
   if (w->gexec) cudaGraphExecDestroy(w->gexec);
+  slab_free_view(w->view[0]);
+  slab_free_view(w->view[1]);
   delete w;
 }
 
@@ -686,5 +756,46 @@ extern "C" abm_status abm_load(abm_world* w, const void* buf, size_t bytes, void
   w->bar_next = 0;
   ABM_CUDA_TRY(cudaStreamSynchronize(st));
   w->steps_host = h.step;
+  return ABM_OK;
+}
+
+extern "C" abm_status abm_digest(abm_world* w, uint64_t* out, void* stream) {
+  if (!w || !out) return ABM_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  ABM_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(uint64_t), st));
+  k_world_digest<<<num_sms() * 4, kPredThreads, 0, st>>>(w->d, (u64*)out);
+  ABM_LAUNCH_CHECK();
+  return ABM_OK;
+}
+
+extern "C" abm_status abm_world_slab(abm_world* w, int32_t species, abm_slab** out, void* stream) {
+  if (!w || !out || species < 0 || species > 1) return ABM_ERR_ARG;
+  if (!w->view[species]) {
+    abm_status e = slab_create_view(w->d.sp[species].cap, w->d.seed, w->d.model, w->d.sp[species].active,
+                                    reinterpret_cast<int32_t*>(w->d.sp[species].agent), &w->view[species]);
+    if (e != ABM_OK) return e;
+  }
+  k_view_open<<<1, 1, 0, (cudaStream_t)stream>>>(w->d.ctr, species, w->view[species]->d.counters);
+  ABM_LAUNCH_CHECK();
+  *out = w->view[species];
+  return ABM_OK;
+}
+
+extern "C" abm_status abm_world_slab_commit(abm_world* w, int32_t species, void* stream) {
+  if (!w || species < 0 || species > 1) return ABM_ERR_ARG;
+  abm_slab* v = w->view[species];
+  if (!v) return ABM_ERR_STATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  int* scan = v->d.meta;  // free between the view's calls
+  ABM_CUDA_TRY(cudaMemsetAsync(scan, 0, sizeof(int) * 2, st));
+  const int cap = w->d.sp[species].cap;
+  k_view_scan<<<std::max(1, std::min((cap + 255) / 256, num_sms() * 4)), 256, 0, st>>>(w->d.sp[species].active, cap,
+                                                                                       scan);
+  ABM_LAUNCH_CHECK();
+  k_view_commit<<<1, 1, 0, st>>>(w->d.ctr, species, v->d.counters, scan);
+  ABM_LAUNCH_CHECK();
+  // the per-cell claim tables are rebuilt by the next step, as after abm_load
+  k_reset_tables<<<num_sms() * 4, 256, 0, st>>>(w->d);
+  ABM_LAUNCH_CHECK();
   return ABM_OK;
 }

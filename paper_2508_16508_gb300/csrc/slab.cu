@@ -543,10 +543,11 @@ extern "C" const char* abm_strerror(abm_status st) {
 
 extern "C" int32_t abm_version(void) { return 100; }
 
-extern "C" abm_status abm_slab_destroy(abm_slab* s) {
-  if (!s) return ABM_ERR_ARG;
-  cudaFree(s->d.active);
-  cudaFree(s->d.fields);
+static void slab_free(abm_slab* s) {
+  if (!s->view) {
+    cudaFree(s->d.active);
+    cudaFree(s->d.fields);
+  }
   cudaFree(s->d.counters);
   cudaFree(s->d.rec_idx);
   cudaFree(s->d.err);
@@ -562,15 +563,23 @@ extern "C" abm_status abm_slab_destroy(abm_slab* s) {
   cudaFree(s->ctrl);
   sort_scratch_free(s->sort);
   delete s;
+}
+
+extern "C" abm_status abm_slab_destroy(abm_slab* s) {
+  if (!s) return ABM_ERR_ARG;
+  if (s->view) return ABM_ERR_STATE;  // a world's view lives as long as the world
+  slab_free(s);
   return ABM_OK;
 }
 
-extern "C" abm_status abm_slab_create(int32_t capacity, int32_t n_fields, uint32_t seed,
-                                      uint32_t model, int32_t init, void* stream, abm_slab** out) {
-  if (!out || capacity < 1 || capacity > (1 << 28) - 1 || n_fields < 1 || n_fields > kMaxFields ||
-      (init != ABM_INIT_EMPTY && init != ABM_INIT_HALF_LIVE))
-    return ABM_ERR_ARG;
-  cudaStream_t st = (cudaStream_t)stream;
+void abm::slab_free_view(abm_slab* s) {
+  if (s) slab_free(s);
+}
+
+// host part of slab creation: the struct, its scratch and counters, and the
+// live flags and fields unless they are borrowed (active != nullptr)
+static abm_status slab_alloc(int capacity, int n_fields, u32 seed, u32 model, int32_t* active, int32_t* fields,
+                             abm_slab** out) {
   abm_slab* s = new (std::nothrow) abm_slab();
   if (!s) return ABM_ERR_OOM;
   std::memset(s, 0, sizeof(*s));
@@ -583,9 +592,16 @@ extern "C" abm_status abm_slab_create(int32_t capacity, int32_t n_fields, uint32
   s->max_ctas = num_sms() * 16;
   s->fused_threads = 256;
   s->fused_ctas_per_sm = 8;
-  bool ok = cudaMalloc(&s->d.active, sizeof(int32_t) * (size_t)s->n_pad) == cudaSuccess &&
-            cudaMalloc(&s->d.fields, sizeof(int32_t) * (size_t)s->n_pad * s->d.Fp) == cudaSuccess &&
-            cudaMalloc(&s->d.counters, sizeof(int32_t) * 4) == cudaSuccess &&
+  s->view = active != nullptr;
+  bool ok = true;
+  if (s->view) {
+    s->d.active = active;
+    s->d.fields = fields;
+  } else {
+    ok = cudaMalloc(&s->d.active, sizeof(int32_t) * (size_t)s->n_pad) == cudaSuccess &&
+         cudaMalloc(&s->d.fields, sizeof(int32_t) * (size_t)s->n_pad * s->d.Fp) == cudaSuccess;
+  }
+  ok = ok && cudaMalloc(&s->d.counters, sizeof(int32_t) * 4) == cudaSuccess &&
             cudaMalloc(&s->d.rec_idx, sizeof(int32_t) * (size_t)capacity) == cudaSuccess &&
             cudaMalloc(&s->d.err, sizeof(int)) == cudaSuccess &&
             cudaMalloc(&s->planes, sizeof(u32) * 2 * (size_t)(s->n_pad / 32)) == cudaSuccess &&
@@ -600,19 +616,47 @@ extern "C" abm_status abm_slab_create(int32_t capacity, int32_t n_fields, uint32
             cudaMalloc(&s->ctrl, sizeof(u32) * 8) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
-    abm_slab_destroy(s);
+    slab_free(s);
     return ABM_ERR_OOM;
   }
+  *out = s;
+  return ABM_OK;
+}
+
+abm_status abm::slab_create_view(int cap, u32 seed, u32 model, int32_t* active, int32_t* fields, abm_slab** out) {
+  if (!active || !fields || !out || cap < 1 || cap > (1 << 28) - 1) return ABM_ERR_ARG;
+  abm_slab* s = nullptr;
+  const abm_status e = slab_alloc(cap, 4, seed, model, active, fields, &s);
+  if (e != ABM_OK) return e;
+  // zeroed synchronously: a view is made once, outside any stream order
+  if (cudaMemset(s->d.counters, 0, sizeof(int32_t) * 4) != cudaSuccess ||
+      cudaMemset(s->d.err, 0, sizeof(int)) != cudaSuccess || cudaMemset(s->ctrl, 0, sizeof(u32) * 8) != cudaSuccess) {
+    slab_free(s);
+    return ABM_ERR_CUDA;
+  }
+  *out = s;
+  return ABM_OK;
+}
+
+extern "C" abm_status abm_slab_create(int32_t capacity, int32_t n_fields, uint32_t seed,
+                                      uint32_t model, int32_t init, void* stream, abm_slab** out) {
+  if (!out || capacity < 1 || capacity > (1 << 28) - 1 || n_fields < 1 || n_fields > kMaxFields ||
+      (init != ABM_INIT_EMPTY && init != ABM_INIT_HALF_LIVE))
+    return ABM_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  abm_slab* s = nullptr;
+  const abm_status e = slab_alloc(capacity, n_fields, seed, model, nullptr, nullptr, &s);
+  if (e != ABM_OK) return e;
   if (cudaMemsetAsync(s->d.counters, 0, sizeof(int32_t) * 4, st) != cudaSuccess ||
       cudaMemsetAsync(s->d.err, 0, sizeof(int), st) != cudaSuccess ||
       cudaMemsetAsync(s->ctrl, 0, sizeof(u32) * 8, st) != cudaSuccess) {
-    abm_slab_destroy(s);
+    slab_free(s);
     return ABM_ERR_CUDA;
   }
   k_slab_init<<<num_sms() * 4, 256, 0, st>>>(s->d, init, s->n_pad);
   k_count_live<<<num_sms() * 4, 256, 0, st>>>(s->d);
   if (cudaGetLastError() != cudaSuccess) {
-    abm_slab_destroy(s);
+    slab_free(s);
     return ABM_ERR_CUDA;
   }
   *out = s;

@@ -39,4 +39,13 @@ struct abm_slab {
   // shape of the fused selective-update pass (abm_slab_tune)
   int fused_threads, fused_ctas_per_sm;
   abm::SortScratch* sort;  // buffers of abm_sort, allocated by its first call
+  int view;                // 1: active / fields belong to a predation world (abm_world_slab)
 };
+
+namespace abm {
+// A slab over arrays owned by someone else (a world's species): own scratch
+// and counters, borrowed live flags and fields (F = Fp = 4). Freed by
+// slab_free_view, never by abm_slab_destroy.
+abm_status slab_create_view(int cap, u32 seed, u32 model, int32_t* active, int32_t* fields, abm_slab** out);
+void slab_free_view(abm_slab* s);
+}  // namespace abm

@@ -257,6 +257,7 @@ using namespace abm;
 
 extern "C" abm_status abm_sort(abm_slab* s, int32_t field, int32_t* out_perm, void* stream) {
   if (!s || field < 0 || field >= s->d.F) return ABM_ERR_ARG;
+  if (s->view) return ABM_ERR_STATE;  // the sort swaps the slab's arrays, which a world's view does not own
   SortScratch* p = nullptr;
   abm_status e = sort_scratch(s, &p);
   if (e != ABM_OK) return e;

@@ -127,6 +127,23 @@ class Slab:
         return out[:k]
 
 
+class WorldSlab(Slab):
+    """A species of a World as a Set (abm_world_slab): F = 4 fields (cell,
+    energy, id, age) over the world's own arrays. Owned by the world; call
+    World.slab_commit after editing, before the next step."""
+
+    def __init__(self, world, species: int, stream=None):
+        h = C.c_void_p()
+        call("abm_world_slab", world.h, int(species), C.byref(h), _stream(stream))
+        self.h = h
+        self.world = world  # the view lives as long as the world
+        self.capacity, self.F = world.cap[species], 4
+        self._i32 = dict(dtype=torch.int32, device=world.dev)
+
+    def close(self):
+        self.h = C.c_void_p()  # freed with the world
+
+
 class Resolver:
     """Per-resource conflict resolution with a reusable scratch table."""
 
@@ -198,6 +215,18 @@ class World:
 
     def check(self, stream=None):
         call("abm_world_check", self.h, _stream(stream))
+
+    def digest(self, stream=None) -> int:
+        out = torch.zeros(1, dtype=torch.int64, device=self.dev)
+        call("abm_digest", self.h, ptr(out), _stream(stream))
+        return int(out.item())
+
+    def slab(self, species: int, stream=None) -> "WorldSlab":
+        """The species as a Set for edits between steps (commit with slab_commit)."""
+        return WorldSlab(self, species, stream)
+
+    def slab_commit(self, species: int, stream=None):
+        call("abm_world_slab_commit", self.h, int(species), _stream(stream))
 
     def agents(self, species: int, which: str, stream=None) -> torch.Tensor:
         out = torch.empty(self.cap[species], dtype=torch.int32, device=self.dev)
@@ -348,8 +377,24 @@ class Batch:
                         "agent_steps": c.agent_steps})
         return out
 
+    def capacity(self, m: int) -> list:
+        """Current capacities of model m (its rerun's after rerun_overflowed)."""
+        cap = (C.c_int32 * 2)()
+        call("abm_batch_capacity", self.h, int(m), cap)
+        return [cap[0], cap[1]]
+
+    def rerun_overflowed(self, cap_fixed, sweep: int = abm.SWEEP_CAPACITY, stream=None) -> tuple:
+        """Rerun the overflowed models at cap_fixed[m] (int32 [n][2]); returns
+        (models rerun, rerun models that overflowed again)."""
+        import numpy as np
+        cf = np.ascontiguousarray(np.asarray(cap_fixed, dtype=np.int32).reshape(self.n, 2))
+        nr, nu = C.c_int32(), C.c_int32()
+        call("abm_batch_rerun_overflowed", self.h, cf.ctypes.data_as(C.c_void_p), sweep, C.byref(nr), C.byref(nu),
+             _stream(stream))
+        return nr.value, nu.value
+
     def agents(self, m: int, species: int, which: str, stream=None) -> torch.Tensor:
-        out = torch.empty(self.caps[m][species], dtype=torch.int32, device=self.dev)
+        out = torch.empty(self.capacity(m)[species], dtype=torch.int32, device=self.dev)
         call("abm_batch_read_agents", self.h, m, species, AGENT_FIELDS.index(which), ptr(out),
              _stream(stream))
         return out

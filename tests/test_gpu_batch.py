@@ -116,3 +116,32 @@ def test_overflow_list(eng):
             want.append(m)
         compare_model(b, m, ow, "overflow")
     assert ov == want and len(want) > 0
+
+
+@pytest.mark.parametrize("sweep", [0, 1])
+def test_sampler_models_full_horizon(eng, sweep):
+    """The batched workload at its own horizon: 10 models of its sampler with
+    sides spread over [16, 256] (fixed capacity 4 side^2) run all 500 steps in
+    one launch, against the oracle model by model (whole state and counters).
+    In this workload the wolves boom and eat the sheep; on the oracle these
+    models lose their sheep by step 8-23 and their wolves by step 53-137, so
+    the horizon covers growth, collapse and the empty slabs after it."""
+    B = workloads.BATCH
+    tab = workloads.sample_models(B["n_models"], B["sampler_seed"])
+    caps = workloads.fixed_caps(tab["side"])
+    order = np.argsort(tab["side"], kind="stable")
+    pick = [int(order[int(q)]) for q in np.linspace(0, len(order) - 1, 10)]
+    models = [dict(side=int(tab["side"][i]), seed=B["philox_seed"], model=i, params=tab["params"][i],
+                   cap=caps[i], n0=tab["n0"][i]) for i in pick]
+    b = eng.Batch(models)
+    b.run(B["steps"], sweep=sweep)
+    cnt = b.counters()
+    b.check()
+    for m, md in enumerate(models):
+        ow = oracle.World(md["side"], md["seed"], md["model"], md["params"], md["cap"], md["n0"])
+        agents = sum(st["n_start"][0] + st["n_start"][1] for st in ow.step(B["steps"]))
+        compare_model(b, m, ow, f"model {pick[m]} (side {md['side']})")
+        oc = ow.counters()
+        for k in ("n_active", "next_id", "hw", "overflow", "step"):
+            assert cnt[m][k] == oc[k], (pick[m], k, cnt[m][k], oc[k])
+        assert cnt[m]["agent_steps"] == agents
