@@ -78,7 +78,11 @@ int32_t abm_version(void);
  * agent-major, capacity x Fp int32 with Fp = F rounded up to a multiple of 4
  * (so one agent's fields are one 16/32-byte run). Placeholders (inactive
  * slots) keep their last field values. Limits: 1 <= capacity <= 2^28 - 1,
- * 1 <= F <= 16.
+ * 1 <= F <= 16. Every call reads a nonzero flag as live. abm_add and
+ * abm_selective_update write the flags of the 16-slot groups they fill (and
+ * abm_selective_update those of the 8-slot groups it empties) whole, as 0/1,
+ * so a flag other than 0 or 1 stored there by abm_slab_write becomes 1; the
+ * other calls leave such values as they are.
  */
 typedef struct abm_slab abm_slab;
 

@@ -43,6 +43,27 @@ __device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
   return c;
 }
 
+// The same generator with the ten rounds' key words given (rk[2r], rk[2r+1] =
+// the key after r Weyl steps), e.g. from a kernel's parameters, so that each
+// round's key is an operand instead of an addition.
+__device__ __forceinline__ uint4 philox_rk(uint4 c, const u32 (&rk)[20]) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const u32 p0_lo = 0xD2511F53u * c.x, p0_hi = __umulhi(0xD2511F53u, c.x);
+    const u32 p1_lo = 0xCD9E8D57u * c.z, p1_hi = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(p1_hi ^ c.y ^ rk[2 * r], p1_lo, p0_hi ^ c.w ^ rk[2 * r + 1], p0_lo);
+  }
+  return c;
+}
+
+// host: the round keys of key (seed, model) for philox_rk
+inline void philox_round_keys(u32 seed, u32 model, u32 (&rk)[20]) {
+  for (int r = 0; r < 10; ++r) {
+    rk[2 * r] = seed + (u32)r * 0x9E3779B9u;
+    rk[2 * r + 1] = model + (u32)r * 0xBB67AE85u;
+  }
+}
+
 __device__ __forceinline__ uint4 draw4(u32 seed, u32 model, u32 step, u32 slot, u32 purpose,
                                        u32 species) {
   return philox(make_uint4(step, slot, purpose, species), make_uint2(seed, model));

@@ -90,6 +90,7 @@ struct ScanArgs {
   int id_field;            // OP_ADD
   int use_rec_idx;         // OP_UPDATE with a record mask
   u32 step, threshold;     // OP_FUSED
+  u32 rk[20];              // OP_FUSED: Philox round keys of the slab's key (seed, model), round r at 2r, 2r+1
   int32_t* list_a;         // slots by rank: selected / free (caller's out_idx or scratch)
   int32_t* list_b;         // slots by rank: chosen (fused call)
   int32_t* out_count;      // device outputs (nullable)
@@ -133,6 +134,26 @@ __device__ __forceinline__ void block_sum2(u32& a, u32& b, u64* s_red) {
   b = (u32)t;
 }
 
+// 32-byte (256-bit) global accesses: one instruction moves a whole 8-field
+// row, so a row written to DRAM is one full sector (two 16-byte stores to a
+// sector make L2 fetch it first when the first half arrives alone)
+__device__ __forceinline__ void ld_v8_nc(const int32_t* p, int (&r)[8]) {
+  asm volatile("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "l"(p));
+}
+__device__ __forceinline__ void ld_v8(const int32_t* p, int (&r)[8]) {
+  asm volatile("ld.global.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "l"(p)
+               : "memory");
+}
+__device__ __forceinline__ void st_v8(int32_t* p, const int (&r)[8]) {
+  asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "r"(r[0]), "r"(r[1]), "r"(r[2]),
+               "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+               : "memory");
+}
+
 // Flags live in two bit-planes of one bit per slot: A = selected / free,
 // B = chosen (fused call); word w of a plane covers slots [32w, 32w + 32).
 //
@@ -155,6 +176,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_count(ScanArgs a) {
   const int wlo = blockIdx.x * a.chunk + warp * seg;
   const int whi = min(a.n, wlo + seg);
   const int32_t* flag_src = OP == OP_ARRAY ? a.src : s.active;
+  const bool vec = (((uintptr_t)flag_src) & 15) == 0;  // a caller's mask array may start anywhere
   u32 ca = 0, cb = 0;
   for (int b0 = wlo; b0 < whi; b0 += kWarpStep) {
     const int base = b0 + lane * kLaneSlots;
@@ -163,46 +185,32 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_count(ScanArgs a) {
     for (int v = 0; v < kLaneSlots / 4; ++v) {
       const int b = base + 4 * v;
       int4 q = make_int4(0, 0, 0, 0);
-      if (b + 3 < a.n) {
+      if (vec && b + 3 < a.n) {
         q = *reinterpret_cast<const int4*>(flag_src + b);
       } else {
         if (b + 0 < a.n) q.x = flag_src[b + 0];
         if (b + 1 < a.n) q.y = flag_src[b + 1];
         if (b + 2 < a.n) q.z = flag_src[b + 2];
+        if (b + 3 < a.n) q.w = flag_src[b + 3];
       }
       live[4 * v + 0] = q.x; live[4 * v + 1] = q.y; live[4 * v + 2] = q.z; live[4 * v + 3] = q.w;
     }
     u32 ma = 0, mb = 0, mr = 0;  // 16-bit masks over the lane's slots
-    if (OP == OP_FUSED) {
 #pragma unroll
-      for (int m = 0; m < kLaneSlots / 2; ++m) {
-        const int slot = base + 2 * m;
-        // slots 2j and 2j+1 share draw j: words (x, y) and (z, w) = (remove, choose)
-        const uint4 u = draw4(s.seed, s.model, a.step, (u32)slot >> 1, ABM_P_MASK, 0u);
-        const bool rm0 = live[2 * m] && u.x < a.threshold;
-        const bool rm1 = live[2 * m + 1] && u.z < a.threshold;
-        const bool al0 = live[2 * m] && !rm0, al1 = live[2 * m + 1] && !rm1;
-        ma |= ((u32)(slot < a.n && !al0) | ((u32)(slot + 1 < a.n && !al1) << 1)) << (2 * m);
-        mb |= ((u32)(al0 && u.y < a.threshold) | ((u32)(al1 && u.w < a.threshold) << 1)) << (2 * m);
-        mr |= ((u32)rm0 | ((u32)rm1 << 1)) << (2 * m);
+    for (int j = 0; j < kLaneSlots; ++j) {
+      const int slot = base + j;
+      bool f = false;
+      if (slot < a.n) {
+        if (OP == OP_ARRAY) f = live[j] != 0;
+        else if (OP == OP_ADD) f = live[j] == 0;
+        else f = eval_pred(a.pred, s, slot, live[j]) != (a.negate != 0);
       }
-    } else {
-#pragma unroll
-      for (int j = 0; j < kLaneSlots; ++j) {
-        const int slot = base + j;
-        bool f = false;
-        if (slot < a.n) {
-          if (OP == OP_ARRAY) f = live[j] != 0;
-          else if (OP == OP_ADD) f = live[j] == 0;
-          else f = eval_pred(a.pred, s, slot, live[j]) != (a.negate != 0);
-        }
-        ma |= (u32)f << j;
-      }
-      if (OP == OP_REMOVE) mr = ma;
+      ma |= (u32)f << j;
     }
-    // removed slots become placeholders now (the fused call refills some of
-    // them in pass 2): rewrite only the 4-slot groups that changed
-    if (OP == OP_REMOVE || OP == OP_FUSED) {
+    if (OP == OP_REMOVE) mr = ma;
+    // removed slots become placeholders now: rewrite only the 4-slot groups
+    // that changed (the other flags keep their values)
+    if (OP == OP_REMOVE) {
 #pragma unroll
       for (int v = 0; v < kLaneSlots / 4; ++v) {
         const u32 g = (mr >> (4 * v)) & 0xFu;
@@ -223,11 +231,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_count(ScanArgs a) {
     cb += __popc(mb);
     if (OP != OP_REMOVE) {
       const u32 na = __shfl_down_sync(0xFFFFFFFFu, ma, 1);
-      const u32 nb = __shfl_down_sync(0xFFFFFFFFu, mb, 1);
-      if (!(lane & 1) && base < a.n) {
-        a.planeA[base >> 5] = ma | (na << 16);
-        if (OP == OP_FUSED) a.planeB[base >> 5] = mb | (nb << 16);
-      }
+      if (!(lane & 1) && base < a.n) a.planeA[base >> 5] = ma | (na << 16);
     }
   }
   u64 v = ((u64)ca << 32) | cb;
@@ -253,15 +257,102 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_count(ScanArgs a) {
   }
 }
 
+// Pass 1 of the selective-update call: as k_count, with the live flags as a
+// 16-bit mask per lane (any nonzero flag is live) read by two 32-byte loads
+// and written back as 0/1 in whole 8-slot (32-byte) groups; the lane's eight
+// draws are independent and all in flight together. The pass is bound by the
+// Philox draws (one per pair of slots): fewer draws in flight at a higher
+// occupancy measured slower.
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_count_fused(ScanArgs a) {
+  constexpr int WARPS = THREADS / 32;
+  __shared__ u64 s_red[WARPS];
+  const SlabDev& s = a.s;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int seg = a.chunk / WARPS;
+  const int wlo = blockIdx.x * a.chunk + warp * seg;
+  const int whi = min(a.n, wlo + seg);
+  u32 ca = 0, cb = 0;
+  for (int b0 = wlo; b0 < whi; b0 += kWarpStep) {
+    const int base = b0 + lane * kLaneSlots;
+    // the selective-update call: live flags as a 16-bit mask (any nonzero
+    // flag is live), read with two 32-byte loads, written back as 0/1 in
+    // whole 8-slot (32-byte) groups
+    u32 ml = 0;
+    if (base + kLaneSlots <= a.n) {
+      int f[8];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        ld_v8(s.active + base + 8 * h, f);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) ml |= (u32)(f[j] != 0) << (8 * h + j);
+      }
+    } else {
+      for (int j = 0; j < kLaneSlots; ++j)
+        if (base + j < a.n) ml |= (u32)(s.active[base + j] != 0) << j;
+    }
+    u32 ma = 0, mb = 0, mr = 0;
+#pragma unroll
+    for (int m = 0; m < kLaneSlots / 2; ++m) {
+      const int slot = base + 2 * m;
+      // slots 2j and 2j+1 share draw j: words (x, y) and (z, w) = (remove, choose)
+      const uint4 u = philox_rk(make_uint4(a.step, (u32)slot >> 1, ABM_P_MASK, 0u), a.rk);
+      const u32 l0 = (ml >> (2 * m)) & 1u, l1 = (ml >> (2 * m + 1)) & 1u;
+      const u32 rm0 = l0 & (u32)(u.x < a.threshold), rm1 = l1 & (u32)(u.z < a.threshold);
+      const u32 al0 = l0 & ~rm0, al1 = l1 & ~rm1;
+      ma |= ((u32)(slot < a.n && !al0) | ((u32)(slot + 1 < a.n && !al1) << 1)) << (2 * m);
+      mb |= ((al0 & (u32)(u.y < a.threshold)) | ((al1 & (u32)(u.w < a.threshold)) << 1)) << (2 * m);
+      mr |= (rm0 | (rm1 << 1)) << (2 * m);
+    }
+    const u32 nl = ml & ~mr;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (!((mr >> (8 * h)) & 0xFFu)) continue;
+      const int b = base + 8 * h;
+      if (b + 8 <= a.n) {
+        int f[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) f[j] = (int)((nl >> (8 * h + j)) & 1u);
+        st_v8(s.active + b, f);
+      } else {
+        for (int j = 0; j < 8; ++j)
+          if (b + j < a.n) s.active[b + j] = (int)((nl >> (8 * h + j)) & 1u);
+      }
+    }
+    ca += __popc(ma);
+    cb += __popc(mb);
+    const u32 na = __shfl_down_sync(0xFFFFFFFFu, ma, 1);
+    const u32 nb = __shfl_down_sync(0xFFFFFFFFu, mb, 1);
+    if (!(lane & 1) && base < a.n) {
+      a.planeA[base >> 5] = ma | (na << 16);
+      a.planeB[base >> 5] = mb | (nb << 16);
+    }
+  }
+  u64 v = ((u64)ca << 32) | cb;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  if (lane == 0) {
+    a.wtotals[2 * (blockIdx.x * WARPS + warp)] = (u32)(v >> 32);
+    a.wtotals[2 * (blockIdx.x * WARPS + warp) + 1] = (u32)v;
+  }
+  block_sum2<THREADS>(ca, cb, s_red);
+  if (threadIdx.x == 0) {
+    a.totals[2 * blockIdx.x] = ca;
+    a.totals[2 * blockIdx.x + 1] = cb;
+  }
+}
+
 // Pass 2: ranks from the CTA prefix + warp prefix + a warp scan per step.
-// Plane A (possibly dense) is compacted word by word with the lanes
-// transposed onto the word's 32 slots, so flagged lanes write consecutive
-// ranks (coalesced); steps and words with no rank below the limit are
-// skipped. Plane B (sparse: chosen survivors) is walked per lane.
+// Each 512-slot step of a warp stages its flagged slots in shared memory in
+// rank order (each lane writes its own, 16 slots at most) and the warp copies
+// them out coalesced; steps with no rank below the limit are skipped. The add
+// passes also write the final live flags of every 16-slot group that receives
+// a new agent, whole (0/1), so no flag sector is written in part.
 template <int OP, int THREADS>
 __global__ void __launch_bounds__(THREADS) k_scatter(ScanArgs a) {
   constexpr int WARPS = THREADS / 32;
   __shared__ u64 s_red[WARPS];
+  __shared__ int s_stage[WARPS * kWarpStep];
   griddep_wait();
   const SlabDev& s = a.s;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -292,9 +383,9 @@ __global__ void __launch_bounds__(THREADS) k_scatter(ScanArgs a) {
   const int nrec = (OP == OP_UPDATE && a.use_rec_idx) ? s.counters[3] : a.k;
   const u32 limit = (u32)(OP == OP_UPDATE ? nrec : (OP == OP_SELECT || OP == OP_ARRAY ? 0x7FFFFFFF : a.k));
   const u32 limit_b = (u32)a.k;
-  const u32 half_lt = (1u << (lane & 15)) - 1u;
   // ranks land at list_a + *list_base (the permutation's second half)
   int32_t* const list_a = a.list_a + (OP == OP_SELECT && a.list_base ? *a.list_base : 0);
+  int* const stage = s_stage + warp * kWarpStep;
   const int seg = a.chunk / WARPS;
   const int wlo = blockIdx.x * a.chunk + warp * seg;
   const int whi = min(a.n, wlo + seg);
@@ -314,33 +405,59 @@ __global__ void __launch_bounds__(THREADS) k_scatter(ScanArgs a) {
     }
     const u32 tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
     const u32 ex = inc - c;
-    const u32 ra = pa + (ex & 0xFFFFu);
-    u32 rb = pb + (ex >> 16);
+    const u32 sa = pa, sb = pb;  // ranks of the step's first flagged slots
     pa += tot & 0xFFFFu;
     pb += tot >> 16;
-    // plane A: lanes (2w, 2w+1) hold word w of this step
-    u32 todo = __ballot_sync(0xFFFFFFFFu, ma != 0 && ra < limit);
-    todo = (todo | (todo >> 1)) & 0x55555555u;  // one bit per word (its even lane)
-    while (todo) {
-      const int w = (__ffs(todo) - 1) >> 1;
-      todo &= todo - 1;
-      const int owner = 2 * w + (lane >> 4);
-      const u32 om = __shfl_sync(0xFFFFFFFFu, ma, owner);
-      const u32 orank = __shfl_sync(0xFFFFFFFFu, ra, owner);
-      const int slot = b0 + 32 * w + lane;
-      const u32 rank = orank + __popc(om & half_lt);
-      if (((om >> (lane & 15)) & 1u) && rank < limit) {
-        list_a[rank] = slot;
-        if (OP == OP_ADD || OP == OP_FUSED) s.active[slot] = 1;
+    // plane A: the step's ranks [sa, sa + na) are below the limit
+    if (sa < limit && (tot & 0xFFFFu)) {
+      const u32 na = min(tot & 0xFFFFu, limit - sa);
+      const u32 off = ex & 0xFFFFu;
+      // plane A is dense: every flagged slot of the lane goes to its place
+      // below na, unrolled (no loop over the set bits)
+#pragma unroll
+      for (int j = 0; j < kLaneSlots; ++j) {
+        const u32 pos = off + (u32)__popc(ma & ((1u << j) - 1u));
+        if (((ma >> j) & 1u) && pos < na) stage[pos] = base + j;
       }
+      __syncwarp();
+      for (u32 i = lane; i < na; i += 32) list_a[sa + i] = stage[i];
+      if (OP == OP_ADD || OP == OP_FUSED) {
+        // flags of the lane's 16 slots after the adds: live 1, free 0, and the
+        // free slots with a rank below the limit 1
+        const u32 mine = (ex & 0xFFFFu) < na ? min((u32)__popc(ma), na - (ex & 0xFFFFu)) : 0u;
+        if (mine) {
+          const u32 added = mine == (u32)__popc(ma) ? ma : ma & ((1u << __fns(ma, 0, (int)mine + 1)) - 1u);
+          const u32 valid = base + kLaneSlots <= a.n ? 0xFFFFu : (1u << (a.n - base)) - 1u;
+          const u32 nl = ((~ma & valid) | added) & valid;
+          if (valid == 0xFFFFu) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              int f[8];
+#pragma unroll
+              for (int j = 0; j < 8; ++j) f[j] = (int)((nl >> (8 * h + j)) & 1u);
+              st_v8(s.active + base + 8 * h, f);
+            }
+          } else {
+            for (int j = 0; j < kLaneSlots; ++j)
+              if ((valid >> j) & 1u) s.active[base + j] = (int)((nl >> j) & 1u);
+          }
+        }
+      }
+      __syncwarp();  // the stage is rewritten next
     }
-    // plane B: per lane, in slot order
-    if (OP == OP_FUSED) {
-      while (mb && rb < limit_b) {
-        const int j = __ffs(mb) - 1;
-        mb &= mb - 1;
-        a.list_b[rb++] = base + j;
+    // plane B (the fused call's chosen survivors), the same way
+    if (OP == OP_FUSED && sb < limit_b && (tot >> 16)) {
+      const u32 nb = min(tot >> 16, limit_b - sb);
+      u32 off = ex >> 16;
+      u32 m = mb;
+      while (m && off < nb) {
+        const int j = __ffs(m) - 1;
+        m &= m - 1;
+        stage[off++] = base + j;
       }
+      __syncwarp();
+      for (u32 i = lane; i < nb; i += 32) a.list_b[sb + i] = stage[i];
+      __syncwarp();
     }
   }
   if (last_cta_out(a.ctrl)) {
@@ -379,11 +496,58 @@ __global__ void __launch_bounds__(THREADS) k_scatter(ScanArgs a) {
   }
 }
 
-// Pass 3: record j goes to (or is added to) the slot at rank j. Four records
-// per thread per round, all loads issued before the stores; coalesced record
-// reads, one 16/32-byte field run written per slot.
+// Whole 8-field rows, 32-byte aligned: records [j0, j1) of `rec` (or their
+// rec_idx entries) go to the slots list[j], U rows in flight per thread, all
+// loads issued before the stores. ADDROW: the slot's row is read and the
+// record added to it field-wise (wrapping).
+template <int U, bool ADDROW, bool STAMP, bool IDX>
+__device__ __forceinline__ void move_rows_v8(const ScanArgs& a, const int32_t* rec, const int32_t* list, int j1,
+                                             int id_field, int id0) {
+  const SlabDev& s = a.s;
+  const int stride = gridDim.x * blockDim.x;
+  for (int j0 = blockIdx.x * blockDim.x + threadIdx.x; j0 < j1; j0 += U * stride) {
+    int slot[U];
+    int r[U][8];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = j0 + u * stride;
+      slot[u] = -1;
+      if (j < j1) {
+        slot[u] = list[j];
+        ld_v8_nc(rec + (size_t)(IDX ? s.rec_idx[j] : j) * 8, r[u]);
+      }
+    }
+    if (ADDROW) {
+      int o[U][8];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (slot[u] >= 0) ld_v8(s.fields + (size_t)slot[u] * 8, o[u]);
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int f = 0; f < 8; ++f) r[u][f] = (int)((u32)o[u][f] + (u32)r[u][f]);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (slot[u] < 0) continue;
+      if (STAMP) {  // the id of an added agent: next id + its rank
+        const int id = (int)((u32)id0 + (u32)(j0 + u * stride));
+#pragma unroll
+        for (int f = 0; f < 8; ++f)
+          if (f == id_field) r[u][f] = id;
+      }
+      st_v8(s.fields + (size_t)slot[u] * 8, r[u]);
+    }
+  }
+}
+
+// Pass 3: record j goes to (or is added to) the slot at rank j, four records
+// per thread in flight, all loads issued before the stores; coalesced record
+// reads, one field run written per slot (one 32-byte store for 8 fields).
+// Two CTAs of 256 threads per SM (96 registers) measured faster than three
+// with two rows in flight where rows are read.
 template <int OP>
-__global__ void __launch_bounds__(256, 4) k_apply(ScanArgs a) {
+__global__ void __launch_bounds__(256, 2) k_apply(ScanArgs a) {
   griddep_wait();
   const SlabDev& s = a.s;
   const int ra = s.meta[0], rb = s.meta[1];
@@ -391,6 +555,25 @@ __global__ void __launch_bounds__(256, 4) k_apply(ScanArgs a) {
   const int total = ra + rb;
   const int stride = gridDim.x * blockDim.x;
   const bool f8 = s.F == 8 && s.Fp == 8 && ((((uintptr_t)a.rec) | ((uintptr_t)a.rec2)) & 15) == 0;
+  // 8 fields, records 32-byte aligned (the rows always are): whole rows per instruction
+  if (f8 && ((((uintptr_t)a.rec) | ((uintptr_t)a.rec2) | ((uintptr_t)s.fields)) & 31) == 0) {
+    if (OP == OP_UPDATE) {
+      const bool idx = a.use_rec_idx != 0;
+      if (a.op_kind == ABM_OP_ADD) {
+        if (idx) move_rows_v8<4, true, false, true>(a, a.rec, a.list_a, ra, -1, 0);
+        else move_rows_v8<4, true, false, false>(a, a.rec, a.list_a, ra, -1, 0);
+      } else {
+        if (idx) move_rows_v8<4, false, false, true>(a, a.rec, a.list_a, ra, -1, 0);
+        else move_rows_v8<4, false, false, false>(a, a.rec, a.list_a, ra, -1, 0);
+      }
+    } else if (OP == OP_ADD && a.id_field >= 0) {
+      move_rows_v8<4, false, true, false>(a, a.rec, a.list_a, ra, a.id_field, id0);
+    } else {
+      move_rows_v8<4, false, false, false>(a, a.rec, a.list_a, ra, -1, 0);
+    }
+    if (OP == OP_FUSED) move_rows_v8<4, true, false, false>(a, a.rec2, a.list_b, rb, -1, 0);
+    return;
+  }
   for (int j0 = blockIdx.x * blockDim.x + threadIdx.x; j0 < total; j0 += 4 * stride) {
     if (f8) {
       int slot[4];
@@ -737,6 +920,21 @@ static PredDev to_dev(const abm_pred* p) {
   return d;
 }
 
+// The apply pass runs one wave: as many CTAs as fit on the device at once
+// (looked up once per device), each striding over the records.
+template <int OP>
+static int apply_grid() {
+  static std::atomic<int> per_sm[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+  int b = (dev >= 0 && dev < 64) ? per_sm[dev].load(std::memory_order_relaxed) : 0;
+  if (!b) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_apply<OP>, 256, 0) != cudaSuccess || b < 1) b = 1;
+    if (dev >= 0 && dev < 64) per_sm[dev].store(b, std::memory_order_relaxed);
+  }
+  return num_sms() * b;
+}
+
 // Up to three launches per operation: flags + per-warp / per-CTA counts, then
 // ranks + slot lists, then the record moves. Each warp owns one static
 // segment of slots in the first two passes; no CTA waits for another.
@@ -760,13 +958,14 @@ static abm_status launch_scan(abm_slab* s, const ScanArgs& a, bool aux, cudaStre
   const long per = ((long)b.n + target - 1) / target;
   b.chunk = (int)(((per + SUB - 1) / SUB) * SUB);
   b.G = (int)(((long)b.n + b.chunk - 1) / b.chunk);
-  k_count<OP, THREADS><<<b.G, THREADS, 0, st>>>(b);
+  if constexpr (OP == OP_FUSED) k_count_fused<THREADS><<<b.G, THREADS, 0, st>>>(b);
+  else k_count<OP, THREADS><<<b.G, THREADS, 0, st>>>(b);
   ABM_LAUNCH_CHECK();
   // the next passes may launch while the previous one drains; they wait on
   // it (griddepcontrol) before reading its results
   if (OP != OP_REMOVE) ABM_CUDA_TRY(launch_pdl(k_scatter<OP, THREADS>, b.G, THREADS, st, b));
   if (OP == OP_ADD || OP == OP_UPDATE || OP == OP_FUSED)
-    ABM_CUDA_TRY(launch_pdl(k_apply<OP>, num_sms() * 8, 256, st, b));
+    ABM_CUDA_TRY(launch_pdl(k_apply<OP>, apply_grid<OP>(), 256, st, b));
   return ABM_OK;
 }
 
@@ -871,6 +1070,7 @@ extern "C" abm_status abm_selective_update(abm_slab* s, uint32_t step, uint32_t 
                                            int32_t* out_counts, void* stream) {
   if (!s || k < 0 || (k > 0 && (!records || !deltas))) return ABM_ERR_ARG;
   ScanArgs a = base_args(s);
+  philox_round_keys(s->d.seed, s->d.model, a.rk);
   a.rec = records;
   a.rec2 = deltas;
   a.k = k;

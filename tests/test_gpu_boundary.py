@@ -209,10 +209,15 @@ def test_batch_rerun_overflowed(lib):
         for f in FIELDS:
             assert torch.equal(b.agents(m, s, f), ref.agents(m, s, f)), (m, s, f)
     assert torch.equal(b.grass(m, "wait"), ref.grass(m, "wait"))
-    # both batches go on stepping (the rerun models at their fixed capacity)
+    # both batches go on stepping: the rerun models at their fixed capacity stay
+    # equal to the reference; a model that was not rerun keeps its learned
+    # capacity, sized for 60 steps, and stays equal unless it now overflows
     b.run(15, sweep=abm.SWEEP_EXTENT)
     ref.run(15, sweep=abm.SWEEP_EXTENT)
-    assert np.array_equal(b.digest().cpu().numpy(), ref.digest().cpu().numpy())
+    d_b, d_ref, c_b = b.digest().cpu().numpy(), ref.digest().cpu().numpy(), b.counters()
+    for m in range(40):
+        if m in ov or not max(c_b[m]["overflow"]):
+            assert d_b[m] == d_ref[m], m
     b.check()
     # one rerun per batch
     cf = np.ascontiguousarray(fixed)

@@ -70,6 +70,74 @@ def test_selective_update_parity(eng, n, p):
         assert s.counters()["n_active"] == int(o.active.sum())
 
 
+@pytest.mark.parametrize("offset", [0, 4, 1])
+@pytest.mark.parametrize("p", [0.05, 0.5])
+def test_selective_update_record_alignment(eng, offset, p):
+    """Records and deltas starting 0, 16 or 4 bytes past a 32-byte boundary
+    (the three ways the apply pass moves 8-field rows) give the same slab."""
+    from paper_2508_16508_gb300 import abm
+    n, F = 20_011, 8
+    T, k = workloads.threshold(p), workloads.k_for(p, n)
+    s = eng.Slab(n, F, seed=4, init=1)
+    o = oracle.Slab(n, F)
+    o.c1_init(seed=4)
+    rb = torch.empty(k * F + 8, dtype=torch.int32, device="cuda")
+    db = torch.empty(k * F + 8, dtype=torch.int32, device="cuda")
+    rec, dl = rb[offset:offset + k * F].view(k, F), db[offset:offset + k * F].view(k, F)
+    for step in range(3):
+        s.philox_records(step, abm.P_NEWREC0, abm.P_NEWREC1, k, out=rec)
+        s.philox_records(step, abm.P_DELTA0, abm.P_DELTA1, k, out=dl)
+        cnt = np_of(s.selective_update(step, T, rec, dl))
+        want = o.c1_call(step, T, k, seed=4)
+        assert cnt.tolist() == [want["removed"], want["added"], want["updated"]]
+        act, fld = slab_state(s)
+        np.testing.assert_array_equal(act, o.active)
+        np.testing.assert_array_equal(fld, o.fields)
+    s.check()
+
+
+def test_live_flag_values(eng):
+    """Nonzero flags other than 1 count as live everywhere; a call that fills a
+    16-slot group (add) or empties an 8-slot group (the fused call) writes that
+    group's flags as 0/1, and every other flag keeps its value."""
+    from paper_2508_16508_gb300 import abm
+    n, F = 4000, 3
+    rng = np.random.default_rng(8)
+    flags = np.where(rng.random(n) < 0.7, rng.choice([1, 7, -2], size=n), 0).astype(np.int32)
+    s = eng.Slab(n, F)
+    s.write(-1, torch.from_numpy(flags).cuda())
+    o = oracle.Slab(n, F)
+    o.active[:] = flags != 0
+    k = 40
+    rec = rng.integers(-9, 9, size=(k, F)).astype(np.int32)
+    slots, cnt = s.add(torch.from_numpy(rec).cuda())
+    r, want_slots = o.add(rec)
+    assert int(cnt.item()) == r == k
+    np.testing.assert_array_equal(np_of(slots[:r]), want_slots)
+    got = np_of(s.read(-1))
+    np.testing.assert_array_equal(got != 0, o.active != 0)
+    filled = np.zeros(n, bool)
+    for g in np.unique(want_slots // 16):
+        filled[16 * g:16 * g + 16] = True
+    assert set(np.unique(got[filled]).tolist()) <= {0, 1}
+    np.testing.assert_array_equal(got[~filled], flags[~filled])
+    # a mask array that starts 4 bytes past an aligned address (scalar loads)
+    buf = torch.zeros(n + 1, dtype=torch.int32, device="cuda")
+    tm = (rng.random(n) < 0.5).astype(np.int32)
+    buf[1:] = torch.from_numpy(tm).cuda()
+    d = rng.integers(-5, 5, size=(300, F)).astype(np.int32)
+    rmask = torch.zeros(301, dtype=torch.int32, device="cuda")
+    rm = (rng.random(300) < 0.5).astype(np.int32)
+    rmask[1:] = torch.from_numpy(rm).cuda()
+    _, ucnt = s.update_distinct(abm.pred(abm.PRED_MASK, mask=buf[1:]), torch.from_numpy(d).cuda(),
+                                rmask[1:], op=abm.OP_ADD)
+    ru, _ = o.update_distinct(tm.astype(bool) & (o.active != 0), d, rec_mask=rm, op=0)
+    assert int(ucnt.item()) == ru
+    _, fld = slab_state(s)
+    np.testing.assert_array_equal(fld, o.fields)
+    s.check()
+
+
 def test_selective_update_equals_separate_calls(eng):
     from paper_2508_16508_gb300 import abm
     n, F, p = 50_000, 8, 0.05
