@@ -348,8 +348,48 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_count_fused(ScanArg
 // them out coalesced; steps with no rank below the limit are skipped. The add
 // passes also write the final live flags of every 16-slot group that receives
 // a new agent, whole (0/1), so no flag sector is written in part.
-template <int OP, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_scatter(ScanArgs a) {
+// The selective-update call's records moved by the pass that ranks them:
+// the staged slots [0, n) of a warp step take records r0 + i (ADDROW: added
+// to the row, wrapping), two 32-byte rows per lane in flight. With a slab
+// that is mostly live, free and chosen slots spread evenly over it, so the
+// static slot partition also balances the record moves.
+template <bool ADDROW>
+__device__ __forceinline__ void move_staged(const ScanArgs& a, const int* stage, u32 n, u32 r0, const int32_t* rec,
+                                            int lane) {
+  constexpr int U = 2;
+  for (u32 i0 = lane; i0 < n; i0 += 32 * U) {
+    int slot[U];
+    int r[U][8];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const u32 i = i0 + 32 * u;
+      slot[u] = -1;
+      if (i < n) {
+        slot[u] = stage[i];
+        ld_v8_nc(rec + (size_t)(r0 + i) * 8, r[u]);
+      }
+    }
+    if (ADDROW) {
+      int o[U][8];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (slot[u] >= 0) ld_v8(a.s.fields + (size_t)slot[u] * 8, o[u]);
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int f = 0; f < 8; ++f) r[u][f] = (int)((u32)o[u][f] + (u32)r[u][f]);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (slot[u] >= 0) st_v8(a.s.fields + (size_t)slot[u] * 8, r[u]);
+  }
+}
+
+// MOVE (selective-update call, 8 fields, 32-byte aligned records): the pass
+// moves the records itself instead of writing the rank-ordered slot lists, and
+// no apply pass follows.
+template <int OP, int THREADS, bool MOVE = false>
+__global__ void __launch_bounds__(THREADS, MOVE ? (768 / THREADS > 0 ? 768 / THREADS : 1) : 1) k_scatter(ScanArgs a) {
   constexpr int WARPS = THREADS / 32;
   __shared__ u64 s_red[WARPS];
   __shared__ int s_stage[WARPS * kWarpStep];
@@ -420,7 +460,8 @@ __global__ void __launch_bounds__(THREADS) k_scatter(ScanArgs a) {
         if (((ma >> j) & 1u) && pos < na) stage[pos] = base + j;
       }
       __syncwarp();
-      for (u32 i = lane; i < na; i += 32) list_a[sa + i] = stage[i];
+      if constexpr (MOVE) move_staged<false>(a, stage, na, sa, a.rec, lane);
+      else for (u32 i = lane; i < na; i += 32) list_a[sa + i] = stage[i];
       if (OP == OP_ADD || OP == OP_FUSED) {
         // flags of the lane's 16 slots after the adds: live 1, free 0, and the
         // free slots with a rank below the limit 1
@@ -456,7 +497,8 @@ __global__ void __launch_bounds__(THREADS) k_scatter(ScanArgs a) {
         stage[off++] = base + j;
       }
       __syncwarp();
-      for (u32 i = lane; i < nb; i += 32) a.list_b[sb + i] = stage[i];
+      if constexpr (MOVE) move_staged<true>(a, stage, nb, sb, a.rec2, lane);
+      else for (u32 i = lane; i < nb; i += 32) a.list_b[sb + i] = stage[i];
       __syncwarp();
     }
   }
@@ -963,6 +1005,17 @@ static abm_status launch_scan(abm_slab* s, const ScanArgs& a, bool aux, cudaStre
   ABM_LAUNCH_CHECK();
   // the next passes may launch while the previous one drains; they wait on
   // it (griddepcontrol) before reading its results
+  if constexpr (OP == OP_FUSED) {
+    // many records (k >= capacity / 8), 8 fields, 32-byte aligned records and
+    // deltas: the ranking pass moves them. With fewer records a warp step holds
+    // too few to keep memory busy, and the separate apply pass (four records
+    // per thread over the whole grid) measured faster.
+    if ((long long)b.k * 8 >= (long long)s->d.cap && s->d.F == 8 && s->d.Fp == 8 &&
+        ((((uintptr_t)b.rec) | ((uintptr_t)b.rec2)) & 31) == 0) {
+      ABM_CUDA_TRY(launch_pdl(k_scatter<OP, THREADS, true>, b.G, THREADS, st, b));
+      return ABM_OK;
+    }
+  }
   if (OP != OP_REMOVE) ABM_CUDA_TRY(launch_pdl(k_scatter<OP, THREADS>, b.G, THREADS, st, b));
   if (OP == OP_ADD || OP == OP_UPDATE || OP == OP_FUSED)
     ABM_CUDA_TRY(launch_pdl(k_apply<OP>, apply_grid<OP>(), 256, st, b));
