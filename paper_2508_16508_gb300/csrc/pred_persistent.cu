@@ -630,6 +630,49 @@ struct Births {
   int r, F, ext, id0;
 };
 
+// A thread's first birth in two halves, so that other work runs between its
+// round trips: the parent and slot indices are loaded first (p < 0: none),
+// the parent's record and the writes come later (p_births_from, which also
+// takes the births beyond the first one per thread).
+struct FirstBirth {
+  int p, slot;
+};
+
+template <int S>
+__device__ __forceinline__ FirstBirth births_prefetch(const WorldDev& w, const Births& b) {
+  const SpeciesDev& sp = w.sp[S];
+  const int i = blockIdx.x + gridDim.x * threadIdx.x;
+  FirstBirth f{-1, 0};
+  if (i < b.r) {
+    f.p = sp.parents[i];
+    f.slot = i < b.F ? sp.freel[i] : b.ext + (i - b.F);
+  }
+  return f;
+}
+
+template <int S>
+__device__ __forceinline__ void births_finish(const WorldDev& w, int t, const Births& b, FirstBirth f) {
+  const SpeciesDev& sp = w.sp[S];
+  if (f.p >= 0) {
+    const int i = blockIdx.x + gridDim.x * threadIdx.x;
+    const int4 pa = sp.agent[f.p];
+    const int half = pa.y >> 1;
+    sp.agent[f.p].y = pa.y - half;
+    sp.agent[f.slot] = make_int4(pa.x, half, (int)((u32)b.id0 + (u32)i), 0);
+    sp.active[f.slot] = 1;
+  }
+  // births beyond one per thread (S == 1 only: wolf births carry no victim key)
+  for (int i = blockIdx.x + gridDim.x * (threadIdx.x + kPT); i < b.r; i += gridDim.x * kPT) {
+    const int p = sp.parents[i];
+    const int slot = i < b.F ? sp.freel[i] : b.ext + (i - b.F);
+    const int4 pa = sp.agent[p];
+    const int half = pa.y >> 1;
+    sp.agent[p].y = pa.y - half;
+    sp.agent[slot] = make_int4(pa.x, half, (int)((u32)b.id0 + (u32)i), 0);
+    sp.active[slot] = 1;
+  }
+}
+
 __device__ __forceinline__ u64 globaltimer() {
   u64 t;
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
@@ -697,9 +740,11 @@ __global__ void __launch_bounds__(kPT, MINB) k_persistent(WorldDev w, int nsteps
   abm_step_stats* stp = nullptr;
   auto wolf_ranks = [&](int tw /* step whose wolves are ranked */) {
     int* accw = ps.acc + 4 * (tw & 1);
+    // the step's counters (complete since the last barrier), loaded before the
+    // rank phase so that their round trip overlaps its own loads
+    const int starved1 = accw[1], eaten = accw[2];
     u32 F1, P1;
     rank_phase<1>(w, ext[1], kseg1, F1, P1, s_red, s_pre);
-    const int starved1 = accw[1], eaten = accw[2];
     const int avail1 = (int)F1 + (cap[1] - ext[1]);
     const int r1 = min((int)P1, avail1);
     wb = {r1, (int)F1, ext[1], nid[1]};
@@ -748,11 +793,14 @@ __global__ void __launch_bounds__(kPT, MINB) k_persistent(WorldDev w, int nsteps
     clk.lap(0);
     if (*(volatile int*)w.err) return;
     // ---- P2: wolf births of the previous step | sheep eat / select / die / flags
-    if (it > 0) p_births<1>(w, t - 1, wb.r, wb.F, wb.ext, wb.id0);
+    // the previous step's wolf births around the sheep's eat/select/die: their
+    // index loads are in flight while the sheep work runs
+    const FirstBirth fb = it > 0 ? births_prefetch<1>(w, wb) : FirstBirth{-1, 0};
     if (blockIdx.x == 0)  // wolf segment sums: last read in P1
       for (int j = threadIdx.x; j < (int)gridDim.x; j += kPT) ps.seg[1][j] = 0ull;
     const int kseg0 = (((ext[0] + 127) >> 7) + (int)gridDim.x - 1) / (int)gridDim.x;
     p_count<0>(w, t, ext[0], kseg0, acc, cl, carried, s_upar, s_acc);
+    if (it > 0) births_finish<1>(w, t - 1, wb, fb);
     grid_sync(ps.bar, w.err, bar_target);
     clk.lap(1);
     // ---- P3: sheep ranks and lists | wolves move + claims
@@ -766,11 +814,11 @@ __global__ void __launch_bounds__(kPT, MINB) k_persistent(WorldDev w, int nsteps
     grid_sync(ps.bar, w.err, bar_target);
     clk.lap(2);
     // ---- P4: sheep births; sheep counters
+    starved0p = acc[0];  // written in P2: loaded ahead of the births' own loads
+    grassp = acc[3];
     p_births<0>(w, t, sb.r, sb.F, sb.ext, sb.id0);
     if (blockIdx.x == 0)  // sheep segment sums: last read in P3
       for (int j = threadIdx.x; j < (int)gridDim.x; j += kPT) ps.seg[0][j] = 0ull;
-    starved0p = acc[0];
-    grassp = acc[3];
     {
       const int n_after = nstart0 + r0;
       if (n_after > hw[0]) hw[0] = n_after;
