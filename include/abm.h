@@ -23,6 +23,14 @@
  *  - Spin-waits inside kernels are bounded. A wait that runs out sets a
  *    device error word and the kernel returns; abm_*_check() reports
  *    ABM_ERR_DEVICE_TIMEOUT and the handle's results are then undefined.
+ *  - Check build (libabm_check.so, the same sources compiled with -DABM_CHECK,
+ *    slower): every data-dependent index (a slot from a list, a cell from an
+ *    agent record, a parent, a victim) is tested before use; a violation is
+ *    recorded in the handle's error word and the access skipped. The padding
+ *    past each slab's capacity holds canaries (agent fields 0x7E57CA11, live
+ *    flags 0). abm_slab_check / abm_world_check / abm_batch_check then report
+ *    ABM_ERR_CHECK for a recorded violation or a damaged canary. abm_version()
+ *    is negative in a check build.
  *  - Randomness is Philox4x32-10 (Salmon et al., SC'11) with counter
  *    (step, slot, purpose, species) and key (seed, model); a probability p is
  *    an integer threshold T = floor(p * 2^32) and an event happens iff the
@@ -47,6 +55,7 @@ typedef int32_t abm_status;
 #define ABM_ERR_OVERFLOW 5       /* informational: more agents asked for a slot than were free */
 #define ABM_ERR_STATE 6          /* operation not valid for this handle */
 #define ABM_ERR_TOO_LARGE 7      /* size beyond a fixed, documented maximum */
+#define ABM_ERR_CHECK 8          /* check build only: an index out of range or a damaged canary was recorded */
 
 const char* abm_strerror(abm_status s);
 /* Library version: major * 10000 + minor * 100 + patch. */
@@ -401,6 +410,12 @@ abm_status abm_world_tune(abm_world* w, int32_t engine, int32_t ctas_per_sm);
  * and reported -- the expected outcome -- and leaves the context usable.
  * Synchronises `stream`. */
 abm_status abm_diag_barrier_timeout(int32_t spin_limit, void* stream);
+/* Self-check of the check build's index test (no counterpart in the paper):
+ * tests index i against [0, n) on the device, the way the kernels test their
+ * indices, without any access. Check build: ABM_ERR_CHECK if i is out of
+ * range, else ABM_OK. Other builds: ABM_OK (nothing is tested). Synchronises
+ * `stream`. */
+abm_status abm_diag_check_index(int64_t i, int64_t n, void* stream);
 /* Synchronises `stream`; reports a recorded device error (e.g. a timed-out wait). */
 abm_status abm_world_check(abm_world* w, void* stream);
 

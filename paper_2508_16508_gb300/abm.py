@@ -13,11 +13,14 @@ import os
 import threading
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libabm.so")
+# ABM_LIBRARY=check selects the check build (libabm_check.so: index tests and
+# canaries, slower), for the whole process
+CHECK_BUILD = os.environ.get("ABM_LIBRARY", "") == "check"
+LIB_PATH = os.path.join(_HERE, "libabm_check.so" if CHECK_BUILD else "libabm.so")
 _lock = threading.Lock()
 _lib = None
 
-OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_DEVICE_TIMEOUT, ERR_OVERFLOW, ERR_STATE, ERR_TOO_LARGE = range(8)
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_DEVICE_TIMEOUT, ERR_OVERFLOW, ERR_STATE, ERR_TOO_LARGE, ERR_CHECK = range(9)
 RESOLVE_STATIC_MAX_R = 1 << 18
 
 P_MOVE, P_PRIO, P_REPRO, P_VICTIM = 1, 2, 3, 4
@@ -159,6 +162,7 @@ def _sig(L):
         "abm_digest": ([vp, vp, vp], st),
         "abm_world_slab": ([vp, i32, pp, vp], st),
         "abm_world_slab_commit": ([vp, i32, vp], st),
+        "abm_diag_check_index": ([i64, i64, vp], st),
         "abm_capacity_features": ([vp, i32, vp, vp, vp], st),
         "abm_capacity_from_prediction": ([vp, i32, C.c_float, i32, vp, vp, vp, vp], st),
         "abm_lob_match": ([i32, i32, vp, vp, vp, vp, vp, vp, vp, vp], st),
@@ -183,10 +187,10 @@ def lib():
     with _lock:
         if _lib is None:
             from . import build as _build
-            if not _build.up_to_date():
-                _build.build()
+            if not _build.up_to_date(CHECK_BUILD):
+                _build.build(check=CHECK_BUILD)
             if not os.path.exists(LIB_PATH):
-                raise RuntimeError(f"libabm.so not found at {LIB_PATH}")
+                raise RuntimeError(f"{os.path.basename(LIB_PATH)} not found at {LIB_PATH}")
             _lib = _sig(C.CDLL(LIB_PATH))
     return _lib
 

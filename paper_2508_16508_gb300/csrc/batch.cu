@@ -83,6 +83,7 @@ template <int T>
 __device__ __forceinline__ void move_agent(const BatchDev& b, const MCtx& c, int S, int t, int slot, int4 a) {
   int4* ag = b.agent[S] + c.m.oa[S];
   u64* victim = b.victim + c.m.oc;
+  if (!in_range(a.x, c.m.ncells, b.err)) return;  // check builds: a cell outside the model's lattice
   if (S == 0) victim[a.x] = kNoKey;
   const u32 dir = draw(c.m.seed, c.m.model, (u32)t, (u32)slot, ABM_P_MOVE, (u32)S) >> 29;
   const int cell = step_cell(a.x, c.m.side, dir);
@@ -152,6 +153,7 @@ __device__ __forceinline__ u32 scan_agent(const BatchDev& b, const MCtx& c, int 
   u64* victim = b.victim + c.m.oc;
   int4 a = ag[slot];
   const int cell = a.x;
+  if (!in_range(cell, c.m.ncells, b.err)) return 0u;  // check builds only
   const u64 cl = claim[cell];
   u32 r = 0;
   if (cl != kNoKey && (u32)cl == (u32)slot) {
@@ -163,7 +165,7 @@ __device__ __forceinline__ u32 scan_agent(const BatchDev& b, const MCtx& c, int 
       b.regrow[c.m.oc + cell] = t + c.m.prm[PRM_REGROWTH];
     } else {
       const u64 v = victim[cell];
-      b.active[0][c.m.oa[0] + (u32)v] = 0;
+      if (in_range((u32)v, c.m.cap[0], b.err)) b.active[0][c.m.oa[0] + (u32)v] = 0;
       victim[cell] = kNoKey;
     }
   }
@@ -228,13 +230,14 @@ __device__ __forceinline__ void b_scan(const BatchDev& b, MCtx& c, int S, int sw
     while (frm) {
       const int j = __ffs(frm) - 1;
       frm &= frm - 1;
-      if ((int)rf < bound) flist[rf] = base + j;
+      if ((int)rf < bound && in_range(rf, c.m.cap_pad[S], b.err)) flist[rf] = base + j;
       ++rf;
     }
     while (par) {
       const int j = __ffs(par) - 1;
       par &= par - 1;
-      plist[rp++] = base + j;
+      if (in_range(rp, c.m.cap_pad[S], b.err)) plist[rp] = base + j;
+      ++rp;
     }
     pf += tot_f;
     pp += tot_p;
@@ -268,6 +271,7 @@ __device__ __forceinline__ void b_births(const BatchDev& b, MCtx& c, int S, int 
   for (int i = threadIdx.x; i < r; i += T) {
     const int p = plist[i];
     const int slot = i < Fin ? flist[i] : ext + (i - Fin);
+    if (!in_range(p, c.m.cap[S], b.err) || !in_range(slot, c.m.cap[S], b.err)) continue;
     const int4 pa = ag[p];
     const int half = pa.y >> 1;
     ag[p].y = pa.y - half;
@@ -402,7 +406,8 @@ __global__ void k_batch_init(BatchDev b) {
         b.agent[s][g] = make_int4(uniform_below(u.x, m.ncells), uniform_below(u.y, 2 * gain), k, 0);
         b.active[s][g] = 1;
       } else {
-        b.agent[s][g] = make_int4(0, 0, 0, 0);
+        // check builds: canaries in the fields past the capacity (the flags stay 0)
+        b.agent[s][g] = (kCheck && k >= m.cap[s]) ? make_int4(kCanary, kCanary, kCanary, kCanary) : make_int4(0, 0, 0, 0);
         b.active[s][g] = 0;
       }
     }
@@ -465,6 +470,18 @@ __global__ void k_batch_overflowed(BatchDev b, int32_t* list, int32_t* count) {
     __syncthreads();
   }
   if (threadIdx.x == 0) *count = n;
+}
+
+// check builds: one CTA per model verifies the padding past each capacity
+__global__ void k_batch_canaries(BatchDev b) {
+  const BModel m = b.models[blockIdx.x];
+  bool bad = false;
+  for (int s = 0; s < 2; ++s)
+    for (int k = m.cap[s] + (int)threadIdx.x; k < m.cap_pad[s]; k += blockDim.x) {
+      const int4 a = b.agent[s][m.oa[s] + k];
+      bad |= b.active[s][m.oa[s] + k] != 0 || a.x != kCanary || a.y != kCanary || a.z != kCanary || a.w != kCanary;
+    }
+  if (bad) atomicCAS(b.err, 0, kErrCheck);
 }
 
 // order-independent digest of one model's observable state (digest_* terms)
@@ -747,10 +764,14 @@ extern "C" abm_status abm_batch_digest(abm_batch* b, uint64_t* out, void* stream
 
 extern "C" abm_status abm_batch_check(abm_batch* b, void* stream) {
   if (!b) return ABM_ERR_ARG;
+  if (kCheck) {
+    k_batch_canaries<<<b->d.nmodels, 128, 0, (cudaStream_t)stream>>>(b->d);
+    ABM_LAUNCH_CHECK();
+  }
   ABM_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
   int err = 0;
   ABM_CUDA_TRY(cudaMemcpy(&err, b->d.err, sizeof(int), cudaMemcpyDeviceToHost));
-  if (err) return ABM_ERR_DEVICE_TIMEOUT;
+  if (err) return ABM_ERR_OF(err);
   return b->rerun ? abm_batch_check(b->rerun, stream) : ABM_OK;
 }
 

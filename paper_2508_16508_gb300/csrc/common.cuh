@@ -26,6 +26,31 @@ constexpr int kMaxSpin = 1 << 23;  // bounded waits: ~2 s with the back-off belo
 
 // Device error codes written into a handle's error word.
 constexpr int kErrTimeout = 1;
+constexpr int kErrCheck = 2;  // check builds: an index out of range or a damaged canary
+
+// Check builds (compiled with -DABM_CHECK into libabm_check.so; a stand-in for
+// a memory checker): data-dependent indices are tested before they are used,
+// and the padding past each slab's capacity holds canaries that the *_check
+// calls verify. Other builds compile every test away.
+#ifdef ABM_CHECK
+constexpr bool kCheck = true;
+#else
+constexpr bool kCheck = false;
+#endif
+constexpr int kCanary = 0x7E57CA11;  // agent fields past the capacity (live flags there stay 0)
+
+// true iff 0 <= i < n; in a check build a violation is recorded in *err (the
+// first error word set wins) and false is returned, so that the caller skips
+// the access. Always true in other builds.
+__device__ __forceinline__ bool in_range(long long i, long long n, int* err) {
+  if constexpr (kCheck) {
+    if (i < 0 || i >= n) {
+      if (err) atomicCAS(err, 0, kErrCheck);
+      return false;
+    }
+  }
+  return true;
+}
 
 // ----------------------------------------------------------------------------
 // Philox4x32-10: ten rounds; each multiplies counter words 0 and 2 by the two
@@ -277,6 +302,9 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, cudaStream
     cudaError_t _e = (expr);                   \
     if (_e != cudaSuccess) return ABM_ERR_CUDA; \
   } while (0)
+
+// status of a handle's device error word
+#define ABM_ERR_OF(word) ((word) == 0 ? ABM_OK : ((word) == abm::kErrCheck ? ABM_ERR_CHECK : ABM_ERR_DEVICE_TIMEOUT))
 
 #define ABM_LAUNCH_CHECK()                      \
   do {                                          \

@@ -138,6 +138,7 @@ __device__ __forceinline__ void list_push(u64* head, u64* next, u64* keys, int c
 template <int S>
 __device__ __forceinline__ int4 move_one(const WorldDev& w, int t, int slot, int4 ag, int L, int metab) {
   const SpeciesDev& sp = w.sp[S];
+  if (!in_range(ag.x, w.ncells, w.err)) return ag;  // check builds: a cell outside the lattice
   if (S == 0 && !(w.variant & ABM_VARIANT_MANY_WOLVES)) w.victim[ag.x] = kNoKey;  // last step's victim entry here
   const u32 dir = draw(w.seed, w.model, (u32)t, (u32)slot, ABM_P_MOVE, (u32)S) >> 29;
   const int cell = step_cell(ag.x, L, dir);
@@ -282,7 +283,7 @@ __device__ __forceinline__ u32 count_one(const WorldDev& w, int t, int slot, int
     } else {
       w.wclaim[cell] = kNoKey;
       const u64 v = w.victim[cell];
-      w.sp[0].active[(u32)v] = 0;
+      if (in_range((u32)v, w.sp[0].cap, w.err)) w.sp[0].active[(u32)v] = 0;
       w.victim[cell] = kNoKey;
     }
   }
@@ -353,6 +354,8 @@ __device__ __forceinline__ void p_count(const WorldDev& w, int t, int ext, int k
         aa = sp.agent[sa];
         if (sb >= 0) ab = sp.agent[sb];
       }
+      if (!in_range(aa.x, w.ncells, w.err)) aa.x = 0;  // check builds only (recorded, then harmless)
+      if (sb >= 0 && !in_range(ab.x, w.ncells, w.err)) ab.x = 0;
       const u64 ca = claim[aa.x];
       const u64 cb = sb >= 0 ? claim[ab.x] : kNoKey;
       u32 r = count_one<S>(w, t, sa, aa, ca, gain, Tr, regrowth);
@@ -496,12 +499,14 @@ __device__ __forceinline__ void p_ranks(const WorldDev& w, int ext, int kseg, u3
       while (fr && rf < P) {  // only the first P free slots can receive a child
         const int jj = __ffs(fr) - 1;
         fr &= fr - 1;
-        sp.freel[rf++] = base + jj;
+        if (in_range(rf, sp.cap, w.err)) sp.freel[rf] = base + jj;
+        ++rf;
       }
       while (par) {
         const int jj = __ffs(par) - 1;
         par &= par - 1;
-        sp.parents[rp++] = base + jj;
+        if (in_range(rp, sp.cap, w.err)) sp.parents[rp] = base + jj;
+        ++rp;
       }
     }
     cf += tf;
@@ -593,12 +598,14 @@ __device__ __forceinline__ void rank_phase(const WorldDev& w, int ext, int kseg,
     while (fr && rf < P) {  // only the first P free slots can receive a child
       const int jj = __ffs(fr) - 1;
       fr &= fr - 1;
-      sp.freel[rf++] = base + jj;
+      if (in_range(rf, sp.cap, w.err)) sp.freel[rf] = base + jj;
+      ++rf;
     }
     while (par) {
       const int jj = __ffs(par) - 1;
       par &= par - 1;
-      sp.parents[rp++] = base + jj;
+      if (in_range(rp, sp.cap, w.err)) sp.parents[rp] = base + jj;
+      ++rp;
     }
   }
   __syncthreads();  // s_pre and s_red are reused
@@ -611,6 +618,7 @@ __device__ __forceinline__ void p_births(const WorldDev& w, int t, int r, int F,
   for (int i = blockIdx.x + gridDim.x * threadIdx.x; i < r; i += gridDim.x * kPT) {
     const int p = sp.parents[i];
     const int slot = i < F ? sp.freel[i] : ext + (i - F);
+    if (!in_range(p, sp.cap, w.err) || !in_range(slot, sp.cap, w.err)) continue;
     const int4 pa = sp.agent[p];
     const int half = pa.y >> 1;
     sp.agent[p].y = pa.y - half;
@@ -653,7 +661,7 @@ __device__ __forceinline__ FirstBirth births_prefetch(const WorldDev& w, const B
 template <int S>
 __device__ __forceinline__ void births_finish(const WorldDev& w, int t, const Births& b, FirstBirth f) {
   const SpeciesDev& sp = w.sp[S];
-  if (f.p >= 0) {
+  if (f.p >= 0 && in_range(f.p, sp.cap, w.err) && in_range(f.slot, sp.cap, w.err)) {
     const int i = blockIdx.x + gridDim.x * threadIdx.x;
     const int4 pa = sp.agent[f.p];
     const int half = pa.y >> 1;
@@ -665,6 +673,7 @@ __device__ __forceinline__ void births_finish(const WorldDev& w, int t, const Bi
   for (int i = blockIdx.x + gridDim.x * (threadIdx.x + kPT); i < b.r; i += gridDim.x * kPT) {
     const int p = sp.parents[i];
     const int slot = i < b.F ? sp.freel[i] : b.ext + (i - b.F);
+    if (!in_range(p, sp.cap, w.err) || !in_range(slot, sp.cap, w.err)) continue;
     const int4 pa = sp.agent[p];
     const int half = pa.y >> 1;
     sp.agent[p].y = pa.y - half;

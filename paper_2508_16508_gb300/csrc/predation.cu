@@ -56,6 +56,7 @@ __global__ void __launch_bounds__(kPredThreads) k_move(WorldDev w, abm_step_stat
       if (!a4[j]) continue;
       const int slot = 4 * q + j;
       int4 ag = sp.agent[slot];
+      if (!in_range(ag.x, w.ncells, w.err)) continue;  // check builds: a cell outside the lattice
       if (S == 0) w.victim[ag.x] = kNoKey;  // last step's victim entry for this cell
       const u32 dir = draw(w.seed, w.model, (u32)t, (u32)slot, ABM_P_MOVE, (u32)S) >> 29;
       const int cell = step_cell(ag.x, L, dir);
@@ -113,6 +114,7 @@ __global__ void __launch_bounds__(kPredThreads) k_scan(WorldDev w) {
       }
       int4 ag = sp.agent[slot];
       const int cell = ag.x;
+      if (!in_range(cell, w.ncells, w.err)) continue;  // check builds only
       u64* claim = S == 0 ? w.gclaim : w.wclaim;
       const u64 cl = claim[cell];
       if (cl != kNoKey && (u32)cl == (u32)slot) {
@@ -124,7 +126,7 @@ __global__ void __launch_bounds__(kPredThreads) k_scan(WorldDev w) {
           ++grass;
         } else {
           const u64 v = w.victim[cell];
-          w.sp[0].active[(u32)v] = 0;
+          if (in_range((u32)v, w.sp[0].cap, w.err)) w.sp[0].active[(u32)v] = 0;
           w.victim[cell] = kNoKey;
           ++eaten;
         }
@@ -152,10 +154,13 @@ __global__ void __launch_bounds__(kPredThreads) k_scan(WorldDev w) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       if ((fr >> j) & 1u) {
-        if ((int)rf < bound) sp.freel[rf] = base + j;
+        if ((int)rf < bound && in_range(rf, sp.cap, w.err)) sp.freel[rf] = base + j;
         ++rf;
       }
-      if ((par >> j) & 1u) sp.parents[rp++] = base + j;
+      if ((par >> j) & 1u) {
+        if (in_range(rp, sp.cap, w.err)) sp.parents[rp] = base + j;
+        ++rp;
+      }
     }
     if (died) reinterpret_cast<int4*>(sp.active)[base >> 2] = make_int4(a4[0], a4[1], a4[2], a4[3]);
   }
@@ -181,6 +186,7 @@ __global__ void __launch_bounds__(kPredThreads) k_births(WorldDev w, abm_step_st
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < r; i += gridDim.x * blockDim.x) {
     const int p = sp.parents[i];
     const int slot = i < Fin ? sp.freel[i] : ext + (i - Fin);
+    if (!in_range(p, sp.cap, w.err) || !in_range(slot, sp.cap, w.err)) continue;
     const int4 pa = sp.agent[p];
     const int half = pa.y >> 1;
     sp.agent[p].y = pa.y - half;
@@ -489,7 +495,10 @@ extern "C" abm_status abm_create(const abm_config* cfg, void* stream, abm_world*
   w->engine = ABM_ENGINE_PERSISTENT;
   w->pgrid = std::min(w->pgrid_max, num_sms() * 2);
   k_world_init<<<num_sms() * 4, 256, 0, st>>>(d, cfg->n0[0], cfg->n0[1]);
-  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
+  for (int s = 0; s < 2; ++s)  // check builds: canaries past the capacity
+    if (slab_canary_fill(reinterpret_cast<int32_t*>(d.sp[s].agent), 4, d.sp[s].cap, w->cap_pad[s], st) != ABM_OK)
+      ok = false;
+  if (!ok || cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
     world_free(w);
     return ABM_ERR_CUDA;
   }
@@ -642,10 +651,15 @@ extern "C" abm_status abm_world_tune(abm_world* w, int32_t engine, int32_t ctas_
 
 extern "C" abm_status abm_world_check(abm_world* w, void* stream) {
   if (!w) return ABM_ERR_ARG;
+  for (int s = 0; s < 2; ++s) {
+    const abm_status e = canary_check(w->d.sp[s].active, reinterpret_cast<const int32_t*>(w->d.sp[s].agent), 4,
+                                      w->d.sp[s].cap, w->cap_pad[s], w->d.err, (cudaStream_t)stream);
+    if (e != ABM_OK) return e;
+  }
   ABM_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
   int err = 0;
   ABM_CUDA_TRY(cudaMemcpy(&err, w->d.err, sizeof(int), cudaMemcpyDeviceToHost));
-  return err ? ABM_ERR_DEVICE_TIMEOUT : ABM_OK;
+  return ABM_ERR_OF(err);
 }
 
 extern "C" abm_status abm_read_agents(abm_world* w, int32_t species, int32_t which, int32_t* dst, void* stream) {

@@ -366,6 +366,7 @@ __device__ __forceinline__ void move_staged(const ScanArgs& a, const int* stage,
       slot[u] = -1;
       if (i < n) {
         slot[u] = stage[i];
+        if (!in_range(slot[u], a.s.cap, a.s.err)) slot[u] = -1;
         ld_v8_nc(rec + (size_t)(r0 + i) * 8, r[u]);
       }
     }
@@ -556,6 +557,7 @@ __device__ __forceinline__ void move_rows_v8(const ScanArgs& a, const int32_t* r
       slot[u] = -1;
       if (j < j1) {
         slot[u] = list[j];
+        if (!in_range(slot[u], s.cap, s.err)) slot[u] = -1;
         ld_v8_nc(rec + (size_t)(IDX ? s.rec_idx[j] : j) * 8, r[u]);
       }
     }
@@ -691,6 +693,26 @@ __global__ void __launch_bounds__(256, 2) k_apply(ScanArgs a) {
 }
 
 // --------------------------------------------------------------------------
+// check builds: the fields past the capacity hold the canary, the live flags
+// there stay 0; k_canary_check records kErrCheck if either changed
+__global__ void k_canary_fill(int32_t* fields, int Fp, int cap, int n_pad) {
+  const long long n = (long long)(n_pad - cap) * Fp;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    fields[(long long)cap * Fp + i] = kCanary;
+}
+
+__global__ void k_canary_check(const int32_t* active, const int32_t* fields, int Fp, int cap, int n_pad, int* err) {
+  const long long n = (long long)(n_pad - cap) * Fp;
+  bool bad = false;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    bad |= fields[(long long)cap * Fp + i] != kCanary;
+  for (int i = cap + blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += gridDim.x * blockDim.x)
+    bad |= active[i] != 0;
+  if (bad) atomicCAS(err, 0, kErrCheck);
+}
+
+__global__ void k_check_index(long long i, long long n, int* err) { in_range(i, n, err); }
+
 __global__ void k_slab_init(SlabDev s, int init, int n_pad) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += gridDim.x * blockDim.x) {
     const bool inside = i < s.cap;
@@ -762,11 +784,12 @@ extern "C" const char* abm_strerror(abm_status st) {
     case ABM_ERR_OVERFLOW: return "more agents asked for a slot than were free";
     case ABM_ERR_STATE: return "operation not valid for this handle";
     case ABM_ERR_TOO_LARGE: return "size beyond the fixed maximum of this entry point";
+    case ABM_ERR_CHECK: return "check build: an index out of range or a damaged canary was recorded";
   }
   return "unknown status";
 }
 
-extern "C" int32_t abm_version(void) { return 100; }
+extern "C" int32_t abm_version(void) { return kCheck ? -101 : 101; }
 
 static void slab_free(abm_slab* s) {
   if (!s->view) {
@@ -880,6 +903,7 @@ extern "C" abm_status abm_slab_create(int32_t capacity, int32_t n_fields, uint32
   }
   k_slab_init<<<num_sms() * 4, 256, 0, st>>>(s->d, init, s->n_pad);
   k_count_live<<<num_sms() * 4, 256, 0, st>>>(s->d);
+  if (kCheck) k_canary_fill<<<num_sms() * 4, 256, 0, st>>>(s->d.fields, s->d.Fp, s->d.cap, s->n_pad);
   if (cudaGetLastError() != cudaSuccess) {
     slab_free(s);
     return ABM_ERR_CUDA;
@@ -890,10 +914,49 @@ extern "C" abm_status abm_slab_create(int32_t capacity, int32_t n_fields, uint32
 
 extern "C" abm_status abm_slab_check(abm_slab* s, void* stream) {
   if (!s) return ABM_ERR_ARG;
+  // check builds: the padding of a slab's own arrays (a world's view has none of its own)
+  if (kCheck && !s->view && s->n_pad > s->d.cap) {
+    k_canary_check<<<num_sms() * 4, 256, 0, (cudaStream_t)stream>>>(s->d.active, s->d.fields, s->d.Fp, s->d.cap,
+                                                                    s->n_pad, s->d.err);
+    ABM_LAUNCH_CHECK();
+  }
   ABM_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
   int err = 0;
   ABM_CUDA_TRY(cudaMemcpy(&err, s->d.err, sizeof(int), cudaMemcpyDeviceToHost));
-  return err ? ABM_ERR_DEVICE_TIMEOUT : ABM_OK;
+  return ABM_ERR_OF(err);
+}
+
+abm_status abm::slab_canary_fill(int32_t* fields, int Fp, int cap, int n_pad, cudaStream_t st) {
+  if (!kCheck || n_pad <= cap) return ABM_OK;
+  k_canary_fill<<<num_sms() * 4, 256, 0, st>>>(fields, Fp, cap, n_pad);
+  ABM_LAUNCH_CHECK();
+  return ABM_OK;
+}
+
+abm_status abm::canary_check(const int32_t* active, const int32_t* fields, int Fp, int cap, int n_pad, int* err,
+                             cudaStream_t st) {
+  if (!kCheck || n_pad <= cap) return ABM_OK;
+  k_canary_check<<<num_sms() * 4, 256, 0, st>>>(active, fields, Fp, cap, n_pad, err);
+  ABM_LAUNCH_CHECK();
+  return ABM_OK;
+}
+
+extern "C" abm_status abm_diag_check_index(int64_t i, int64_t n, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  int* err = nullptr;
+  ABM_CUDA_TRY(cudaMalloc(&err, sizeof(int)));
+  abm_status rc = ABM_OK;
+  int h = 0;
+  if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) rc = ABM_ERR_CUDA;
+  if (rc == ABM_OK) {
+    k_check_index<<<1, 1, 0, st>>>((long long)i, (long long)n, err);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      rc = ABM_ERR_CUDA;
+  }
+  cudaFree(err);
+  return rc != ABM_OK ? rc : ABM_ERR_OF(h);
 }
 
 extern "C" abm_status abm_slab_arrays(abm_slab* s, int32_t** active, int32_t** fields, int32_t* stride) {

@@ -48,4 +48,9 @@ namespace abm {
 // slab_free_view, never by abm_slab_destroy.
 abm_status slab_create_view(int cap, u32 seed, u32 model, int32_t* active, int32_t* fields, abm_slab** out);
 void slab_free_view(abm_slab* s);
+// check builds: canaries in the fields past the capacity (fields: n_pad x Fp)
+abm_status slab_canary_fill(int32_t* fields, int Fp, int cap, int n_pad, cudaStream_t st);
+// check builds: records kErrCheck in *err if the canaries past the capacity changed
+abm_status canary_check(const int32_t* active, const int32_t* fields, int Fp, int cap, int n_pad, int* err,
+                        cudaStream_t st);
 }  // namespace abm

@@ -241,6 +241,8 @@ static abm_status sort_scratch(abm_slab* s, SortScratch** out) {
   // rows past the capacity are never gathered: keep them as the slab keeps its own
   ok = ok && cudaMemset(p->fields, 0, sizeof(int32_t) * (size_t)p->n_pad * p->Fp) == cudaSuccess;
   ok = ok && cudaMemset(p->active, 0, sizeof(int32_t) * (size_t)p->n_pad) == cudaSuccess;
+  if (kCheck && ok)  // check builds: the spare arrays carry the canaries too (they become the slab's)
+    ok = slab_canary_fill(p->fields, p->Fp, s->d.cap, p->n_pad, 0) == ABM_OK && cudaDeviceSynchronize() == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     sort_scratch_free(p);

@@ -59,3 +59,19 @@ def test_host_only_calls(lib_path):
     assert L.abm_lob_add(1, 8, None, None, None, None, None, None, None, -1, None, None) == abm.ERR_ARG
     assert L.abm_lob_add(1, 8, None, None, None, None, None, None, None, 0, None, None) == abm.ERR_ARG
     assert L.abm_lob_tune(3) == abm.ERR_ARG and L.abm_lob_tune(0) == abm.OK
+
+
+def test_check_build_exports_the_same_functions():
+    """The check build (-DABM_CHECK: index tests and canaries) compiles from the
+    same sources and exports the same entry points; its version is negative."""
+    from paper_2508_16508_gb300 import build
+    path = build.build(check=True)
+    assert path.endswith("libabm_check.so")
+    L = C.CDLL(path)
+    missing = sorted(n for n in declared() if not hasattr(L, n))
+    assert not missing, missing
+    L.abm_version.restype = C.c_int32
+    assert L.abm_version() < 0
+    L.abm_strerror.restype = C.c_char_p
+    L.abm_strerror.argtypes = [C.c_int32]
+    assert b"check build" in L.abm_strerror(8)
