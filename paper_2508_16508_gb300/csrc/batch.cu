@@ -11,6 +11,7 @@
 // the same results, and the capacity sweep is what a tighter capacity speeds
 // up. A CTA never waits for another CTA.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <new>
 #include <numeric>
@@ -19,6 +20,8 @@
 #include "pred_rules.cuh"
 
 namespace abm {
+
+constexpr int kBatchLiveWordsMax = 1 << 15;  // 128 KiB: live-flag bitmask of up to 1Mi slots per CTA
 
 struct BModel {
   int side, ncells;
@@ -102,9 +105,13 @@ __device__ __forceinline__ void move_agent(const BatchDev& b, const MCtx& c, int
 
 template <int T>
 __device__ __forceinline__ void b_move(const BatchDev& b, MCtx& c, int S, int sweep, int t, unsigned short* s_list,
-                                       u64* s_warp) {
+                                       u64* s_warp, u32* s_live, int live_words) {
   const int32_t* act = b.active[S] + c.m.oa[S];
   const int4* ag = b.agent[S] + c.m.oa[S];
+  // the sweep's live flags also go into a shared-memory bitmask (when it fits)
+  // that the scan of the same species reads instead of the flags: nothing
+  // changes this species' flags between its move and its scan
+  const bool keep = sweep <= 32 * live_words;
   // per chunk: four 128-bit loads of live flags per thread (int4 q0 + u*T),
   // the live slots listed, then two agents in flight per thread
   for (int c0 = 0; c0 < sweep; c0 += 16 * T) {
@@ -118,6 +125,18 @@ __device__ __forceinline__ void b_move(const BatchDev& b, MCtx& c, int S, int sw
       m |= ((u32)(a.x != 0) | ((u32)(a.y != 0) << 1) | ((u32)(a.z != 0) << 2) | ((u32)(a.w != 0) << 3)) << (4 * u);
     }
     // bit 4u + j of m is slot 4 (q0 + u T) + j = c0 + 4 tid + 4 u T + j
+    if (keep) {
+      // the nibbles of 8 neighbouring threads make one bitmask word (slots 4 (q0 + u T) .. + 32)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        u32 v = ((m >> (4 * u)) & 0xFu) << (4 * (threadIdx.x & 7));
+        v |= __shfl_xor_sync(0xFFFFFFFFu, v, 1);
+        v |= __shfl_xor_sync(0xFFFFFFFFu, v, 2);
+        v |= __shfl_xor_sync(0xFFFFFFFFu, v, 4);
+        const int wd = (c0 + 4 * (threadIdx.x + u * T)) >> 5;
+        if ((threadIdx.x & 7) == 0 && wd < live_words) s_live[wd] = v;
+      }
+    }
     if (!__syncthreads_or(m != 0)) continue;  // no live agent in the chunk
     u32 ex, ex2, tot, tot2;
     block_scan2<T>((u32)__popc(m), 0u, ex, ex2, tot, tot2, s_warp);
@@ -186,21 +205,27 @@ __device__ __forceinline__ u32 scan_agent(const BatchDev& b, const MCtx& c, int 
 // the chunk are listed and shared by all threads.
 template <int T>
 __device__ __forceinline__ void b_scan(const BatchDev& b, MCtx& c, int S, int sweep, int t, u64* s_warp,
-                                       int* s_acc, unsigned short* s_list, u32* s_par) {
+                                       int* s_acc, unsigned short* s_list, u32* s_par, const u32* s_live,
+                                       int live_words) {
   const int32_t* act = b.active[S] + c.m.oa[S];
   int32_t* plist = b.plist[S] + c.m.oa[S];
   int32_t* flist = b.flist[S] + c.m.oa[S];
   const int bound = c.n_active[S];
+  const bool kept = sweep <= 32 * live_words;  // the move left this sweep's flags in s_live
   int starved = 0, won = 0;
   u32 pf = 0, pp = 0;
   for (int c0 = 0; c0 < sweep; c0 += 16 * T) {
     const int base = c0 + 16 * threadIdx.x;
     u32 m = 0, valid = 0;
+    if (kept) {
+      if (base < sweep) m = (s_live[base >> 5] >> (base & 16)) & 0xFFFFu;
+    } else {
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      int4 q = make_int4(0, 0, 0, 0);
-      if (base + 4 * v < sweep) q = reinterpret_cast<const int4*>(act)[(base >> 2) + v];
-      m |= ((u32)(q.x != 0) | ((u32)(q.y != 0) << 1) | ((u32)(q.z != 0) << 2) | ((u32)(q.w != 0) << 3)) << (4 * v);
+      for (int v = 0; v < 4; ++v) {
+        int4 q = make_int4(0, 0, 0, 0);
+        if (base + 4 * v < sweep) q = reinterpret_cast<const int4*>(act)[(base >> 2) + v];
+        m |= ((u32)(q.x != 0) | ((u32)(q.y != 0) << 1) | ((u32)(q.z != 0) << 2) | ((u32)(q.w != 0) << 3)) << (4 * v);
+      }
     }
 #pragma unroll
     for (int j = 0; j < 16; ++j) valid |= (u32)(base + j < sweep) << j;
@@ -300,7 +325,8 @@ __device__ __forceinline__ void b_count_births(const BatchDev& b, MCtx& c, int S
 }
 
 template <int T>
-__global__ void __launch_bounds__(T) k_batch_run(BatchDev b, int nsteps, int sweep_extent) {
+__global__ void __launch_bounds__(T) k_batch_run(BatchDev b, int nsteps, int sweep_extent, int live_words) {
+  extern __shared__ u32 s_live[];  // [live_words]: one species' live flags, move -> scan
   __shared__ MCtx c;
   __shared__ u64 s_warp[T / 32 + 1];
   __shared__ int s_acc[4];
@@ -340,9 +366,9 @@ __global__ void __launch_bounds__(T) k_batch_run(BatchDev b, int nsteps, int swe
       const int sw0 = sweep_extent ? c.extent[0] : c.m.cap[0];
       __syncthreads();
       // sheep: move + grass claims; eat, select, die, compact
-      b_move<T>(b, c, 0, sw0, t, s_list, s_warp);
+      b_move<T>(b, c, 0, sw0, t, s_list, s_warp, s_live, live_words);
       __syncthreads();
-      b_scan<T>(b, c, 0, sw0, t, s_warp, s_acc, s_list, s_par);
+      b_scan<T>(b, c, 0, sw0, t, s_warp, s_acc, s_list, s_par, s_live, live_words);
       __syncthreads();
       const int avail0 = c.F[0] + (sweep_extent ? c.m.cap[0] - c.extent[0] : 0);
       const int r0 = min(c.P[0], avail0);
@@ -351,7 +377,7 @@ __global__ void __launch_bounds__(T) k_batch_run(BatchDev b, int nsteps, int swe
       // claim only needs the cell to hold a live sheep; every newborn lamb
       // sits with its live parent)
       b_births<T>(b, c, 0, r0, t);
-      b_move<T>(b, c, 1, sw1, t, s_list, s_warp);
+      b_move<T>(b, c, 1, sw1, t, s_list, s_warp, s_live, live_words);
       __syncthreads();
       if (threadIdx.x == 0) {
         b_count_births(b, c, 0, r0, s_acc[0], avail0);
@@ -360,7 +386,7 @@ __global__ void __launch_bounds__(T) k_batch_run(BatchDev b, int nsteps, int swe
         s_acc[0] = s_acc[1] = 0;
       }
       __syncthreads();
-      b_scan<T>(b, c, 1, sw1, t, s_warp, s_acc, s_list, s_par);
+      b_scan<T>(b, c, 1, sw1, t, s_warp, s_acc, s_list, s_par, s_live, live_words);
       __syncthreads();
       const int avail1 = c.F[1] + (sweep_extent ? c.m.cap[1] - c.extent[1] : 0);
       const int r1 = min(c.P[1], avail1);
@@ -665,13 +691,32 @@ extern "C" abm_status abm_batch_run(abm_batch* b, int32_t nsteps, int32_t sweep,
   cudaStream_t st = (cudaStream_t)stream;
   const int grid = std::max(1, std::min(b->d.nmodels, num_sms() * b->ctas_per_sm));
   const int ext = sweep == ABM_SWEEP_EXTENT;
+  // the live-flag bitmask of the largest sweep of the batch (at most 1M slots:
+  // 128 KiB of shared memory per CTA; larger models read their flags twice)
+  int live_words = 0;
+  for (const BModel& m : b->models) live_words = std::max(live_words, (std::max(m.cap[0], m.cap[1]) + 31) / 32);
+  live_words = std::min(live_words, kBatchLiveWordsMax);
+  const size_t smem = sizeof(u32) * (size_t)live_words;
+  static std::atomic<unsigned long long> attr[4];
   for (int done = 0; done < nsteps;) {
     const int s = std::min(nsteps - done, b->steps_per_launch);
     switch (b->threads) {
-      case 128: k_batch_run<128><<<grid, 128, 0, st>>>(b->d, s, ext); break;
-      case 256: k_batch_run<256><<<grid, 256, 0, st>>>(b->d, s, ext); break;
-      case 512: k_batch_run<512><<<grid, 512, 0, st>>>(b->d, s, ext); break;
-      default: k_batch_run<1024><<<grid, 1024, 0, st>>>(b->d, s, ext); break;
+      case 128:
+        ABM_CUDA_TRY(smem_attr_once(k_batch_run<128>, (int)kBatchLiveWordsMax * 4, attr[0]));
+        k_batch_run<128><<<grid, 128, smem, st>>>(b->d, s, ext, live_words);
+        break;
+      case 256:
+        ABM_CUDA_TRY(smem_attr_once(k_batch_run<256>, (int)kBatchLiveWordsMax * 4, attr[1]));
+        k_batch_run<256><<<grid, 256, smem, st>>>(b->d, s, ext, live_words);
+        break;
+      case 512:
+        ABM_CUDA_TRY(smem_attr_once(k_batch_run<512>, (int)kBatchLiveWordsMax * 4, attr[2]));
+        k_batch_run<512><<<grid, 512, smem, st>>>(b->d, s, ext, live_words);
+        break;
+      default:
+        ABM_CUDA_TRY(smem_attr_once(k_batch_run<1024>, (int)kBatchLiveWordsMax * 4, attr[3]));
+        k_batch_run<1024><<<grid, 1024, smem, st>>>(b->d, s, ext, live_words);
+        break;
     }
     ABM_LAUNCH_CHECK();
     done += s;
