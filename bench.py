@@ -373,18 +373,21 @@ def batched_leg(torch, engine, capacity, autotune, abm, hbm_peak, n_models=None,
     fixed = workloads.fixed_caps(tab["side"])[:n_models]
     models = [dict(side=int(tab["side"][i]), seed=B["philox_seed"], model=i, params=tab["params"][i],
                    cap=fixed[i], n0=tab["n0"][i]) for i in range(n_models)]
-    default = {"threads": 512, "ctas_per_sm": 2}
+    default = {"threads": 512, "ctas_per_sm": 2, "models_per_cta": 1}
     tf = autotune.tune_batch(models, steps, abm.SWEEP_CAPACITY) if tune else default
-    th, cps = tf["threads"], tf["ctas_per_sm"]
-    trials = lambda tt: [[x["threads"], x["ctas_per_sm"], round(x["ms"], 2)] for x in tt.get("trials", [])]
+    th, cps, g = tf["threads"], tf["ctas_per_sm"], tf.get("models_per_cta", 1)
+    trials = lambda tt: [[x["threads"], x["ctas_per_sm"], x.get("models_per_cta", 1), round(x["ms"], 2)]  # noqa: E731
+                         for x in tt.get("trials", [])]
+    shape = lambda tt: (f"{tt['threads']} threads x {tt['ctas_per_sm']} CTAs/SM x {tt.get('models_per_cta', 1)} "  # noqa: E731
+                        f"models/CTA" + (" (autotuned)" if tune else ""))
     out = {"workload": B["name"] if n_models == B["n_models"] and steps == B["steps"]
            else f"{n_models} models of {B['name']}, {steps} steps",
            "models": n_models, "steps": steps,
-           "launch_fixed": f"{th} threads x {cps} CTAs/SM" + (" (autotuned)" if tune else ""),
-           "tune_trials_fixed_ms": trials(tf)}
+           "launch_fixed": shape(tf),
+           "tune_trials_fixed_ms": trials(tf), "tune_trial_columns": ["threads", "ctas_per_sm", "models_per_cta", "ms"]}
     # plain fixed capacity (one persistent launch for all 500 steps)
     b = engine.Batch(models)
-    b.tune(th, cps)
+    b.tune(th, cps, models_per_cta=g)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     b.run(steps, sweep=abm.SWEEP_CAPACITY)
@@ -408,7 +411,7 @@ def batched_leg(torch, engine, capacity, autotune, abm, hbm_peak, n_models=None,
     # the same models with extent sweeps (a stronger plain baseline: placeholders past
     # the highest slot ever used are never visited)
     b = engine.Batch(models)
-    b.tune(th, cps)
+    b.tune(th, cps, models_per_cta=g)
     e0.record()
     b.run(steps, sweep=abm.SWEEP_EXTENT)
     e1.record()
@@ -431,9 +434,10 @@ def batched_leg(torch, engine, capacity, autotune, abm, hbm_peak, n_models=None,
     # one small learned-capacity run with a rerun first, so that the timed runs
     # do not pay the first call's one-time costs (module loading, first allocations)
     capacity.run_learned(models[:8], np.maximum(np.asarray(tab["n0"][:8]), 1), fixed[:8], 20)
-    out["launch_learned"] = f"{tl['threads']} threads x {tl['ctas_per_sm']} CTAs/SM" + (" (autotuned)" if tune else "")
+    out["launch_learned"] = shape(tl)
     out["tune_trials_learned_ms"] = trials(tl)
-    res = capacity.run_learned(models, learned, fixed, steps, threads=tl["threads"], ctas_per_sm=tl["ctas_per_sm"])
+    res = capacity.run_learned(models, learned, fixed, steps, threads=tl["threads"], ctas_per_sm=tl["ctas_per_sm"],
+                               models_per_cta=tl.get("models_per_cta", 1))
     t_learned = res["ms_learned"] + res["ms_rerun"] + t_mlp
     out["_digest_learned"] = res["digest"]
     n_over = np.array([max(c["overflow"]) for c in res["counters"]])
@@ -451,7 +455,7 @@ def batched_leg(torch, engine, capacity, autotune, abm, hbm_peak, n_models=None,
     # learned capacities (memory) with extent sweeps (work): compared with the
     # extent-sweep fixed run, the fair plain baseline for it
     res = capacity.run_learned(models, learned, fixed, steps, sweep=abm.SWEEP_EXTENT, threads=tl["threads"],
-                               ctas_per_sm=tl["ctas_per_sm"])
+                               ctas_per_sm=tl["ctas_per_sm"], models_per_cta=tl.get("models_per_cta", 1))
     t_le = res["ms_learned"] + res["ms_rerun"] + t_mlp
     out["learned_extent_sweep"] = {"ms": t_le, "ms_run": res["ms_learned"], "ms_rerun": res["ms_rerun"],
                                    "agent_steps_per_s": agents / (t_le * 1e-3),

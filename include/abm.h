@@ -503,6 +503,13 @@ abm_status abm_batch_destroy(abm_batch* b);
  * (a run of nsteps is split into ceil(nsteps / steps_per_launch) launches,
  * each replayable in a CUDA graph). Results never depend on it. */
 abm_status abm_batch_tune(abm_batch* b, int32_t threads, int32_t ctas_per_sm, int32_t steps_per_launch);
+/* Launch shape: models run at once by one CTA (1, 2 or 4), each on a group of
+ * threads / models_per_cta threads with its own barrier, so that small models
+ * need not occupy a whole CTA; the groups take models from the same queue
+ * (largest first). Groups must keep at least 128 threads (ABM_ERR_ARG
+ * otherwise; abm_batch_tune resets it to 1 when a new CTA size would break
+ * that). Results never depend on it. Host only. */
+abm_status abm_batch_models_per_cta(abm_batch* b, int32_t models_per_cta);
 /* Advance every model by nsteps (asynchronous on `stream`). */
 abm_status abm_batch_run(abm_batch* b, int32_t nsteps, int32_t sweep, void* stream);
 /* Host copy of every model's counters (out: host abm_batch_counters[n]; synchronises `stream`). */

@@ -5,7 +5,7 @@ runs each candidate on a short, representative slice of the real work, keeps
 the fastest, and records it in a JSON cache keyed by the device name and a
 signature of the workload. Tuned knobs:
 
-  batched runs    CTA size (threads), CTAs per SM, steps per launch
+  batched runs    CTA size (threads), CTAs per SM, models per CTA, steps per launch
   large worlds    engine (persistent / per-phase kernels), CTAs per SM
   slab passes     CTA size, CTAs per SM of the fused selective-update call
 """
@@ -62,7 +62,7 @@ def _time(fn) -> float:
 
 def tune_batch(models: list, steps: int, sweep: int, trial_steps: int | None = None, rounds: int = 1,
                use_cache: bool = True, **_ignored) -> dict:
-    """Pick (threads, ctas_per_sm) for a batch of models. By default every
+    """Pick (threads, ctas_per_sm, models_per_cta) for a batch of models. By default every
     candidate runs the whole batch for all `steps` from the initial state, so
     each times exactly the work it will be chosen for (populations change a
     lot over a run, so a short slice of it misjudges the shapes); a smaller
@@ -71,36 +71,39 @@ def tune_batch(models: list, steps: int, sweep: int, trial_steps: int | None = N
     sig = {"n": len(models), "steps": steps, "sweep": sweep,
            "sides": np.histogram([m["side"] for m in models], bins=8)[0].tolist(),
            "cap": int(sum(int(m["cap"][0]) + int(m["cap"][1]) for m in models))}
-    key = _key("batch", sig)
+    key = _key("batch2", sig)
     if use_cache:
         hit = _load().get(key)
         if hit:
             return hit
-    # shapes whose CTAs can all be resident at 64 registers per thread
-    cands = [(256, 1), (256, 2), (256, 4), (512, 1), (512, 2), (1024, 1)]
+    # shapes whose CTAs can all be resident at 64 registers per thread: CTA
+    # size, CTAs per SM, models per CTA (groups of at least 128 threads)
+    cands = [(256, 1, 1), (256, 2, 1), (256, 4, 1), (512, 1, 1), (512, 2, 1), (1024, 1, 1),
+             (256, 4, 2), (512, 2, 2), (512, 2, 4), (1024, 1, 2), (1024, 1, 4)]
     acc = {cnd: 0.0 for cnd in cands}
     if trial_steps is None or trial_steps >= steps:
         for _ in range(rounds):
-            for th, cps in cands:
+            for th, cps, g in cands:
                 b = engine.Batch(models)
-                b.tune(th, cps)
-                acc[(th, cps)] += _time(lambda: b.run(steps, sweep=sweep))
+                b.tune(th, cps, models_per_cta=g)
+                acc[(th, cps, g)] += _time(lambda: b.run(steps, sweep=sweep))
                 b.check()
                 del b
     else:
         b = engine.Batch(models)
         b.run(2, sweep=sweep)
         for _ in range(rounds):
-            for th, cps in cands:
-                b.tune(th, cps)
-                acc[(th, cps)] += _time(lambda: b.run(trial_steps, sweep=sweep))
+            for th, cps, g in cands:
+                b.tune(th, cps, models_per_cta=g)
+                acc[(th, cps, g)] += _time(lambda: b.run(trial_steps, sweep=sweep))
         b.check()
         del b
     torch.cuda.empty_cache()
-    results = sorted((ms, th, cps) for (th, cps), ms in acc.items())
-    ms, th, cps = results[0]
-    best = {"threads": th, "ctas_per_sm": cps, "steps_per_launch": max(steps, 1),
-            "trial_ms": ms, "trials": [{"threads": t, "ctas_per_sm": c, "ms": m} for m, t, c in results],
+    results = sorted((ms, th, cps, g) for (th, cps, g), ms in acc.items())
+    ms, th, cps, g = results[0]
+    best = {"threads": th, "ctas_per_sm": cps, "models_per_cta": g, "steps_per_launch": max(steps, 1),
+            "trial_ms": ms,
+            "trials": [{"threads": t, "ctas_per_sm": c, "models_per_cta": gg, "ms": m} for m, t, c, gg in results],
             "tuned_at": time.strftime("%Y-%m-%dT%H:%M:%S")}
     _store(key, best)
     return best

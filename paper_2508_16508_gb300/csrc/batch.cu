@@ -64,25 +64,85 @@ struct MCtx {
   int n_start[2], P[2], F[2], starved[2], eaten, grass;
 };
 
+// Models per CTA: a CTA of N threads runs G models at once, each on a group
+// of T = N / G threads (thread gt of group g) with its own barrier -- the CTA
+// barrier when G = 1, else the named barrier 1 + g -- and its own shared arrays.
+template <int G>
+__device__ __forceinline__ void gsync(int g, int nthreads) {
+  if (G == 1) {
+    __syncthreads();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(nthreads) : "memory");
+  }
+}
+
+// gsync that also returns whether pred holds in any thread of the group
+template <int G>
+__device__ __forceinline__ int gsync_or(int g, int nthreads, int pred) {
+  if (G == 1) return __syncthreads_or(pred);
+  int r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.s32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n selp.s32 %0, 1, 0, q;\n}"
+      : "=r"(r)
+      : "r"(pred), "r"(1 + g), "r"(nthreads)
+      : "memory");
+  return r;
+}
+
+// exclusive scan of two counts (packed in one u64) over a group of T threads
+template <int T, int G>
+__device__ __forceinline__ void group_scan2(int g, int gt, u32 a, u32 b, u32& ex_a, u32& ex_b, u32& tot_a,
+                                            u32& tot_b, u64* s_warp /* [T / 32 + 1] */) {
+  constexpr int W = T / 32;
+  const int lane = gt & 31, warp = gt >> 5;
+  const u64 v = ((u64)a << 32) | b;
+  u64 incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u64 x = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= o) incl += x;
+  }
+  if (lane == 31) s_warp[warp] = incl;
+  gsync<G>(g, T);
+  if (warp == 0) {
+    const u64 w = lane < W ? s_warp[lane] : 0ull;
+    u64 wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const u64 x = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+      if (lane >= o) wi += x;
+    }
+    if (lane < W) s_warp[lane] = wi - w;
+    if (lane == W - 1) s_warp[W] = wi;
+  }
+  gsync<G>(g, T);
+  const u64 ex = s_warp[warp] + incl - v;
+  const u64 tot = s_warp[W];
+  ex_a = (u32)(ex >> 32);
+  ex_b = (u32)ex;
+  tot_a = (u32)(tot >> 32);
+  tot_b = (u32)tot;
+}
+
 // Live agents of a chunk of 16 * T slots, listed in shared memory (offsets
 // within the chunk, in the order of the threads' masks) so that all T threads
 // share the work whatever the chunk's density. m = the thread's 16-bit live
 // mask over slots base16[j]; returns the list's length.
-template <int T>
-__device__ __forceinline__ int chunk_list(u32 m, int first_off, int stride_off, unsigned short* s_list, u64* s_warp) {
+template <int T, int G>
+__device__ __forceinline__ int chunk_list(int g, int gt, u32 m, int first_off, int stride_off, unsigned short* s_list, u64* s_warp) {
   u32 ex, ex2, tot, tot2;
-  block_scan2<T>((u32)__popc(m), 0u, ex, ex2, tot, tot2, s_warp);
+  group_scan2<T, G>(g, gt, (u32)__popc(m), 0u, ex, ex2, tot, tot2, s_warp);
   u32 pos = ex;
   while (m) {
     const int j = __ffs(m) - 1;
     m &= m - 1;
     s_list[pos++] = (unsigned short)(first_off + j * stride_off);
   }
-  __syncthreads();
+  gsync<G>(g, T);
   return (int)tot;
 }
 
-template <int T>
+template <int T, int G>
 __device__ __forceinline__ void move_agent(const BatchDev& b, const MCtx& c, int S, int t, int slot, int4 a) {
   int4* ag = b.agent[S] + c.m.oa[S];
   u64* victim = b.victim + c.m.oc;
@@ -103,8 +163,8 @@ __device__ __forceinline__ void move_agent(const BatchDev& b, const MCtx& c, int
   }
 }
 
-template <int T>
-__device__ __forceinline__ void b_move(const BatchDev& b, MCtx& c, int S, int sweep, int t, unsigned short* s_list,
+template <int T, int G>
+__device__ __forceinline__ void b_move(int g, int gt, const BatchDev& b, MCtx& c, int S, int sweep, int t, unsigned short* s_list,
                                        u64* s_warp, u32* s_live, int live_words) {
   const int32_t* act = b.active[S] + c.m.oa[S];
   const int4* ag = b.agent[S] + c.m.oa[S];
@@ -115,7 +175,7 @@ __device__ __forceinline__ void b_move(const BatchDev& b, MCtx& c, int S, int sw
   // per chunk: four 128-bit loads of live flags per thread (int4 q0 + u*T),
   // the live slots listed, then two agents in flight per thread
   for (int c0 = 0; c0 < sweep; c0 += 16 * T) {
-    const int q0 = (c0 >> 2) + threadIdx.x;
+    const int q0 = (c0 >> 2) + gt;
     const int nq = (sweep + 3) >> 2;
     u32 m = 0;
 #pragma unroll
@@ -129,42 +189,42 @@ __device__ __forceinline__ void b_move(const BatchDev& b, MCtx& c, int S, int sw
       // the nibbles of 8 neighbouring threads make one bitmask word (slots 4 (q0 + u T) .. + 32)
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        u32 v = ((m >> (4 * u)) & 0xFu) << (4 * (threadIdx.x & 7));
+        u32 v = ((m >> (4 * u)) & 0xFu) << (4 * (gt & 7));
         v |= __shfl_xor_sync(0xFFFFFFFFu, v, 1);
         v |= __shfl_xor_sync(0xFFFFFFFFu, v, 2);
         v |= __shfl_xor_sync(0xFFFFFFFFu, v, 4);
-        const int wd = (c0 + 4 * (threadIdx.x + u * T)) >> 5;
-        if ((threadIdx.x & 7) == 0 && wd < live_words) s_live[wd] = v;
+        const int wd = (c0 + 4 * (gt + u * T)) >> 5;
+        if ((gt & 7) == 0 && wd < live_words) s_live[wd] = v;
       }
     }
-    if (!__syncthreads_or(m != 0)) continue;  // no live agent in the chunk
+    if (!gsync_or<G>(g, T, m != 0)) continue;  // no live agent in the chunk
     u32 ex, ex2, tot, tot2;
-    block_scan2<T>((u32)__popc(m), 0u, ex, ex2, tot, tot2, s_warp);
+    group_scan2<T, G>(g, gt, (u32)__popc(m), 0u, ex, ex2, tot, tot2, s_warp);
     {
       u32 pos = ex, mb = m;
       while (mb) {
         const int bit = __ffs(mb) - 1;
         mb &= mb - 1;
-        s_list[pos++] = (unsigned short)(4 * threadIdx.x + 4 * (bit >> 2) * T + (bit & 3));
+        s_list[pos++] = (unsigned short)(4 * gt + 4 * (bit >> 2) * T + (bit & 3));
       }
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < (int)tot; e += 2 * T) {
+    gsync<G>(g, T);
+    for (int e = gt; e < (int)tot; e += 2 * T) {
       const int sa = c0 + s_list[e];
       const int sb = e + T < (int)tot ? c0 + s_list[e + T] : -1;
       const int4 aa = ag[sa];
       int4 ab = make_int4(0, 0, 0, 0);
       if (sb >= 0) ab = ag[sb];
-      move_agent<T>(b, c, S, t, sa, aa);
-      if (sb >= 0) move_agent<T>(b, c, S, t, sb, ab);
+      move_agent<T, G>(b, c, S, t, sa, aa);
+      if (sb >= 0) move_agent<T, G>(b, c, S, t, sb, ab);
     }
-    __syncthreads();  // the list is rewritten by the next chunk
+    gsync<G>(g, T);  // the list is rewritten by the next chunk
   }
 }
 
 // eat (claim winners), select parents or die; returns bit 0 = parent, bit 1 =
 // died, bit 2 = ate
-template <int T>
+template <int T, int G>
 __device__ __forceinline__ u32 scan_agent(const BatchDev& b, const MCtx& c, int S, int t, int slot) {
   int32_t* act = b.active[S] + c.m.oa[S];
   int4* ag = b.agent[S] + c.m.oa[S];
@@ -203,8 +263,8 @@ __device__ __forceinline__ u32 scan_agent(const BatchDev& b, const MCtx& c, int 
 // slots and the parents (ranks by block scans, chunk by chunk). Thread i holds
 // the 16 contiguous slots 16 i.. of a chunk for the ranks; the live agents of
 // the chunk are listed and shared by all threads.
-template <int T>
-__device__ __forceinline__ void b_scan(const BatchDev& b, MCtx& c, int S, int sweep, int t, u64* s_warp,
+template <int T, int G>
+__device__ __forceinline__ void b_scan(int g, int gt, const BatchDev& b, MCtx& c, int S, int sweep, int t, u64* s_warp,
                                        int* s_acc, unsigned short* s_list, u32* s_par, const u32* s_live,
                                        int live_words) {
   const int32_t* act = b.active[S] + c.m.oa[S];
@@ -215,7 +275,7 @@ __device__ __forceinline__ void b_scan(const BatchDev& b, MCtx& c, int S, int sw
   int starved = 0, won = 0;
   u32 pf = 0, pp = 0;
   for (int c0 = 0; c0 < sweep; c0 += 16 * T) {
-    const int base = c0 + 16 * threadIdx.x;
+    const int base = c0 + 16 * gt;
     u32 m = 0, valid = 0;
     if (kept) {
       if (base < sweep) m = (s_live[base >> 5] >> (base & 16)) & 0xFFFFu;
@@ -233,23 +293,23 @@ __device__ __forceinline__ void b_scan(const BatchDev& b, MCtx& c, int S, int sw
     const u32 fr = ~m & valid;
     // a chunk without live agents whose free slots all rank past the free-list
     // bound only adds to the free count
-    if ((int)pf >= bound && !__syncthreads_or(m != 0)) {
+    if ((int)pf >= bound && !gsync_or<G>(g, T, m != 0)) {
       pf += (u32)min(16 * T, sweep - c0);
       continue;
     }
-    const int tot = chunk_list<T>(m, 16 * threadIdx.x, 1, s_list, s_warp);
-    for (int e = threadIdx.x; e < tot; e += T) {
+    const int tot = chunk_list<T, G>(g, gt, m, 16 * gt, 1, s_list, s_warp);
+    for (int e = gt; e < tot; e += T) {
       const int off = s_list[e];
-      const u32 r = scan_agent<T>(b, c, S, t, c0 + off);
+      const u32 r = scan_agent<T, G>(b, c, S, t, c0 + off);
       if (r & 1u) atomicOr(&s_par[off >> 5], 1u << (off & 31));
       starved += (r >> 1) & 1u;
       won += (r >> 2) & 1u;
     }
-    __syncthreads();
-    u32 par = (s_par[threadIdx.x >> 1] >> (16 * (threadIdx.x & 1))) & 0xFFFFu;
+    gsync<G>(g, T);
+    u32 par = (s_par[gt >> 1] >> (16 * (gt & 1))) & 0xFFFFu;
     u32 ex_f, ex_p, tot_f, tot_p;
-    block_scan2<T>(__popc(fr), __popc(par), ex_f, ex_p, tot_f, tot_p, s_warp);
-    if (!(threadIdx.x & 1)) s_par[threadIdx.x >> 1] = 0u;  // both halves were read before the scan's barrier
+    group_scan2<T, G>(g, gt, __popc(fr), __popc(par), ex_f, ex_p, tot_f, tot_p, s_warp);
+    if (!(gt & 1)) s_par[gt >> 1] = 0u;  // both halves were read before the scan's barrier
     u32 rf = pf + ex_f, rp = pp + ex_p;
     u32 frm = fr;
     while (frm) {
@@ -266,7 +326,7 @@ __device__ __forceinline__ void b_scan(const BatchDev& b, MCtx& c, int S, int sw
     }
     pf += tot_f;
     pp += tot_p;
-    __syncthreads();  // the list and the parent words are rewritten by the next chunk
+    gsync<G>(g, T);  // the list and the parent words are rewritten by the next chunk
   }
   // per-CTA sums of the winners and the starved
 #pragma unroll
@@ -274,26 +334,26 @@ __device__ __forceinline__ void b_scan(const BatchDev& b, MCtx& c, int S, int sw
     starved += __shfl_xor_sync(0xFFFFFFFFu, starved, o);
     won += __shfl_xor_sync(0xFFFFFFFFu, won, o);
   }
-  if ((threadIdx.x & 31) == 0) {
+  if ((gt & 31) == 0) {
     if (starved) atomicAdd(&s_acc[0], starved);
     if (won) atomicAdd(&s_acc[1], won);
   }
-  if (threadIdx.x == 0) {
+  if (gt == 0) {
     c.P[S] = (int)pp;
     c.F[S] = (int)pf;
   }
 }
 
 // children: the i-th parent (ascending slot) fills the i-th free slot
-template <int T>
-__device__ __forceinline__ void b_births(const BatchDev& b, MCtx& c, int S, int r, int t) {
+template <int T, int G>
+__device__ __forceinline__ void b_births(int g, int gt, const BatchDev& b, MCtx& c, int S, int r, int t) {
   int32_t* act = b.active[S] + c.m.oa[S];
   int4* ag = b.agent[S] + c.m.oa[S];
   const int32_t* plist = b.plist[S] + c.m.oa[S];
   const int32_t* flist = b.flist[S] + c.m.oa[S];
   const int Fin = c.F[S], ext = c.extent[S];
   const int id0 = c.next_id[S];
-  for (int i = threadIdx.x; i < r; i += T) {
+  for (int i = gt; i < r; i += T) {
     const int p = plist[i];
     const int slot = i < Fin ? flist[i] : ext + (i - Fin);
     if (!in_range(p, c.m.cap[S], b.err) || !in_range(slot, c.m.cap[S], b.err)) continue;
@@ -324,24 +384,35 @@ __device__ __forceinline__ void b_count_births(const BatchDev& b, MCtx& c, int S
   if (c.P[S] > avail) c.overflow[S] = 1;
 }
 
-template <int T>
-__global__ void __launch_bounds__(T) k_batch_run(BatchDev b, int nsteps, int sweep_extent, int live_words) {
-  extern __shared__ u32 s_live[];  // [live_words]: one species' live flags, move -> scan
-  __shared__ MCtx c;
-  __shared__ u64 s_warp[T / 32 + 1];
-  __shared__ int s_acc[4];
-  __shared__ int s_idx;
-  __shared__ unsigned short s_list[16 * T];  // live agents of a chunk
-  __shared__ u32 s_par[16 * T / 32];         // parent bits of a chunk
-  if (threadIdx.x < 16 * T / 32) s_par[threadIdx.x] = 0u;
+// N threads per CTA, G models per CTA (groups of N / G threads)
+template <int N, int G>
+__global__ void __launch_bounds__(N, (1024 / N > 0 ? 1024 / N : 1)) k_batch_run(BatchDev b, int nsteps, int sweep_extent,
+                                                                        int live_words) {
+  constexpr int T = N / G;
+  extern __shared__ u32 s_live_all[];  // [G][live_words]: one species' live flags per group, move -> scan
+  __shared__ MCtx s_c[G];
+  __shared__ u64 s_warp_all[G][T / 32 + 1];
+  __shared__ int s_acc_all[G][4];
+  __shared__ int s_idx_all[G];
+  __shared__ unsigned short s_list_all[G][16 * T];  // live agents of a chunk
+  __shared__ u32 s_par_all[G][16 * T / 32];         // parent bits of a chunk
+  const int g = (int)threadIdx.x / T, gt = (int)threadIdx.x % T;
+  MCtx& c = s_c[g];
+  u64* s_warp = s_warp_all[g];
+  int* s_acc = s_acc_all[g];
+  int& s_idx = s_idx_all[g];
+  unsigned short* s_list = s_list_all[g];
+  u32* s_par = s_par_all[g];
+  u32* s_live = s_live_all + (size_t)g * live_words;
+  if (gt < 16 * T / 32) s_par[gt] = 0u;
   while (true) {
-    __syncthreads();
-    if (threadIdx.x == 0) s_idx = (int)atomicAdd(&b.ctrl[0], 1u);
-    __syncthreads();
+    gsync<G>(g, T);
+    if (gt == 0) s_idx = (int)atomicAdd(&b.ctrl[0], 1u);
+    gsync<G>(g, T);
     const int idx = s_idx;
     if (idx >= b.nmodels) break;
     const int mi = b.order[idx];
-    if (threadIdx.x == 0) {
+    if (gt == 0) {
       c.m = b.models[mi];
       const BCtr k = b.ctr[mi];
       for (int s = 0; s < 2; ++s) {
@@ -354,54 +425,54 @@ __global__ void __launch_bounds__(T) k_batch_run(BatchDev b, int nsteps, int swe
       c.step = k.step;
       c.agent_steps = k.agent_steps;
     }
-    __syncthreads();
+    gsync<G>(g, T);
     for (int it = 0; it < nsteps; ++it) {
       const int t = c.step;
-      if (threadIdx.x == 0) {
+      if (gt == 0) {
         c.n_start[0] = c.n_active[0];
         c.n_start[1] = c.n_active[1];
         c.agent_steps += c.n_active[0] + c.n_active[1];
         s_acc[0] = s_acc[1] = s_acc[2] = s_acc[3] = 0;
       }
       const int sw0 = sweep_extent ? c.extent[0] : c.m.cap[0];
-      __syncthreads();
+      gsync<G>(g, T);
       // sheep: move + grass claims; eat, select, die, compact
-      b_move<T>(b, c, 0, sw0, t, s_list, s_warp, s_live, live_words);
-      __syncthreads();
-      b_scan<T>(b, c, 0, sw0, t, s_warp, s_acc, s_list, s_par, s_live, live_words);
-      __syncthreads();
+      b_move<T, G>(g, gt, b, c, 0, sw0, t, s_list, s_warp, s_live, live_words);
+      gsync<G>(g, T);
+      b_scan<T, G>(g, gt, b, c, 0, sw0, t, s_warp, s_acc, s_list, s_par, s_live, live_words);
+      gsync<G>(g, T);
       const int avail0 = c.F[0] + (sweep_extent ? c.m.cap[0] - c.extent[0] : 0);
       const int r0 = min(c.P[0], avail0);
       const int sw1 = sweep_extent ? c.extent[1] : c.m.cap[1];
       // sheep births, concurrently the wolves' move + victim claims (a wolf's
       // claim only needs the cell to hold a live sheep; every newborn lamb
       // sits with its live parent)
-      b_births<T>(b, c, 0, r0, t);
-      b_move<T>(b, c, 1, sw1, t, s_list, s_warp, s_live, live_words);
-      __syncthreads();
-      if (threadIdx.x == 0) {
+      b_births<T, G>(g, gt, b, c, 0, r0, t);
+      b_move<T, G>(g, gt, b, c, 1, sw1, t, s_list, s_warp, s_live, live_words);
+      gsync<G>(g, T);
+      if (gt == 0) {
         b_count_births(b, c, 0, r0, s_acc[0], avail0);
         c.starved[0] = s_acc[0];
         c.grass = s_acc[1];
         s_acc[0] = s_acc[1] = 0;
       }
-      __syncthreads();
-      b_scan<T>(b, c, 1, sw1, t, s_warp, s_acc, s_list, s_par, s_live, live_words);
-      __syncthreads();
+      gsync<G>(g, T);
+      b_scan<T, G>(g, gt, b, c, 1, sw1, t, s_warp, s_acc, s_list, s_par, s_live, live_words);
+      gsync<G>(g, T);
       const int avail1 = c.F[1] + (sweep_extent ? c.m.cap[1] - c.extent[1] : 0);
       const int r1 = min(c.P[1], avail1);
-      b_births<T>(b, c, 1, r1, t);
-      __syncthreads();
-      if (threadIdx.x == 0) {
+      b_births<T, G>(g, gt, b, c, 1, r1, t);
+      gsync<G>(g, T);
+      if (gt == 0) {
         b_count_births(b, c, 1, r1, s_acc[0], avail1);
         c.starved[1] = s_acc[0];
         c.eaten = s_acc[1];
         c.n_active[0] -= s_acc[1];
         c.step = t + 1;
       }
-      __syncthreads();
+      gsync<G>(g, T);
     }
-    if (threadIdx.x == 0) {
+    if (gt == 0) {
       BCtr k;
       for (int s = 0; s < 2; ++s) {
         k.n_active[s] = c.n_active[s];
@@ -416,7 +487,7 @@ __global__ void __launch_bounds__(T) k_batch_run(BatchDev b, int nsteps, int swe
       b.ctr[mi] = k;
     }
   }
-  last_cta_out(b.ctrl);
+  last_cta_out(b.ctrl);  // its barrier waits for every group of the CTA
 }
 
 // one CTA per model: initial agents, grass, empty claim tables, counters
@@ -544,7 +615,7 @@ struct abm_batch {
   BModel* models_dev;
   std::vector<BModel> models;
   long long slots[2], cells;
-  int threads, ctas_per_sm, steps_per_launch;
+  int threads, ctas_per_sm, steps_per_launch, models_per_cta;
   // fixed-capacity rerun of the models whose slabs overflowed (abm_batch_rerun_overflowed)
   abm_batch* rerun;
   std::vector<int> rerun_of;  // per model: its index in `rerun`, or -1
@@ -672,6 +743,7 @@ extern "C" abm_status abm_batch_create(const abm_batch_model* models, int32_t n,
   b->threads = 256;
   b->ctas_per_sm = 4;
   b->steps_per_launch = 1 << 30;
+  b->models_per_cta = 1;
   *out = b;
   return ABM_OK;
 }
@@ -683,6 +755,15 @@ extern "C" abm_status abm_batch_tune(abm_batch* b, int32_t threads, int32_t ctas
   b->threads = threads;
   b->ctas_per_sm = ctas_per_sm;
   b->steps_per_launch = steps_per_launch;
+  if (threads / b->models_per_cta < 128) b->models_per_cta = 1;
+  return ABM_OK;
+}
+
+extern "C" abm_status abm_batch_models_per_cta(abm_batch* b, int32_t models_per_cta) {
+  if (!b || (models_per_cta != 1 && models_per_cta != 2 && models_per_cta != 4)) return ABM_ERR_ARG;
+  // groups of at least 128 threads (the launch shapes instantiated)
+  if (b->threads / models_per_cta < 128) return ABM_ERR_ARG;
+  b->models_per_cta = models_per_cta;
   return ABM_OK;
 }
 
@@ -691,33 +772,35 @@ extern "C" abm_status abm_batch_run(abm_batch* b, int32_t nsteps, int32_t sweep,
   cudaStream_t st = (cudaStream_t)stream;
   const int grid = std::max(1, std::min(b->d.nmodels, num_sms() * b->ctas_per_sm));
   const int ext = sweep == ABM_SWEEP_EXTENT;
-  // the live-flag bitmask of the largest sweep of the batch (at most 1M slots:
-  // 128 KiB of shared memory per CTA; larger models read their flags twice)
+  // the live-flag bitmask of the largest sweep of the batch, per model run at
+  // once (at most 1Mi slots per CTA: 128 KiB of shared memory; larger models
+  // read their flags twice)
+  const int G = b->models_per_cta;
   int live_words = 0;
   for (const BModel& m : b->models) live_words = std::max(live_words, (std::max(m.cap[0], m.cap[1]) + 31) / 32);
-  live_words = std::min(live_words, kBatchLiveWordsMax);
-  const size_t smem = sizeof(u32) * (size_t)live_words;
-  static std::atomic<unsigned long long> attr[4];
+  live_words = std::min(live_words, kBatchLiveWordsMax / G);
+  const size_t smem = sizeof(u32) * (size_t)live_words * (size_t)G;
+  const int smax = (int)sizeof(u32) * kBatchLiveWordsMax;
+  static std::atomic<unsigned long long> attr[9];
   for (int done = 0; done < nsteps;) {
     const int s = std::min(nsteps - done, b->steps_per_launch);
-    switch (b->threads) {
-      case 128:
-        ABM_CUDA_TRY(smem_attr_once(k_batch_run<128>, (int)kBatchLiveWordsMax * 4, attr[0]));
-        k_batch_run<128><<<grid, 128, smem, st>>>(b->d, s, ext, live_words);
-        break;
-      case 256:
-        ABM_CUDA_TRY(smem_attr_once(k_batch_run<256>, (int)kBatchLiveWordsMax * 4, attr[1]));
-        k_batch_run<256><<<grid, 256, smem, st>>>(b->d, s, ext, live_words);
-        break;
-      case 512:
-        ABM_CUDA_TRY(smem_attr_once(k_batch_run<512>, (int)kBatchLiveWordsMax * 4, attr[2]));
-        k_batch_run<512><<<grid, 512, smem, st>>>(b->d, s, ext, live_words);
-        break;
-      default:
-        ABM_CUDA_TRY(smem_attr_once(k_batch_run<1024>, (int)kBatchLiveWordsMax * 4, attr[3]));
-        k_batch_run<1024><<<grid, 1024, smem, st>>>(b->d, s, ext, live_words);
-        break;
+#define ABM_BATCH_LAUNCH(N, GG, I)                                                       \
+  do {                                                                                  \
+    ABM_CUDA_TRY(smem_attr_once(k_batch_run<N, GG>, smax, attr[I]));                   \
+    k_batch_run<N, GG><<<grid, N, smem, st>>>(b->d, s, ext, live_words);                 \
+  } while (0)
+    switch (b->threads * 10 + G) {
+      case 1281: ABM_BATCH_LAUNCH(128, 1, 0); break;
+      case 2561: ABM_BATCH_LAUNCH(256, 1, 1); break;
+      case 2562: ABM_BATCH_LAUNCH(256, 2, 2); break;
+      case 5121: ABM_BATCH_LAUNCH(512, 1, 3); break;
+      case 5122: ABM_BATCH_LAUNCH(512, 2, 4); break;
+      case 5124: ABM_BATCH_LAUNCH(512, 4, 5); break;
+      case 10242: ABM_BATCH_LAUNCH(1024, 2, 6); break;
+      case 10244: ABM_BATCH_LAUNCH(1024, 4, 7); break;
+      default: ABM_BATCH_LAUNCH(1024, 1, 8); break;
     }
+#undef ABM_BATCH_LAUNCH
     ABM_LAUNCH_CHECK();
     done += s;
   }
@@ -875,6 +958,7 @@ extern "C" abm_status abm_batch_rerun_overflowed(abm_batch* b, const int32_t* ca
   r->threads = b->threads;
   r->ctas_per_sm = b->ctas_per_sm;
   r->steps_per_launch = b->steps_per_launch;
+  r->models_per_cta = b->models_per_cta;
   e = abm_batch_run(r, steps, sweep, stream);
   const int nr = (int)rm.size();
   if (e == ABM_OK && (cudaMalloc(&b->rerun_idx, sizeof(int32_t) * (size_t)nr) != cudaSuccess ||

@@ -18,11 +18,13 @@ def test_tune_batch_and_world_and_slab(tmp_path, monkeypatch):
               for i in range(200)]
     best = autotune.tune_batch(models, 30, abm.SWEEP_CAPACITY, trial_steps=3, rounds=1)
     assert best["threads"] in (256, 512, 1024) and best["ctas_per_sm"] in (1, 2, 4)
+    assert best["models_per_cta"] in (1, 2, 4) and best["threads"] // best["models_per_cta"] >= 128
     assert autotune.tune_batch(models, 30, abm.SWEEP_CAPACITY) == best  # cached
     digests = []
-    for th, cps in ((best["threads"], best["ctas_per_sm"]), (256, 1), (1024, 2)):
+    for th, cps, g in ((best["threads"], best["ctas_per_sm"], best["models_per_cta"]), (256, 1, 1), (1024, 2, 1),
+                       (1024, 1, 4), (512, 2, 2)):
         b = engine.Batch(models)
-        b.tune(th, cps, 7)
+        b.tune(th, cps, 7, models_per_cta=g)
         b.run(30)
         digests.append(b.digest().cpu().numpy())
     assert all(np.array_equal(d, digests[0]) for d in digests)
@@ -31,3 +33,19 @@ def test_tune_batch_and_world_and_slab(tmp_path, monkeypatch):
     assert w["engine"] in (abm.ENGINE_PERSISTENT, abm.ENGINE_KERNELS)
     sl = autotune.tune_slab(20000, 8, 0.05, 1000, reps=1)
     assert sl["threads"] in (128, 256, 512)
+
+
+def test_models_per_cta_limits():
+    """Groups keep at least 128 threads; a smaller CTA size resets the packing."""
+    assert torch.cuda.is_available()
+    from paper_2508_16508_gb300 import abm, engine
+    c = workloads.PRED_SMALL
+    b = engine.Batch([dict(side=c["side"], seed=c["seed"], model=c["model"], params=c["params"], cap=c["cap"],
+                           n0=c["n0"])])
+    L = abm.lib()
+    assert L.abm_batch_tune(b.h, 512, 2, 100) == abm.OK
+    assert L.abm_batch_models_per_cta(b.h, 4) == abm.OK
+    assert L.abm_batch_models_per_cta(b.h, 3) == abm.ERR_ARG
+    assert L.abm_batch_tune(b.h, 256, 2, 100) == abm.OK  # 256 / 4 < 128: back to one model per CTA
+    assert L.abm_batch_models_per_cta(b.h, 4) == abm.ERR_ARG
+    assert L.abm_batch_models_per_cta(b.h, 2) == abm.OK

@@ -54,11 +54,12 @@ def compare_model(b, m, ow, where):
 
 
 @pytest.mark.parametrize("sweep", [0, 1])
-@pytest.mark.parametrize("threads,spl", [(256, 1 << 30), (128, 7), (512, 13)])
-def test_random_batch_vs_oracle(eng, sweep, threads, spl):
-    models = random_models(20, 100 + threads + sweep)
+@pytest.mark.parametrize("threads,spl,mpc", [(256, 1 << 30, 1), (128, 7, 1), (512, 13, 1), (256, 11, 2), (512, 1 << 30, 4),
+                                             (1024, 9, 2), (1024, 1 << 30, 4), (512, 17, 2)])
+def test_random_batch_vs_oracle(eng, sweep, threads, spl, mpc):
+    models = random_models(20, 100 + threads + sweep + 7 * mpc)
     b = eng.Batch(models)
-    b.tune(threads, 2, spl)
+    b.tune(threads, 2 if threads < 1024 else 1, spl, models_per_cta=mpc)
     b.run(45, sweep=sweep)
     cnt = b.counters()
     for m, md in enumerate(models):
