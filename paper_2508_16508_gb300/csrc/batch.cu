@@ -173,7 +173,9 @@ __device__ __forceinline__ void b_move(int g, int gt, const BatchDev& b, MCtx& c
   // changes this species' flags between its move and its scan
   const bool keep = sweep <= 32 * live_words;
   // per chunk: four 128-bit loads of live flags per thread (int4 q0 + u*T),
-  // the live slots listed, then two agents in flight per thread
+  // the live slots listed, then two agents in flight per thread (copying the
+  // next chunk's flags into shared memory ahead, with cp.async, measured slower
+  // overall: faster at full capacity, slower with extent sweeps)
   for (int c0 = 0; c0 < sweep; c0 += 16 * T) {
     const int q0 = (c0 >> 2) + gt;
     const int nq = (sweep + 3) >> 2;
@@ -759,6 +761,41 @@ extern "C" abm_status abm_batch_tune(abm_batch* b, int32_t threads, int32_t ctas
   return ABM_OK;
 }
 
+// One launch of the run kernel with N threads and G models per CTA. Its
+// dynamic shared memory (G live-flag bitmasks) is set per device, raised when
+// a batch needs more; the bitmasks shrink (their models then read their flags
+// twice) when the CTA's shared memory is short.
+template <int N, int GG>
+static abm_status batch_launch(const BatchDev& d, int grid, int nsteps, int ext, int live_words, cudaStream_t st) {
+  static std::atomic<int> limit_set[64];
+  static std::atomic<int> max_dyn[64];
+  int dev = 0;
+  ABM_CUDA_TRY(cudaGetDevice(&dev));
+  const bool cache = dev >= 0 && dev < 64;
+  int maxd = cache ? max_dyn[dev].load(std::memory_order_relaxed) : 0;
+  if (maxd == 0) {
+    int optin = 0;
+    cudaFuncAttributes fa;
+    ABM_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    ABM_CUDA_TRY(cudaFuncGetAttributes(&fa, k_batch_run<N, GG>));
+    maxd = std::max(0, optin - (int)fa.sharedSizeBytes);
+    if (cache) max_dyn[dev].store(maxd, std::memory_order_relaxed);
+  }
+  while (live_words > 0 && sizeof(u32) * (size_t)live_words * GG > (size_t)maxd) live_words /= 2;
+  const int smem = (int)(sizeof(u32) * (size_t)live_words * GG);
+  if (!cache || limit_set[dev].load(std::memory_order_acquire) < smem) {
+    ABM_CUDA_TRY(cudaFuncSetAttribute(k_batch_run<N, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    if (cache) {
+      int cur = limit_set[dev].load(std::memory_order_relaxed);
+      while (cur < smem && !limit_set[dev].compare_exchange_weak(cur, smem)) {
+      }
+    }
+  }
+  k_batch_run<N, GG><<<grid, N, smem, st>>>(d, nsteps, ext, live_words);
+  ABM_LAUNCH_CHECK();
+  return ABM_OK;
+}
+
 extern "C" abm_status abm_batch_models_per_cta(abm_batch* b, int32_t models_per_cta) {
   if (!b || (models_per_cta != 1 && models_per_cta != 2 && models_per_cta != 4)) return ABM_ERR_ARG;
   // groups of at least 128 threads (the launch shapes instantiated)
@@ -773,34 +810,27 @@ extern "C" abm_status abm_batch_run(abm_batch* b, int32_t nsteps, int32_t sweep,
   const int grid = std::max(1, std::min(b->d.nmodels, num_sms() * b->ctas_per_sm));
   const int ext = sweep == ABM_SWEEP_EXTENT;
   // the live-flag bitmask of the largest sweep of the batch, per model run at
-  // once (at most 1Mi slots per CTA: 128 KiB of shared memory; larger models
-  // read their flags twice)
+  // once (at most 1Mi slots per CTA, and as much as the CTA's shared memory
+  // allows; larger models read their flags twice)
   const int G = b->models_per_cta;
   int live_words = 0;
   for (const BModel& m : b->models) live_words = std::max(live_words, (std::max(m.cap[0], m.cap[1]) + 31) / 32);
   live_words = std::min(live_words, kBatchLiveWordsMax / G);
-  const size_t smem = sizeof(u32) * (size_t)live_words * (size_t)G;
-  const int smax = (int)sizeof(u32) * kBatchLiveWordsMax;
-  static std::atomic<unsigned long long> attr[9];
   for (int done = 0; done < nsteps;) {
     const int s = std::min(nsteps - done, b->steps_per_launch);
-#define ABM_BATCH_LAUNCH(N, GG, I)                                                       \
-  do {                                                                                  \
-    ABM_CUDA_TRY(smem_attr_once(k_batch_run<N, GG>, smax, attr[I]));                   \
-    k_batch_run<N, GG><<<grid, N, smem, st>>>(b->d, s, ext, live_words);                 \
-  } while (0)
+    abm_status e;
     switch (b->threads * 10 + G) {
-      case 1281: ABM_BATCH_LAUNCH(128, 1, 0); break;
-      case 2561: ABM_BATCH_LAUNCH(256, 1, 1); break;
-      case 2562: ABM_BATCH_LAUNCH(256, 2, 2); break;
-      case 5121: ABM_BATCH_LAUNCH(512, 1, 3); break;
-      case 5122: ABM_BATCH_LAUNCH(512, 2, 4); break;
-      case 5124: ABM_BATCH_LAUNCH(512, 4, 5); break;
-      case 10242: ABM_BATCH_LAUNCH(1024, 2, 6); break;
-      case 10244: ABM_BATCH_LAUNCH(1024, 4, 7); break;
-      default: ABM_BATCH_LAUNCH(1024, 1, 8); break;
+      case 1281: e = batch_launch<128, 1>(b->d, grid, s, ext, live_words, st); break;
+      case 2561: e = batch_launch<256, 1>(b->d, grid, s, ext, live_words, st); break;
+      case 2562: e = batch_launch<256, 2>(b->d, grid, s, ext, live_words, st); break;
+      case 5121: e = batch_launch<512, 1>(b->d, grid, s, ext, live_words, st); break;
+      case 5122: e = batch_launch<512, 2>(b->d, grid, s, ext, live_words, st); break;
+      case 5124: e = batch_launch<512, 4>(b->d, grid, s, ext, live_words, st); break;
+      case 10242: e = batch_launch<1024, 2>(b->d, grid, s, ext, live_words, st); break;
+      case 10244: e = batch_launch<1024, 4>(b->d, grid, s, ext, live_words, st); break;
+      default: e = batch_launch<1024, 1>(b->d, grid, s, ext, live_words, st); break;
     }
-#undef ABM_BATCH_LAUNCH
+    if (e != ABM_OK) return e;
     ABM_LAUNCH_CHECK();
     done += s;
   }

@@ -99,6 +99,18 @@ __device__ __forceinline__ u32 draw(u32 seed, u32 model, u32 step, u32 slot, u32
   return draw4(seed, model, step, slot, purpose, species).x;
 }
 
+// asynchronous global -> shared copies (16 bytes: both addresses 16-byte
+// aligned; 4 bytes: 4-byte aligned), completed by cp_async_wait_0
+__device__ __forceinline__ u32 smem_u32(const void* p) { return (u32)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // uniform integer in [0, n) by multiply-shift
 __device__ __forceinline__ int uniform_below(u32 u, int n) {
   return (int)(((u64)u * (u64)(u32)n) >> 32);

@@ -50,16 +50,6 @@ constexpr u32 kShareBits = 21;          // level words: shares in the low 21 bit
 constexpr u32 kShareMask = (1u << kShareBits) - 1u;
 constexpr u32 kLive = 1u << 31, kAsk = 1u << 30;  // packed slot word: live | ask | qty
 
-__device__ __forceinline__ u32 smem_u32(const void* p) { return (u32)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // order-preserving map of int32 onto u32
 __device__ __forceinline__ u32 ord32(int32_t p) { return (u32)p ^ 0x80000000u; }
