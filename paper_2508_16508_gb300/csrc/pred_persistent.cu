@@ -5,8 +5,9 @@
 // Per step, five barrier-separated phases (each species: move + claims;
 // eat / select / die with flags into bit-planes and per-unit counts; ranks ->
 // parent list and the first P free slots (P = parents); births), with the
-// wolves' ranks and births shifted so that they overlap sheep work (the
-// schedule is spelled out in k_persistent).
+// wolves' ranks and births shifted by one step and run by two warps of each
+// CTA while the other fourteen move and feed the sheep (the schedule is
+// spelled out in k_persistent).
 // Move and count phases deal 128-slot units to warps round-robin over the
 // CTAs (the live agents crowd the low slots) and list the live agents of a
 // CTA's units in shared memory for all its threads; the rank phases give CTA
@@ -64,6 +65,26 @@ __device__ __forceinline__ void grid_sync(u32* bar, int* err, u32& target, u32 e
   __syncthreads();
 }
 
+// Teams: in phases 1 and 2 a CTA splits into a sheep team (warps 0 ..
+// kSheepWarps - 1, named barrier 1) and a wolf team (the last kWolfWarps warps,
+// named barrier 2), so that the previous step's wolf ranks and births run
+// beside the sheep work instead of before it; in the other phases all warps
+// form one team (the CTA barrier). NW = warps of the team (it starts at warp 0
+// for the sheep team and the whole CTA).
+constexpr int kWolfWarps = 2;
+constexpr int kSheepWarps = kPWarps - kWolfWarps;
+
+template <int NW>
+__device__ __forceinline__ void tsync() {
+  if (NW == kPWarps) {
+    __syncthreads();
+  } else if (NW == kSheepWarps) {
+    asm volatile("bar.sync 1, %0;" ::"n"(kSheepWarps * 32) : "memory");
+  } else {
+    asm volatile("bar.sync 2, %0;" ::"n"(kWolfWarps * 32) : "memory");
+  }
+}
+
 // Work compaction over a CTA: in one round every warp loads the live flags of
 // kQ 128-slot units (lane l: slots 4l..4l+3 of each, live mask m[q]); the live
 // slots of the CTA's kQ * 16 units go into one shared list, entry = v << 7 |
@@ -84,6 +105,7 @@ struct CtaList {
   int* energy;           // [kRoundUnits * 128]
 };
 
+template <int NW>
 __device__ __forceinline__ int cta_list_live(const u32 (&m)[kQ], const CtaList& cl) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const u32 lt = (1u << lane) - 1u;
@@ -93,24 +115,24 @@ __device__ __forceinline__ int cta_list_live(const u32 (&m)[kQ], const CtaList& 
     const u32 b0 = __ballot_sync(0xFFFFFFFFu, m[q] & 1u), b1 = __ballot_sync(0xFFFFFFFFu, m[q] & 2u);
     const u32 b2 = __ballot_sync(0xFFFFFFFFu, m[q] & 4u), b3 = __ballot_sync(0xFFFFFFFFu, m[q] & 8u);
     pre[q] = __popc(b0 & lt) + __popc(b1 & lt) + __popc(b2 & lt) + __popc(b3 & lt);
-    if (lane == 0) cl.wcnt[q * kPWarps + warp] = __popc(b0) + __popc(b1) + __popc(b2) + __popc(b3);
+    if (lane == 0) cl.wcnt[q * NW + warp] = __popc(b0) + __popc(b1) + __popc(b2) + __popc(b3);
   }
-  __syncthreads();
+  tsync<NW>();
   int tot = 0;
 #pragma unroll
-  for (int k = 0; k < kRoundUnits; ++k) {
+  for (int k = 0; k < kQ * NW; ++k) {
     const int c = cl.wcnt[k];
 #pragma unroll
     for (int q = 0; q < kQ; ++q)
-      if (k < q * kPWarps + warp) pre[q] += c;
+      if (k < q * NW + warp) pre[q] += c;
     tot += c;
   }
 #pragma unroll
   for (int q = 0; q < kQ; ++q)
 #pragma unroll
     for (int j = 0; j < 4; ++j)
-      if (m[q] & (1u << j)) cl.list[pre[q]++] = (unsigned short)(((q * kPWarps + warp) << 7) | (4 * lane + j));
-  __syncthreads();
+      if (m[q] & (1u << j)) cl.list[pre[q]++] = (unsigned short)(((q * NW + warp) << 7) | (4 * lane + j));
+  tsync<NW>();
   return tot;
 }
 
@@ -118,14 +140,17 @@ __device__ __forceinline__ u32 live_mask(int4 a) {
   return (u32)(a.x != 0) | ((u32)(a.y != 0) << 1) | ((u32)(a.z != 0) << 2) | ((u32)(a.w != 0) << 3);
 }
 
-// unit at place v of round r of this CTA: units are dealt round-robin over
-// the CTAs (unit i -> CTA i mod G), so the crowded low slots spread over all SMs
+// unit at place v of round r of this CTA (a team of NW warps deals kQ * NW
+// units per round): units are dealt round-robin over the CTAs (unit i -> CTA
+// i mod G), so the crowded low slots spread over all SMs
+template <int NW>
 __device__ __forceinline__ int unit_at(int v, int round) {
-  return (int)blockIdx.x + (int)gridDim.x * (v + kRoundUnits * round);
+  return (int)blockIdx.x + (int)gridDim.x * (v + kQ * NW * round);
 }
 
+template <int NW>
 __device__ __forceinline__ int slot_of(u32 entry, int round) {
-  return (unit_at((int)(entry >> 7), round) << 7) + (int)(entry & 127u);
+  return (unit_at<NW>((int)(entry >> 7), round) << 7) + (int)(entry & 127u);
 }
 
 // ---- several-wolves variant: per-cell lists tagged with the step
@@ -164,13 +189,13 @@ __device__ __forceinline__ int4 move_one(const WorldDev& w, int t, int slot, int
 // A world whose units fit in one round leaves the round's list, live words and
 // moved records in shared memory; `carried` = the list's length (-1 if not).
 // live masks of this thread's slots in round `round` of the unit dealing
-template <int S>
+template <int S, int NW>
 __device__ __forceinline__ void round_flags(const WorldDev& w, int ext, int round, u32 (&m)[kQ]) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nblk = (ext + 127) >> 7;
 #pragma unroll
   for (int q = 0; q < kQ; ++q) {
-    const int i = unit_at(q * kPWarps + warp, round);
+    const int i = unit_at<NW>(q * NW + warp, round);
     const int base = (i << 7) + 4 * lane;
     int4 act = make_int4(0, 0, 0, 0);
     if (i < nblk && base < ext) act = reinterpret_cast<const int4*>(w.sp[S].active)[base >> 2];
@@ -179,9 +204,10 @@ __device__ __forceinline__ void round_flags(const WorldDev& w, int ext, int roun
 }
 
 // m0 = round_flags(round 0), loaded by the caller ahead of other work
-template <int S>
+template <int S, int NW>
 __device__ __forceinline__ void p_move(const WorldDev& w, int t, int ext, const CtaList& cl, int& carried,
                                        const u32 (&m0)[kQ]) {
+  constexpr int NT = NW * 32;
   carried = -1;
   const SpeciesDev& sp = w.sp[S];
   const int L = w.side;
@@ -189,25 +215,25 @@ __device__ __forceinline__ void p_move(const WorldDev& w, int t, int ext, const 
   const int metab = (S == 0 && (w.variant & ABM_VARIANT_GRASS_OFF)) ? 0 : w.params[PRM_SHEEP_METAB + S];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nblk = (ext + 127) >> 7;
-  for (int round = 0; unit_at(0, round) < nblk; ++round) {
+  for (int round = 0; unit_at<NW>(0, round) < nblk; ++round) {
     u32 m[kQ];
     if (round == 0) {
 #pragma unroll
       for (int q = 0; q < kQ; ++q) m[q] = m0[q];
     } else {
-      round_flags<S>(w, ext, round, m);
+      round_flags<S, NW>(w, ext, round, m);
     }
 #pragma unroll
     for (int q = 0; q < kQ; ++q) {  // live words of the round's units, for the count phase
       u32 vm = m[q] << (4 * (lane & 7));
 #pragma unroll
       for (int o = 1; o < 8; o <<= 1) vm |= __shfl_xor_sync(0xFFFFFFFFu, vm, o);
-      if ((lane & 7) == 0) cl.live[4 * (q * kPWarps + warp) + (lane >> 3)] = vm;
+      if ((lane & 7) == 0) cl.live[4 * (q * NW + warp) + (lane >> 3)] = vm;
     }
-    const int tot = cta_list_live(m, cl);
-    for (int e = threadIdx.x; e < tot; e += 2 * kPT) {
-      const int sa = slot_of(cl.list[e], round);
-      const int sb = e + kPT < tot ? slot_of(cl.list[e + kPT], round) : -1;
+    const int tot = cta_list_live<NW>(m, cl);
+    for (int e = threadIdx.x; e < tot; e += 2 * NT) {
+      const int sa = slot_of<NW>(cl.list[e], round);
+      const int sb = e + NT < tot ? slot_of<NW>(cl.list[e + NT], round) : -1;
       const int4 aa = sp.agent[sa];
       int4 ab = make_int4(0, 0, 0, 0);
       if (sb >= 0) ab = sp.agent[sb];
@@ -216,12 +242,12 @@ __device__ __forceinline__ void p_move(const WorldDev& w, int t, int ext, const 
       cl.energy[e] = ma.y;
       if (sb >= 0) {
         const int4 mb = move_one<S>(w, t, sb, ab, L, metab);
-        cl.cell[e + kPT] = mb.x;
-        cl.energy[e + kPT] = mb.y;
+        cl.cell[e + NT] = mb.x;
+        cl.energy[e + NT] = mb.y;
       }
     }
     carried = tot;
-    __syncthreads();  // the list is rewritten by the next round
+    tsync<NW>();  // the list is rewritten by the next round
   }
 }
 
@@ -308,10 +334,11 @@ __device__ __forceinline__ u32 count_one(const WorldDev& w, int t, int slot, int
 // parent bits into the bit-planes (word = 32 slots = 8 lanes x 4 slots) and
 // its two counts, which are also summed per run of kseg units (the CTA
 // segments of the rank phase).
-template <int S>
+template <int S, int NW>
 __device__ __forceinline__ void p_count(const WorldDev& w, int t, int ext, int kseg, int* acc, const CtaList& cl,
                                         int carried, u32* s_upar /* [kRoundUnits][4], zero on entry and exit */,
                                         int* s_acc /* [2 * kPWarps] */) {
+  constexpr int NT = NW * 32;
   const SpeciesDev& sp = w.sp[S];
   const PersistDev& ps = w.ps;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -323,15 +350,15 @@ __device__ __forceinline__ void p_count(const WorldDev& w, int t, int ext, int k
   int starved = 0, won = 0;
   // one round and the move phase's list still in shared memory: neither the
   // live flags nor the agent records need reading again
-  const bool reuse = carried >= 0 && unit_at(0, 1) >= nblk;
-  for (int round = 0; unit_at(0, round) < nblk; ++round) {
+  const bool reuse = carried >= 0 && unit_at<NW>(0, 1) >= nblk;
+  for (int round = 0; unit_at<NW>(0, round) < nblk; ++round) {
     u32 m[kQ], fr[kQ];
 #pragma unroll
     for (int q = 0; q < kQ; ++q) {
-      const int i = unit_at(q * kPWarps + warp, round);
+      const int i = unit_at<NW>(q * NW + warp, round);
       const int base = (i << 7) + 4 * lane;
       if (reuse) {
-        m[q] = (cl.live[4 * (q * kPWarps + warp) + (lane >> 3)] >> (4 * (lane & 7))) & 0xFu;
+        m[q] = (cl.live[4 * (q * NW + warp) + (lane >> 3)] >> (4 * (lane & 7))) & 0xFu;
       } else {
         int4 act = make_int4(0, 0, 0, 0);
         if (i < nblk && base < ext) act = reinterpret_cast<const int4*>(sp.active)[base >> 2];
@@ -340,16 +367,16 @@ __device__ __forceinline__ void p_count(const WorldDev& w, int t, int ext, int k
       const u32 valid = (i >= nblk || base >= ext) ? 0u : (ext - base >= 4 ? 0xFu : (1u << (ext - base)) - 1u);
       fr[q] = ~m[q] & valid;
     }
-    const int tot = reuse ? carried : cta_list_live(m, cl);
-    for (int e = threadIdx.x; e < tot; e += 2 * kPT) {
+    const int tot = reuse ? carried : cta_list_live<NW>(m, cl);
+    for (int e = threadIdx.x; e < tot; e += 2 * NT) {
       const u32 ea = cl.list[e];
-      const int eb = e + kPT < tot ? (int)cl.list[e + kPT] : -1;
-      const int sa = slot_of(ea, round);
-      const int sb = eb >= 0 ? slot_of((u32)eb, round) : -1;
+      const int eb = e + NT < tot ? (int)cl.list[e + NT] : -1;
+      const int sa = slot_of<NW>(ea, round);
+      const int sb = eb >= 0 ? slot_of<NW>((u32)eb, round) : -1;
       int4 aa, ab = make_int4(0, 0, 0, 0);
       if (reuse) {
         aa = make_int4(cl.cell[e], cl.energy[e], 0, 0);
-        if (sb >= 0) ab = make_int4(cl.cell[e + kPT], cl.energy[e + kPT], 0, 0);
+        if (sb >= 0) ab = make_int4(cl.cell[e + NT], cl.energy[e + NT], 0, 0);
       } else {
         aa = sp.agent[sa];
         if (sb >= 0) ab = sp.agent[sb];
@@ -369,11 +396,11 @@ __device__ __forceinline__ void p_count(const WorldDev& w, int t, int ext, int k
         won += (r >> 2) & 1u;
       }
     }
-    __syncthreads();
+    tsync<NW>();
 #pragma unroll
     for (int q = 0; q < kQ; ++q) {
-      const int v = q * kPWarps + warp;
-      const int i = unit_at(v, round);
+      const int v = q * NW + warp;
+      const int i = unit_at<NW>(v, round);
       if (i >= nblk) continue;
       const int base = (i << 7) + 4 * lane;
       const u32 pw = s_upar[4 * v + (lane >> 3)];
@@ -397,7 +424,7 @@ __device__ __forceinline__ void p_count(const WorldDev& w, int t, int ext, int k
       __syncwarp();
       if (lane < 4) s_upar[4 * v + lane] = 0u;
     }
-    __syncthreads();  // the list and the unit words are rewritten by the next round
+    tsync<NW>();  // the list and the unit words are rewritten by the next round
   }
   // accumulators: summed over the CTA first, so that the two counters see one
   // atomic per CTA, not one per warp (same-address atomics serialise in L2)
@@ -410,11 +437,11 @@ __device__ __forceinline__ void p_count(const WorldDev& w, int t, int ext, int k
     s_acc[2 * warp] = starved;
     s_acc[2 * warp + 1] = won;
   }
-  __syncthreads();
+  tsync<NW>();
   if (threadIdx.x == 0) {
     int a = 0, b = 0;
 #pragma unroll
-    for (int k = 0; k < kPWarps; ++k) {
+    for (int k = 0; k < NW; ++k) {
       a += s_acc[2 * k];
       b += s_acc[2 * k + 1];
     }
@@ -457,13 +484,47 @@ __device__ __forceinline__ void grand_totals(const PersistDev& ps, u32& F, u32& 
   __syncthreads();  // s_red is reused by the caller
 }
 
+// One unit's ranks: a warp scan of the lanes' (free, parent) counts taken
+// from the unit's plane words wf / wp (zero past the extent) and its prefix
+// pr = free << 32 | parents, then the list writes: the parent list takes
+// every parent, the free list only the ranks below P (the only free slots a
+// child can receive).
+template <int S>
+__device__ __forceinline__ void rank_unit(const WorldDev& w, int base, int ext, u32 wf, u32 wp, u64 pr, u32 P,
+                                          int lane) {
+  const SpeciesDev& sp = w.sp[S];
+  const int sh = 4 * (lane & 7);
+  u32 fr = base < ext ? (wf >> sh) & 0xFu : 0u;
+  u32 par = base < ext ? (wp >> sh) & 0xFu : 0u;
+  const u32 c = (u32)__popc(fr) | ((u32)__popc(par) << 16);
+  u32 inc = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u32 x = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+    if (lane >= o) inc += x;
+  }
+  const u32 ex = inc - c;
+  u32 rf = (u32)(pr >> 32) + (ex & 0xFFFFu), rp = (u32)pr + (ex >> 16);
+  while (fr && rf < P) {
+    const int jj = __ffs(fr) - 1;
+    fr &= fr - 1;
+    if (in_range(rf, sp.cap, w.err)) sp.freel[rf] = base + jj;
+    ++rf;
+  }
+  while (par) {
+    const int jj = __ffs(par) - 1;
+    par &= par - 1;
+    if (in_range(rp, sp.cap, w.err)) sp.parents[rp] = base + jj;
+    ++rp;
+  }
+}
+
 // phase 3/6: ranks -> parent list (all) and free list (ranks below P only).
 // CTA b owns units [b*kseg, (b+1)*kseg); the unit ranks are the segment's
 // prefix plus a block scan of the unit counts; inside a unit, a warp scan.
 template <int S>
 __device__ __forceinline__ void p_ranks(const WorldDev& w, int ext, int kseg, u32 P, u32 preF, u32 preP,
                                         u64* s_red, u64* s_pre) {
-  const SpeciesDev& sp = w.sp[S];
   const PersistDev& ps = w.ps;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nblk = (ext + 127) >> 7;
@@ -478,36 +539,13 @@ __device__ __forceinline__ void p_ranks(const WorldDev& w, int ext, int kseg, u3
     __syncthreads();
     const int cn = min(kPT, j1 - c0);
     for (int q = warp; q < cn; q += kPWarps) {
-      const u64 pre = s_pre[q];
-      u32 pf = (u32)(pre >> 32), pp = (u32)pre;
       const int base = ((c0 + q) << 7) + 4 * lane;
-      u32 fr = 0, par = 0;
+      u32 wf = 0, wp = 0;
       if (base < ext) {
-        const int sh = 4 * (lane & 7);
-        fr = (ps.plane[S][0][base >> 5] >> sh) & 0xFu;
-        par = (ps.plane[S][1][base >> 5] >> sh) & 0xFu;
+        wf = ps.plane[S][0][base >> 5];
+        wp = ps.plane[S][1][base >> 5];
       }
-      const u32 c = (u32)__popc(fr) | ((u32)__popc(par) << 16);
-      u32 inc = c;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const u32 x = __shfl_up_sync(0xFFFFFFFFu, inc, o);
-        if (lane >= o) inc += x;
-      }
-      const u32 ex = inc - c;
-      u32 rf = pf + (ex & 0xFFFFu), rp = pp + (ex >> 16);
-      while (fr && rf < P) {  // only the first P free slots can receive a child
-        const int jj = __ffs(fr) - 1;
-        fr &= fr - 1;
-        if (in_range(rf, sp.cap, w.err)) sp.freel[rf] = base + jj;
-        ++rf;
-      }
-      while (par) {
-        const int jj = __ffs(par) - 1;
-        par &= par - 1;
-        if (in_range(rp, sp.cap, w.err)) sp.parents[rp] = base + jj;
-        ++rp;
-      }
+      rank_unit<S>(w, base, ext, wf, wp, s_pre[q], P, lane);
     }
     cf += tf;
     cp += tp;
@@ -531,7 +569,6 @@ __device__ __forceinline__ void rank_phase(const WorldDev& w, int ext, int kseg,
     p_ranks<S>(w, ext, kseg, P, preF, preP, s_red, s_pre);
     return;
   }
-  const SpeciesDev& sp = w.sp[S];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nblk = (ext + 127) >> 7;
   const int j0 = blockIdx.x * kseg, j1 = min(nblk, j0 + kseg);
@@ -581,41 +618,115 @@ __device__ __forceinline__ void rank_phase(const WorldDev& w, int ext, int kseg,
   for (int k = 0; k < kRankU; ++k) {
     const int q = warp + kPWarps * k;
     if (q >= n) break;
-    const u64 pr = s_pre[q];
-    const int base = ((j0 + q) << 7) + 4 * lane;
-    const int sh = 4 * (lane & 7);
-    u32 fr = base < ext ? (wf[k] >> sh) & 0xFu : 0u;
-    u32 par = base < ext ? (wp[k] >> sh) & 0xFu : 0u;
-    const u32 c = (u32)__popc(fr) | ((u32)__popc(par) << 16);
-    u32 inc = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const u32 x = __shfl_up_sync(0xFFFFFFFFu, inc, o);
-      if (lane >= o) inc += x;
-    }
-    const u32 ex = inc - c;
-    u32 rf = (u32)(pr >> 32) + (ex & 0xFFFFu), rp = (u32)pr + (ex >> 16);
-    while (fr && rf < P) {  // only the first P free slots can receive a child
-      const int jj = __ffs(fr) - 1;
-      fr &= fr - 1;
-      if (in_range(rf, sp.cap, w.err)) sp.freel[rf] = base + jj;
-      ++rf;
-    }
-    while (par) {
-      const int jj = __ffs(par) - 1;
-      par &= par - 1;
-      if (in_range(rp, sp.cap, w.err)) sp.parents[rp] = base + jj;
-      ++rp;
-    }
+    rank_unit<S>(w, ((j0 + q) << 7) + 4 * lane, ext, wf[k], wp[k], s_pre[q], P, lane);
   }
   __syncthreads();  // s_pre and s_red are reused
 }
 
+// A rank phase on the wolf team (kWolfWarps warps, named barrier 2) while the
+// sheep team moves the sheep: the same lists as rank_phase. The segment sums,
+// the first pass's unit counts and the plane words of each warp's first
+// kRankTU units are all loaded up front, in one round trip; longer runs of
+// units take further passes of one unit count per team thread.
+constexpr int kRankTU = 8;
+
 template <int S>
-__device__ __forceinline__ void p_births(const WorldDev& w, int t, int r, int F, int ext, int id0) {
+__device__ __forceinline__ void rank_team(const WorldDev& w, int ext, int kseg, u32& F, u32& P,
+                                          u64* s_red /* [2 * kWolfWarps] */, u64* s_pre /* [kWolfWarps * 32] */) {
+  constexpr int NW = kWolfWarps, NT = NW * 32;
+  const PersistDev& ps = w.ps;
+  const int tt = (int)threadIdx.x - kSheepWarps * 32;
+  const int warp = tt >> 5, lane = tt & 31;
+  const int nblk = (ext + 127) >> 7;
+  const int j0 = blockIdx.x * kseg, j1 = min(nblk, j0 + kseg);
+  const int n = max(0, j1 - j0);
+  const u64 bv0 = tt < n ? ps.blk[S][j0 + tt] : 0ull;
+  u32 wf[kRankTU], wp[kRankTU];
+#pragma unroll
+  for (int k = 0; k < kRankTU; ++k) {
+    const int q = warp + NW * k;
+    const int base = ((j0 + q) << 7) + 4 * lane;
+    wf[k] = 0u;
+    wp[k] = 0u;
+    if (q < n && base < ext) {
+      wf[k] = ps.plane[S][0][base >> 5];
+      wp[k] = ps.plane[S][1][base >> 5];
+    }
+  }
+  // grand totals and the sums of the segments before this CTA's
+  u64 tot = 0, pre = 0;
+  for (int j = tt; j < (int)gridDim.x; j += NT) {
+    const u64 x = ps.seg[S][j];
+    tot += x;
+    if (j < (int)blockIdx.x) pre += x;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    tot += __shfl_xor_sync(0xFFFFFFFFu, tot, o);
+    pre += __shfl_xor_sync(0xFFFFFFFFu, pre, o);
+  }
+  if (lane == 0) {
+    s_red[2 * warp] = tot;
+    s_red[2 * warp + 1] = pre;
+  }
+  tsync<NW>();
+  tot = pre = 0;
+#pragma unroll
+  for (int i = 0; i < NW; ++i) {
+    tot += s_red[2 * i];
+    pre += s_red[2 * i + 1];
+  }
+  F = (u32)(tot >> 32);
+  P = (u32)tot;
+  tsync<NW>();  // s_red is reused by the scan
+  // unit prefixes, packed (free << 32 | parents: the parent sums stay below
+  // the capacity, so the low half never carries into the high one)
+  for (int c0 = 0; c0 < n; c0 += NT) {
+    const u64 v = c0 == 0 ? bv0 : (c0 + tt < n ? ps.blk[S][j0 + c0 + tt] : 0ull);
+    u64 inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const u64 x = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+      if (lane >= o) inc += x;
+    }
+    if (lane == 31) s_red[warp] = inc;
+    tsync<NW>();
+    u64 wpre = 0, ptot = 0;
+#pragma unroll
+    for (int i = 0; i < NW; ++i) {
+      const u64 x = s_red[i];
+      if (i < warp) wpre += x;
+      ptot += x;
+    }
+    s_pre[tt] = pre + wpre + inc - v;
+    tsync<NW>();
+    const int cn = min(NT, n - c0);
+    int q = warp;
+    if (c0 == 0) {
+#pragma unroll
+      for (int k = 0; k < kRankTU; ++k, q += NW)
+        if (q < cn) rank_unit<S>(w, ((j0 + q) << 7) + 4 * lane, ext, wf[k], wp[k], s_pre[q], P, lane);
+    }
+    for (; q < cn; q += NW) {
+      const int base = ((j0 + c0 + q) << 7) + 4 * lane;
+      u32 a = 0, b = 0;
+      if (base < ext) {
+        a = ps.plane[S][0][base >> 5];
+        b = ps.plane[S][1][base >> 5];
+      }
+      rank_unit<S>(w, base, ext, a, b, s_pre[q], P, lane);
+    }
+    pre += ptot;
+    tsync<NW>();  // s_pre and s_red are rewritten by the next pass
+  }
+}
+
+// births on a team of NT threads (tid = the thread's place in it)
+template <int S, int NT>
+__device__ __forceinline__ void p_births(const WorldDev& w, int t, int r, int F, int ext, int id0, int tid) {
   const SpeciesDev& sp = w.sp[S];
   // birth i -> CTA i mod G: the births spread over all SMs
-  for (int i = blockIdx.x + gridDim.x * threadIdx.x; i < r; i += gridDim.x * kPT) {
+  for (int i = blockIdx.x + gridDim.x * tid; i < r; i += gridDim.x * NT) {
     const int p = sp.parents[i];
     const int slot = i < F ? sp.freel[i] : ext + (i - F);
     if (!in_range(p, sp.cap, w.err) || !in_range(slot, sp.cap, w.err)) continue;
@@ -637,50 +748,6 @@ __device__ __forceinline__ void p_births(const WorldDev& w, int t, int r, int F,
 struct Births {
   int r, F, ext, id0;
 };
-
-// A thread's first birth in two halves, so that other work runs between its
-// round trips: the parent and slot indices are loaded first (p < 0: none),
-// the parent's record and the writes come later (p_births_from, which also
-// takes the births beyond the first one per thread).
-struct FirstBirth {
-  int p, slot;
-};
-
-template <int S>
-__device__ __forceinline__ FirstBirth births_prefetch(const WorldDev& w, const Births& b) {
-  const SpeciesDev& sp = w.sp[S];
-  const int i = blockIdx.x + gridDim.x * threadIdx.x;
-  FirstBirth f{-1, 0};
-  if (i < b.r) {
-    f.p = sp.parents[i];
-    f.slot = i < b.F ? sp.freel[i] : b.ext + (i - b.F);
-  }
-  return f;
-}
-
-template <int S>
-__device__ __forceinline__ void births_finish(const WorldDev& w, int t, const Births& b, FirstBirth f) {
-  const SpeciesDev& sp = w.sp[S];
-  if (f.p >= 0 && in_range(f.p, sp.cap, w.err) && in_range(f.slot, sp.cap, w.err)) {
-    const int i = blockIdx.x + gridDim.x * threadIdx.x;
-    const int4 pa = sp.agent[f.p];
-    const int half = pa.y >> 1;
-    sp.agent[f.p].y = pa.y - half;
-    sp.agent[f.slot] = make_int4(pa.x, half, (int)((u32)b.id0 + (u32)i), 0);
-    sp.active[f.slot] = 1;
-  }
-  // births beyond one per thread (S == 1 only: wolf births carry no victim key)
-  for (int i = blockIdx.x + gridDim.x * (threadIdx.x + kPT); i < b.r; i += gridDim.x * kPT) {
-    const int p = sp.parents[i];
-    const int slot = i < b.F ? sp.freel[i] : b.ext + (i - b.F);
-    if (!in_range(p, sp.cap, w.err) || !in_range(slot, sp.cap, w.err)) continue;
-    const int4 pa = sp.agent[p];
-    const int half = pa.y >> 1;
-    sp.agent[p].y = pa.y - half;
-    sp.agent[slot] = make_int4(pa.x, half, (int)((u32)b.id0 + (u32)i), 0);
-    sp.active[slot] = 1;
-  }
-}
 
 __device__ __forceinline__ u64 globaltimer() {
   u64 t;
@@ -718,7 +785,9 @@ __global__ void __launch_bounds__(kPT, MINB) k_persistent(WorldDev w, int nsteps
   __shared__ u32 s_live[kRoundUnits * 4];
   __shared__ int s_cell[kRoundUnits * 128];
   __shared__ int s_energy[kRoundUnits * 128];
+  __shared__ int s_wolf[4];  // the wolf team's F, P, starved and eaten, for the whole CTA
   const CtaList cl{s_clist, s_wcnt, s_live, s_cell, s_energy};
+  const bool wolf_team = (int)threadIdx.x >= kSheepWarps * 32;
   int carried = -1;
   if (threadIdx.x < kRoundUnits * 4) s_upar[threadIdx.x] = 0u;
   PhaseClock clk{phase_ns, 0};
@@ -738,35 +807,48 @@ __global__ void __launch_bounds__(kPT, MINB) k_persistent(WorldDev w, int nsteps
   // Wolf ranks of step t-1 run beside the sheep moves of step t, and the wolf
   // moves of step t beside the sheep ranks: neither needs the other's
   // results, so a step takes five barrier-separated phases:
-  //   P1  wolf ranks (t-1), wolf counters and statistics | sheep move (t)
-  //   P2  wolf births (t-1) | sheep eat / select / die (t)
+  //   P1  wolf team: wolf ranks (t-1) | sheep team: sheep move (t)
+  //   P2  wolf counters and statistics (t-1) in every thread, then
+  //       wolf team: wolf births (t-1) | sheep team: sheep eat / select / die (t)
   //   P3  sheep ranks (t) | wolves move + victim claims (t) (a wolf only
   //       needs a live sheep on its cell: the survivors registered in P2)
   //   P4  sheep births (t) (lambs register as victims before wolves eat)
   //   P5  wolves eat / kill / select / die (t)
-  // and the last step's wolf ranks and births close the launch.
-  int kseg1 = 0, nstart1 = 0, r0p = 0, P0p = 0, starved0p = 0, grassp = 0;  // of the previous step
+  // and the last step's wolf ranks and births close the launch. In P1 and P2
+  // the two teams meet only at the grid barriers; P3 to P5 use every warp.
+  int kseg1 = 0, r0p = 0, P0p = 0, starved0p = 0, grassp = 0;  // of the previous step
   abm_step_stats* stp = nullptr;
-  auto wolf_ranks = [&](int tw /* step whose wolves are ranked */) {
-    int* accw = ps.acc + 4 * (tw & 1);
-    // the step's counters (complete since the last barrier), loaded before the
-    // rank phase so that their round trip overlaps its own loads
+  // wolf team: the ranks of step tw's wolves and that step's counters, left in s_wolf
+  auto wolf_ranks = [&](int tw) {
+    const int* accw = ps.acc + 4 * (tw & 1);
+    // complete since the last barrier; loaded ahead of the rank phase's own loads
     const int starved1 = accw[1], eaten = accw[2];
     u32 F1, P1;
-    rank_phase<1>(w, ext[1], kseg1, F1, P1, s_red, s_pre);
-    const int avail1 = (int)F1 + (cap[1] - ext[1]);
-    const int r1 = min((int)P1, avail1);
-    wb = {r1, (int)F1, ext[1], nid[1]};
+    rank_team<1>(w, ext[1], kseg1, F1, P1, s_red, s_pre);
+    if ((int)threadIdx.x == kSheepWarps * 32) {
+      s_wolf[0] = (int)F1;
+      s_wolf[1] = (int)P1;
+      s_wolf[2] = starved1;
+      s_wolf[3] = eaten;
+    }
+  };
+  // every thread: the counters after step tw's wolf births, from s_wolf
+  auto wolf_counters = [&](int tw) {
+    const int F1 = s_wolf[0], P1 = s_wolf[1], starved1 = s_wolf[2], eaten = s_wolf[3];
+    const int nstart1 = nact[1];
+    const int avail1 = F1 + (cap[1] - ext[1]);
+    const int r1 = min(P1, avail1);
+    wb = {r1, F1, ext[1], nid[1]};
     const int n_after = nstart1 + r1;
     if (n_after > hw[1]) hw[1] = n_after;
     nact[1] = n_after - starved1;
     nid[1] += r1;
-    if (r1 > (int)F1) ext[1] += r1 - (int)F1;
-    if ((int)P1 > avail1) ovf[1] = 1;
+    if (r1 > F1) ext[1] += r1 - F1;
+    if (P1 > avail1) ovf[1] = 1;
     nact[0] -= eaten;
     if (blockIdx.x == 0 && threadIdx.x == 0 && stp) {
       stp->parents[0] = P0p;
-      stp->parents[1] = (int)P1;
+      stp->parents[1] = P1;
       stp->births[0] = r0p;
       stp->births[1] = r1;
       stp->starved[0] = starved0p;
@@ -785,47 +867,52 @@ __global__ void __launch_bounds__(kPT, MINB) k_persistent(WorldDev w, int nsteps
     int* acc = ps.acc + 4 * (t & 1);
     abm_step_stats* st = stats ? stats + it : nullptr;
     // ---- P1: wolf ranks of the previous step | sheep move
-    u32 mf[kQ];
-    round_flags<0>(w, ext[0], 0, mf);  // issued before the wolf ranks, used by the sheep move
-    if (it > 0) wolf_ranks(t - 1);
-    if (blockIdx.x == 0 && threadIdx.x == 0) acc[0] = acc[1] = acc[2] = acc[3] = 0;  // last read in P1 of step t-1
-    const int nstart0 = nact[0];
-    nstart1 = nact[1];
-    p_move<0>(w, t, ext[0], cl, carried, mf);
-    if (blockIdx.x == 0 && threadIdx.x == 0 && st) {
-      st->n_start[0] = nstart0;
-      st->n_start[1] = nstart1;
-      st->extent[0] = ext[0];
-      st->extent[1] = ext[1];
+    if (wolf_team) {
+      if (it > 0) wolf_ranks(t - 1);
+    } else {
+      u32 mf[kQ];
+      round_flags<0, kSheepWarps>(w, ext[0], 0, mf);
+      if (blockIdx.x == 0 && threadIdx.x == 0) acc[0] = acc[1] = acc[2] = acc[3] = 0;  // last read in P1 of step t-1
+      p_move<0, kSheepWarps>(w, t, ext[0], cl, carried, mf);
     }
     grid_sync(ps.bar, w.err, bar_target);
     clk.lap(0);
     if (*(volatile int*)w.err) return;
-    // ---- P2: wolf births of the previous step | sheep eat / select / die / flags
-    // the previous step's wolf births around the sheep's eat/select/die: their
-    // index loads are in flight while the sheep work runs
-    const FirstBirth fb = it > 0 ? births_prefetch<1>(w, wb) : FirstBirth{-1, 0};
-    if (blockIdx.x == 0)  // wolf segment sums: last read in P1
-      for (int j = threadIdx.x; j < (int)gridDim.x; j += kPT) ps.seg[1][j] = 0ull;
+    // ---- P2: wolf counters (t-1) | wolf births (t-1) beside sheep eat / select / die / flags
+    if (it > 0) wolf_counters(t - 1);
+    const int nstart0 = nact[0];
+    if (blockIdx.x == 0 && threadIdx.x == 0 && st) {
+      st->n_start[0] = nstart0;
+      st->n_start[1] = nact[1];
+      st->extent[0] = ext[0];
+      st->extent[1] = ext[1];
+    }
     const int kseg0 = (((ext[0] + 127) >> 7) + (int)gridDim.x - 1) / (int)gridDim.x;
-    p_count<0>(w, t, ext[0], kseg0, acc, cl, carried, s_upar, s_acc);
-    if (it > 0) births_finish<1>(w, t - 1, wb, fb);
+    if (wolf_team) {
+      if (it > 0)
+        p_births<1, kWolfWarps * 32>(w, t - 1, wb.r, wb.F, wb.ext, wb.id0, (int)threadIdx.x - kSheepWarps * 32);
+    } else {
+      if (blockIdx.x == 0)  // wolf segment sums: last read in P1
+        for (int j = threadIdx.x; j < (int)gridDim.x; j += kSheepWarps * 32) ps.seg[1][j] = 0ull;
+      p_count<0, kSheepWarps>(w, t, ext[0], kseg0, acc, cl, carried, s_upar, s_acc);
+    }
     grid_sync(ps.bar, w.err, bar_target);
     clk.lap(1);
     // ---- P3: sheep ranks and lists | wolves move + claims
-    round_flags<1>(w, ext[1], 0, mf);  // issued before the sheep ranks, used by the wolf move
+    u32 mf[kQ];
+    round_flags<1, kPWarps>(w, ext[1], 0, mf);  // issued before the sheep ranks, used by the wolf move
     u32 F0, P0;
     rank_phase<0>(w, ext[0], kseg0, F0, P0, s_red, s_pre);
     const int avail0 = (int)F0 + (cap[0] - ext[0]);
     const int r0 = min((int)P0, avail0);
     const Births sb = {r0, (int)F0, ext[0], nid[0]};
-    p_move<1>(w, t, ext[1], cl, carried, mf);
+    p_move<1, kPWarps>(w, t, ext[1], cl, carried, mf);
     grid_sync(ps.bar, w.err, bar_target);
     clk.lap(2);
     // ---- P4: sheep births; sheep counters
     starved0p = acc[0];  // written in P2: loaded ahead of the births' own loads
     grassp = acc[3];
-    p_births<0>(w, t, sb.r, sb.F, sb.ext, sb.id0);
+    p_births<0, kPT>(w, t, sb.r, sb.F, sb.ext, sb.id0, threadIdx.x);
     if (blockIdx.x == 0)  // sheep segment sums: last read in P3
       for (int j = threadIdx.x; j < (int)gridDim.x; j += kPT) ps.seg[0][j] = 0ull;
     {
@@ -842,7 +929,7 @@ __global__ void __launch_bounds__(kPT, MINB) k_persistent(WorldDev w, int nsteps
     clk.lap(3);
     // ---- P5: wolves eat / kill / select / die / flags
     kseg1 = (((ext[1] + 127) >> 7) + (int)gridDim.x - 1) / (int)gridDim.x;
-    p_count<1>(w, t, ext[1], kseg1, acc, cl, carried, s_upar, s_acc);
+    p_count<1, kPWarps>(w, t, ext[1], kseg1, acc, cl, carried, s_upar, s_acc);
     stp = st;
     ++t;
     grid_sync(ps.bar, w.err, bar_target);
@@ -850,10 +937,12 @@ __global__ void __launch_bounds__(kPT, MINB) k_persistent(WorldDev w, int nsteps
   }
   // the last step's wolf ranks and births
   if (nsteps > 0) {
-    wolf_ranks(t - 1);
+    if (wolf_team) wolf_ranks(t - 1);
+    __syncthreads();
+    wolf_counters(t - 1);
     grid_sync(ps.bar, w.err, bar_target);
     clk.lap(5);
-    p_births<1>(w, t - 1, wb.r, wb.F, wb.ext, wb.id0);
+    p_births<1, kPT>(w, t - 1, wb.r, wb.F, wb.ext, wb.id0, threadIdx.x);
     if (blockIdx.x == 0)  // wolf segment sums, for the next launch
       for (int j = threadIdx.x; j < (int)gridDim.x; j += kPT) ps.seg[1][j] = 0ull;
   }
