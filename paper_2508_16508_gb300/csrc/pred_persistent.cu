@@ -33,7 +33,9 @@ constexpr int kPhases = 5;                // grid barriers per step (plus one cl
 // a release add after its threads meet at __syncthreads and waits with
 // acquire loads, so everything written before the barrier anywhere in the
 // grid is visible after it. A wait that runs out records an error and
-// proceeds (results are then invalid, but the kernel ends).
+// proceeds (results are then invalid, but the kernel ends). Returns, in every
+// thread, whether an error was recorded (by the time this CTA arrived, or
+// during its wait): the error word is read while waiting, not after.
 __device__ __forceinline__ u32 ld_acquire32(const u32* p) {
   u32 v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -44,25 +46,34 @@ __device__ __forceinline__ void red_release_add(u32* p, u32 v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ void grid_sync(u32* bar, int* err, u32& target, u32 expected = 0, int limit = kBarSpin) {
+__device__ __forceinline__ bool grid_sync(u32* bar, int* err, u32& target, u32 expected = 0, int limit = kBarSpin) {
+  __shared__ int s_bad;
   target += expected == 0 ? gridDim.x : expected;
   __syncthreads();
   if (threadIdx.x == 0) {
     red_release_add(bar, 1u);
+    // in flight during the first polls
+    int bad = ld_relaxed32(reinterpret_cast<const u32*>(err)) != 0u;
     int spins = 0;
     u32 backoff = 8;
     while ((int)(ld_acquire32(bar) - target) < 0) {
       if (++spins > limit) {
-        atomicExch(err, kErrTimeout);
+        atomicCAS(err, 0, kErrTimeout);  // the first error recorded is the one reported
+        bad = 1;
         break;
       }
       // another CTA gave up (checked now and then: one round trip per poll)
-      if ((spins & 63) == 0 && ld_relaxed32(reinterpret_cast<const u32*>(err)) != 0u) break;
+      if ((spins & 63) == 0 && ld_relaxed32(reinterpret_cast<const u32*>(err)) != 0u) {
+        bad = 1;
+        break;
+      }
       __nanosleep(backoff);
       if (backoff < 32) backoff <<= 1;
     }
+    s_bad = bad;
   }
   __syncthreads();
+  return s_bad != 0;
 }
 
 // Teams: in phases 1 and 2 a CTA splits into a sheep team (warps 0 ..
@@ -553,15 +564,27 @@ __device__ __forceinline__ void p_ranks(const WorldDev& w, int ext, int kseg, u3
   }
 }
 
+// Stage the two plane-word quads (free, parent: the 4 words of 128 slots) of
+// units j0 .. j0 + min(n, nu) - 1 into s_pw[8 * q + 4 * plane + word] with
+// 16-byte cp.async, threads tid < 2 * nu (one quad each); commits a group.
+template <int S>
+__device__ __forceinline__ void stage_planes(const PersistDev& ps, int j0, int n, int nu, int tid, u32* s_pw) {
+  if (tid < 2 * nu) {
+    const int q = tid >> 1, pl = tid & 1;
+    if (q < n) cp_async16(s_pw + 8 * q + 4 * pl, ps.plane[S][pl] + 4 * (j0 + q));
+  }
+  cp_async_commit();
+}
+
 // A rank phase (grand totals + ranks). When this CTA's run of units is short
 // (kseg <= kPWarps * kRankU, the common case) every load -- the segment sums,
-// the unit counts, the plane words -- is issued up front, so the phase costs
-// one memory round trip instead of three.
+// the unit counts, the plane words (cp.async into shared memory) -- is issued
+// up front, so the phase costs one memory round trip instead of three.
 constexpr int kRankU = 4;
 
 template <int S>
 __device__ __forceinline__ void rank_phase(const WorldDev& w, int ext, int kseg, u32& F, u32& P, u64* s_red,
-                                           u64* s_pre) {
+                                           u64* s_pre, u32* s_pw /* [kPWarps * kRankU][2][4], 16-byte aligned */) {
   const PersistDev& ps = w.ps;
   if (kseg > kPWarps * kRankU || (int)gridDim.x > kPT) {
     u32 preF, preP;
@@ -573,20 +596,9 @@ __device__ __forceinline__ void rank_phase(const WorldDev& w, int ext, int kseg,
   const int nblk = (ext + 127) >> 7;
   const int j0 = blockIdx.x * kseg, j1 = min(nblk, j0 + kseg);
   const int n = max(0, j1 - j0);
+  stage_planes<S>(ps, j0, n, kPWarps * kRankU, threadIdx.x, s_pw);
   const u64 sv = threadIdx.x < (int)gridDim.x ? ps.seg[S][threadIdx.x] : 0ull;
   const u64 bv = threadIdx.x < n ? ps.blk[S][j0 + threadIdx.x] : 0ull;
-  u32 wf[kRankU], wp[kRankU];
-#pragma unroll
-  for (int k = 0; k < kRankU; ++k) {
-    const int q = warp + kPWarps * k;
-    const int base = ((j0 + q) << 7) + 4 * lane;
-    wf[k] = 0u;
-    wp[k] = 0u;
-    if (q < n && base < ext) {
-      wf[k] = ps.plane[S][0][base >> 5];
-      wp[k] = ps.plane[S][1][base >> 5];
-    }
-  }
   // grand totals and the sums of the segments before this CTA's
   u64 tot = sv, pre = (int)threadIdx.x < (int)blockIdx.x ? sv : 0ull;
 #pragma unroll
@@ -608,6 +620,7 @@ __device__ __forceinline__ void rank_phase(const WorldDev& w, int ext, int kseg,
   F = (u32)(tot >> 32);
   P = (u32)tot;
   const u32 preF = (u32)(pre >> 32), preP = (u32)pre;
+  cp_async_wait_0();  // the staged plane words: visible to the CTA after the barrier
   __syncthreads();  // s_red is reused by the scan
   // unit prefixes inside the run
   u32 exf, exp_, tf, tp;
@@ -618,41 +631,35 @@ __device__ __forceinline__ void rank_phase(const WorldDev& w, int ext, int kseg,
   for (int k = 0; k < kRankU; ++k) {
     const int q = warp + kPWarps * k;
     if (q >= n) break;
-    rank_unit<S>(w, ((j0 + q) << 7) + 4 * lane, ext, wf[k], wp[k], s_pre[q], P, lane);
+    rank_unit<S>(w, ((j0 + q) << 7) + 4 * lane, ext, s_pw[8 * q + (lane >> 3)], s_pw[8 * q + 4 + (lane >> 3)],
+                 s_pre[q], P, lane);
   }
   __syncthreads();  // s_pre and s_red are reused
 }
 
 // A rank phase on the wolf team (kWolfWarps warps, named barrier 2) while the
 // sheep team moves the sheep: the same lists as rank_phase. The segment sums,
-// the first pass's unit counts and the plane words of each warp's first
-// kRankTU units are all loaded up front, in one round trip; longer runs of
-// units take further passes of one unit count per team thread.
+// the first pass's unit counts and the plane words of the first
+// kRankTU * kWolfWarps units are all requested up front, in one round trip
+// (the plane words by cp.async into shared memory, 32 bytes a unit, so that
+// they hold no registers); longer runs of units take further passes of one
+// unit count per team thread.
 constexpr int kRankTU = 8;
 
 template <int S>
 __device__ __forceinline__ void rank_team(const WorldDev& w, int ext, int kseg, u32& F, u32& P,
-                                          u64* s_red /* [2 * kWolfWarps] */, u64* s_pre /* [kWolfWarps * 32] */) {
-  constexpr int NW = kWolfWarps, NT = NW * 32;
+                                          u64* s_red /* [2 * kWolfWarps] */,
+                                          u64* s_pre /* [kWolfWarps * 32 + 2 * kRankTU * kWolfWarps] */) {
+  constexpr int NW = kWolfWarps, NT = NW * 32, NU = kRankTU * NW;
   const PersistDev& ps = w.ps;
   const int tt = (int)threadIdx.x - kSheepWarps * 32;
   const int warp = tt >> 5, lane = tt & 31;
   const int nblk = (ext + 127) >> 7;
   const int j0 = blockIdx.x * kseg, j1 = min(nblk, j0 + kseg);
   const int n = max(0, j1 - j0);
+  u32* s_pw = reinterpret_cast<u32*>(s_pre + NT);  // [NU][2][4] plane words of the first NU units
+  stage_planes<S>(ps, j0, n, NU, tt, s_pw);
   const u64 bv0 = tt < n ? ps.blk[S][j0 + tt] : 0ull;
-  u32 wf[kRankTU], wp[kRankTU];
-#pragma unroll
-  for (int k = 0; k < kRankTU; ++k) {
-    const int q = warp + NW * k;
-    const int base = ((j0 + q) << 7) + 4 * lane;
-    wf[k] = 0u;
-    wp[k] = 0u;
-    if (q < n && base < ext) {
-      wf[k] = ps.plane[S][0][base >> 5];
-      wp[k] = ps.plane[S][1][base >> 5];
-    }
-  }
   // grand totals and the sums of the segments before this CTA's
   u64 tot = 0, pre = 0;
   for (int j = tt; j < (int)gridDim.x; j += NT) {
@@ -669,6 +676,7 @@ __device__ __forceinline__ void rank_team(const WorldDev& w, int ext, int kseg, 
     s_red[2 * warp] = tot;
     s_red[2 * warp + 1] = pre;
   }
+  cp_async_wait_0();  // the staged plane words: visible to the team after the barrier
   tsync<NW>();
   tot = pre = 0;
 #pragma unroll
@@ -705,7 +713,9 @@ __device__ __forceinline__ void rank_team(const WorldDev& w, int ext, int kseg, 
     if (c0 == 0) {
 #pragma unroll
       for (int k = 0; k < kRankTU; ++k, q += NW)
-        if (q < cn) rank_unit<S>(w, ((j0 + q) << 7) + 4 * lane, ext, wf[k], wp[k], s_pre[q], P, lane);
+        if (q < cn)
+          rank_unit<S>(w, ((j0 + q) << 7) + 4 * lane, ext, s_pw[8 * q + (lane >> 3)], s_pw[8 * q + 4 + (lane >> 3)],
+                       s_pre[q], P, lane);
     }
     for (; q < cn; q += NW) {
       const int base = ((j0 + c0 + q) << 7) + 4 * lane;
@@ -755,18 +765,31 @@ __device__ __forceinline__ u64 globaltimer() {
   return t;
 }
 
+// Bookkeeping that no phase reads: the live counts, high-water marks,
+// overflow flags and per-step statistics. Block 0's thread 0 keeps it in
+// shared memory, so that it takes no registers of the other threads (a
+// register spilled to local memory costs a round trip at a phase boundary).
+struct StepBook {
+  int nact[2], hw[2], ovf[2];
+  int nstart0, r0p, P0p, starved0p, grassp;  // of the previous step's sheep
+  abm_step_stats* stp;                       // statistics row of the previous step
+  u64 clk_last;                              // phase timing (block 0)
+};
+
+__device__ __forceinline__ bool book_thread() { return blockIdx.x == 0 && threadIdx.x == 0; }
+
 // phase timing by block 0 (nanoseconds from one barrier exit to the next)
 struct PhaseClock {
   unsigned long long* acc;
-  u64 last;
+  StepBook& b;
   __device__ __forceinline__ void start() {
-    if (acc && blockIdx.x == 0 && threadIdx.x == 0) last = globaltimer();
+    if (acc && book_thread()) b.clk_last = globaltimer();
   }
   __device__ __forceinline__ void lap(int k) {
-    if (acc && blockIdx.x == 0 && threadIdx.x == 0) {
+    if (acc && book_thread()) {
       const u64 now = globaltimer();
-      acc[k] += now - last;
-      last = now;
+      acc[k] += now - b.clk_last;
+      b.clk_last = now;
     }
   }
 };
@@ -777,33 +800,38 @@ template <int MINB>
 __global__ void __launch_bounds__(kPT, MINB) k_persistent(WorldDev w, int nsteps, abm_step_stats* stats,
                                                      unsigned long long* phase_ns) {
   __shared__ u64 s_red[2 * kPWarps];
-  __shared__ u64 s_pre[kPT];
+  __shared__ __align__(16) u64 s_pre[kPT];
   __shared__ unsigned short s_clist[kRoundUnits * 128];
   __shared__ int s_wcnt[kRoundUnits];
   __shared__ u32 s_upar[kRoundUnits * 4];
   __shared__ int s_acc[2 * kPWarps];
   __shared__ u32 s_live[kRoundUnits * 4];
-  __shared__ int s_cell[kRoundUnits * 128];
+  __shared__ __align__(16) int s_cell[kRoundUnits * 128];
   __shared__ int s_energy[kRoundUnits * 128];
   __shared__ int s_wolf[4];  // the wolf team's F, P, starved and eaten, for the whole CTA
+  __shared__ StepBook s_book;
   const CtaList cl{s_clist, s_wcnt, s_live, s_cell, s_energy};
   const bool wolf_team = (int)threadIdx.x >= kSheepWarps * 32;
   int carried = -1;
   if (threadIdx.x < kRoundUnits * 4) s_upar[threadIdx.x] = 0u;
-  PhaseClock clk{phase_ns, 0};
-  clk.start();
+  PhaseClock clk{phase_ns, s_book};
   u32 bar_target = w.bar_base;  // arrival count that completes the next barrier
   WorldCtr* c = w.ctr;
   const PersistDev& ps = w.ps;
-  // counters: one copy per thread, all updated identically
+  // counters the phases read: one copy per thread, all updated identically
   int t = c->step;
   int ext[2] = {c->extent[0], c->extent[1]};
-  int nact[2] = {c->n_active[0], c->n_active[1]};
   int nid[2] = {c->next_id[0], c->next_id[1]};
-  int hw[2] = {c->hw[0], c->hw[1]};
-  int ovf[2] = {c->overflow[0], c->overflow[1]};
-  const int cap[2] = {w.sp[0].cap, w.sp[1].cap};
-  Births wb = {0, 0, 0, 0};  // wolf births pending from the previous step
+  if (book_thread()) {
+    for (int s2 = 0; s2 < 2; ++s2) {
+      s_book.nact[s2] = c->n_active[s2];
+      s_book.hw[s2] = c->hw[s2];
+      s_book.ovf[s2] = c->overflow[s2];
+    }
+    s_book.nstart0 = s_book.r0p = s_book.P0p = s_book.starved0p = s_book.grassp = 0;
+    s_book.stp = nullptr;
+  }
+  clk.start();
   // Wolf ranks of step t-1 run beside the sheep moves of step t, and the wolf
   // moves of step t beside the sheep ranks: neither needs the other's
   // results, so a step takes five barrier-separated phases:
@@ -816,14 +844,14 @@ __global__ void __launch_bounds__(kPT, MINB) k_persistent(WorldDev w, int nsteps
   //   P5  wolves eat / kill / select / die (t)
   // and the last step's wolf ranks and births close the launch. In P1 and P2
   // the two teams meet only at the grid barriers; P3 to P5 use every warp.
-  int kseg1 = 0, r0p = 0, P0p = 0, starved0p = 0, grassp = 0;  // of the previous step
-  abm_step_stats* stp = nullptr;
   // wolf team: the ranks of step tw's wolves and that step's counters, left in s_wolf
   auto wolf_ranks = [&](int tw) {
     const int* accw = ps.acc + 4 * (tw & 1);
-    // complete since the last barrier; loaded ahead of the rank phase's own loads
-    const int starved1 = accw[1], eaten = accw[2];
+    // complete since the last barrier; loaded ahead of the rank phase's own
+    // loads (for the bookkeeping of block 0 only)
+    const int starved1 = blockIdx.x == 0 ? accw[1] : 0, eaten = blockIdx.x == 0 ? accw[2] : 0;
     u32 F1, P1;
+    const int kseg1 = (((ext[1] + 127) >> 7) + (int)gridDim.x - 1) / (int)gridDim.x;  // as in the count phase
     rank_team<1>(w, ext[1], kseg1, F1, P1, s_red, s_pre);
     if ((int)threadIdx.x == kSheepWarps * 32) {
       s_wolf[0] = (int)F1;
@@ -833,39 +861,44 @@ __global__ void __launch_bounds__(kPT, MINB) k_persistent(WorldDev w, int nsteps
     }
   };
   // every thread: the counters after step tw's wolf births, from s_wolf
-  auto wolf_counters = [&](int tw) {
-    const int F1 = s_wolf[0], P1 = s_wolf[1], starved1 = s_wolf[2], eaten = s_wolf[3];
-    const int nstart1 = nact[1];
-    const int avail1 = F1 + (cap[1] - ext[1]);
+  // (the bookkeeping and step tw's statistics: block 0's thread 0); returns
+  // the births to place
+  auto wolf_counters = [&](int tw) -> Births {
+    const int F1 = s_wolf[0], P1 = s_wolf[1];
+    const int avail1 = F1 + (w.sp[1].cap - ext[1]);
     const int r1 = min(P1, avail1);
-    wb = {r1, F1, ext[1], nid[1]};
-    const int n_after = nstart1 + r1;
-    if (n_after > hw[1]) hw[1] = n_after;
-    nact[1] = n_after - starved1;
+    const Births wb = {r1, F1, ext[1], nid[1]};
     nid[1] += r1;
     if (r1 > F1) ext[1] += r1 - F1;
-    if (P1 > avail1) ovf[1] = 1;
-    nact[0] -= eaten;
-    if (blockIdx.x == 0 && threadIdx.x == 0 && stp) {
-      stp->parents[0] = P0p;
-      stp->parents[1] = P1;
-      stp->births[0] = r0p;
-      stp->births[1] = r1;
-      stp->starved[0] = starved0p;
-      stp->starved[1] = starved1;
-      stp->eaten = eaten;
-      stp->grass_eaten = grassp;
-      for (int s2 = 0; s2 < 2; ++s2) {
-        stp->n_end[s2] = nact[s2];
-        stp->hw[s2] = hw[s2];
-        stp->overflow[s2] = ovf[s2];
+    if (book_thread()) {
+      StepBook& b = s_book;
+      const int starved1 = s_wolf[2], eaten = s_wolf[3];
+      const int n_after = b.nact[1] + r1;
+      if (n_after > b.hw[1]) b.hw[1] = n_after;
+      b.nact[1] = n_after - starved1;
+      if (P1 > avail1) b.ovf[1] = 1;
+      b.nact[0] -= eaten;
+      if (abm_step_stats* stp = b.stp) {
+        stp->parents[0] = b.P0p;
+        stp->parents[1] = P1;
+        stp->births[0] = b.r0p;
+        stp->births[1] = r1;
+        stp->starved[0] = b.starved0p;
+        stp->starved[1] = starved1;
+        stp->eaten = eaten;
+        stp->grass_eaten = b.grassp;
+        for (int s2 = 0; s2 < 2; ++s2) {
+          stp->n_end[s2] = b.nact[s2];
+          stp->hw[s2] = b.hw[s2];
+          stp->overflow[s2] = b.ovf[s2];
+        }
+        stp->step = tw;
       }
-      stp->step = tw;
     }
+    return wb;
   };
   for (int it = 0; it < nsteps; ++it) {
     int* acc = ps.acc + 4 * (t & 1);
-    abm_step_stats* st = stats ? stats + it : nullptr;
     // ---- P1: wolf ranks of the previous step | sheep move
     if (wolf_team) {
       if (it > 0) wolf_ranks(t - 1);
@@ -875,17 +908,20 @@ __global__ void __launch_bounds__(kPT, MINB) k_persistent(WorldDev w, int nsteps
       if (blockIdx.x == 0 && threadIdx.x == 0) acc[0] = acc[1] = acc[2] = acc[3] = 0;  // last read in P1 of step t-1
       p_move<0, kSheepWarps>(w, t, ext[0], cl, carried, mf);
     }
-    grid_sync(ps.bar, w.err, bar_target);
+    const bool bad = grid_sync(ps.bar, w.err, bar_target);
     clk.lap(0);
-    if (*(volatile int*)w.err) return;
+    if (bad) return;
     // ---- P2: wolf counters (t-1) | wolf births (t-1) beside sheep eat / select / die / flags
-    if (it > 0) wolf_counters(t - 1);
-    const int nstart0 = nact[0];
-    if (blockIdx.x == 0 && threadIdx.x == 0 && st) {
-      st->n_start[0] = nstart0;
-      st->n_start[1] = nact[1];
-      st->extent[0] = ext[0];
-      st->extent[1] = ext[1];
+    const Births wb = it > 0 ? wolf_counters(t - 1) : Births{0, 0, 0, 0};
+    if (book_thread()) {
+      s_book.nstart0 = s_book.nact[0];
+      if (stats) {
+        abm_step_stats* st = stats + it;
+        st->n_start[0] = s_book.nact[0];
+        st->n_start[1] = s_book.nact[1];
+        st->extent[0] = ext[0];
+        st->extent[1] = ext[1];
+      }
     }
     const int kseg0 = (((ext[0] + 127) >> 7) + (int)gridDim.x - 1) / (int)gridDim.x;
     if (wolf_team) {
@@ -902,35 +938,42 @@ __global__ void __launch_bounds__(kPT, MINB) k_persistent(WorldDev w, int nsteps
     u32 mf[kQ];
     round_flags<1, kPWarps>(w, ext[1], 0, mf);  // issued before the sheep ranks, used by the wolf move
     u32 F0, P0;
-    rank_phase<0>(w, ext[0], kseg0, F0, P0, s_red, s_pre);
-    const int avail0 = (int)F0 + (cap[0] - ext[0]);
+    // (s_cell is free between the count phase and the wolf move: plane staging)
+    rank_phase<0>(w, ext[0], kseg0, F0, P0, s_red, s_pre, reinterpret_cast<u32*>(s_cell));
+    const int avail0 = (int)F0 + (w.sp[0].cap - ext[0]);
     const int r0 = min((int)P0, avail0);
     const Births sb = {r0, (int)F0, ext[0], nid[0]};
     p_move<1, kPWarps>(w, t, ext[1], cl, carried, mf);
     grid_sync(ps.bar, w.err, bar_target);
     clk.lap(2);
     // ---- P4: sheep births; sheep counters
-    starved0p = acc[0];  // written in P2: loaded ahead of the births' own loads
-    grassp = acc[3];
+    int starved0 = 0, grass = 0;
+    if (book_thread()) {  // written in P2: loaded ahead of the births' own loads
+      starved0 = acc[0];
+      grass = acc[3];
+    }
     p_births<0, kPT>(w, t, sb.r, sb.F, sb.ext, sb.id0, threadIdx.x);
     if (blockIdx.x == 0)  // sheep segment sums: last read in P3
       for (int j = threadIdx.x; j < (int)gridDim.x; j += kPT) ps.seg[0][j] = 0ull;
-    {
-      const int n_after = nstart0 + r0;
-      if (n_after > hw[0]) hw[0] = n_after;
-      nact[0] = n_after - starved0p;
-      nid[0] += r0;
-      if (r0 > (int)F0) ext[0] += r0 - (int)F0;
-      if ((int)P0 > avail0) ovf[0] = 1;
+    nid[0] += r0;
+    if (r0 > (int)F0) ext[0] += r0 - (int)F0;
+    if (book_thread()) {
+      StepBook& b = s_book;
+      const int n_after = b.nstart0 + r0;
+      if (n_after > b.hw[0]) b.hw[0] = n_after;
+      b.nact[0] = n_after - starved0;
+      if ((int)P0 > avail0) b.ovf[0] = 1;
+      b.r0p = r0;
+      b.P0p = (int)P0;
+      b.starved0p = starved0;
+      b.grassp = grass;
     }
-    r0p = r0;
-    P0p = (int)P0;
     grid_sync(ps.bar, w.err, bar_target);
     clk.lap(3);
     // ---- P5: wolves eat / kill / select / die / flags
-    kseg1 = (((ext[1] + 127) >> 7) + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int kseg1 = (((ext[1] + 127) >> 7) + (int)gridDim.x - 1) / (int)gridDim.x;
     p_count<1, kPWarps>(w, t, ext[1], kseg1, acc, cl, carried, s_upar, s_acc);
-    stp = st;
+    if (book_thread()) s_book.stp = stats ? stats + it : nullptr;
     ++t;
     grid_sync(ps.bar, w.err, bar_target);
     clk.lap(4);
@@ -939,7 +982,7 @@ __global__ void __launch_bounds__(kPT, MINB) k_persistent(WorldDev w, int nsteps
   if (nsteps > 0) {
     if (wolf_team) wolf_ranks(t - 1);
     __syncthreads();
-    wolf_counters(t - 1);
+    const Births wb = wolf_counters(t - 1);
     grid_sync(ps.bar, w.err, bar_target);
     clk.lap(5);
     p_births<1, kPT>(w, t - 1, wb.r, wb.F, wb.ext, wb.id0, threadIdx.x);
@@ -950,10 +993,10 @@ __global__ void __launch_bounds__(kPT, MINB) k_persistent(WorldDev w, int nsteps
     c->step = t;
     for (int s = 0; s < 2; ++s) {
       c->extent[s] = ext[s];
-      c->n_active[s] = nact[s];
+      c->n_active[s] = s_book.nact[s];
       c->next_id[s] = nid[s];
-      c->hw[s] = hw[s];
-      c->overflow[s] = ovf[s];
+      c->hw[s] = s_book.hw[s];
+      c->overflow[s] = s_book.ovf[s];
     }
   }
 }
