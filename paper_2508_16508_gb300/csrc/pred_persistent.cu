@@ -46,12 +46,18 @@ __device__ __forceinline__ void red_release_add(u32* p, u32 v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ bool grid_sync(u32* bar, int* err, u32& target, u32 expected = 0, int limit = kBarSpin) {
-  __shared__ int s_bad;
+// A grid barrier in two halves, so that independent work can run between
+// them: grid_arrive counts this CTA in (after its threads meet), grid_wait
+// waits for the whole grid.
+__device__ __forceinline__ void grid_arrive(u32* bar, u32& target, u32 expected = 0) {
   target += expected == 0 ? gridDim.x : expected;
   __syncthreads();
+  if (threadIdx.x == 0) red_release_add(bar, 1u);
+}
+
+__device__ __forceinline__ bool grid_wait(u32* bar, int* err, u32 target, int limit = kBarSpin) {
+  __shared__ int s_bad;
   if (threadIdx.x == 0) {
-    red_release_add(bar, 1u);
     // in flight during the first polls
     int bad = ld_relaxed32(reinterpret_cast<const u32*>(err)) != 0u;
     int spins = 0;
@@ -74,6 +80,11 @@ __device__ __forceinline__ bool grid_sync(u32* bar, int* err, u32& target, u32 e
   }
   __syncthreads();
   return s_bad != 0;
+}
+
+__device__ __forceinline__ bool grid_sync(u32* bar, int* err, u32& target, u32 expected = 0, int limit = kBarSpin) {
+  grid_arrive(bar, target, expected);
+  return grid_wait(bar, err, target, limit);
 }
 
 // Teams: in phases 1 and 2 a CTA splits into a sheep team (warps 0 ..
@@ -844,6 +855,11 @@ __global__ void __launch_bounds__(kPT, MINB) k_persistent(WorldDev w, int nsteps
   //   P5  wolves eat / kill / select / die (t)
   // and the last step's wolf ranks and births close the launch. In P1 and P2
   // the two teams meet only at the grid barriers; P3 to P5 use every warp.
+  // The barrier between P3 and P4 is split: a CTA counts itself in once its
+  // ranks are written and waits only after its wolf moves, so the wait
+  // overlaps the wolf moves (births touch no wolf, and a lamb lands on its
+  // parent's cell, which already holds a victim key, so no claim condition of
+  // the wolf move changes under it).
   // wolf team: the ranks of step tw's wolves and that step's counters, left in s_wolf
   auto wolf_ranks = [&](int tw) {
     const int* accw = ps.acc + 4 * (tw & 1);
@@ -943,17 +959,19 @@ __global__ void __launch_bounds__(kPT, MINB) k_persistent(WorldDev w, int nsteps
     const int avail0 = (int)F0 + (w.sp[0].cap - ext[0]);
     const int r0 = min((int)P0, avail0);
     const Births sb = {r0, (int)F0, ext[0], nid[0]};
+    // the ranks' half of the barrier; the wolf move needs none of them
+    grid_arrive(ps.bar, bar_target);
     p_move<1, kPWarps>(w, t, ext[1], cl, carried, mf);
-    grid_sync(ps.bar, w.err, bar_target);
+    grid_wait(ps.bar, w.err, bar_target);
     clk.lap(2);
-    // ---- P4: sheep births; sheep counters
+    // ---- P4 (same phase): sheep births (every CTA's lists are complete); sheep counters
     int starved0 = 0, grass = 0;
     if (book_thread()) {  // written in P2: loaded ahead of the births' own loads
       starved0 = acc[0];
       grass = acc[3];
     }
     p_births<0, kPT>(w, t, sb.r, sb.F, sb.ext, sb.id0, threadIdx.x);
-    if (blockIdx.x == 0)  // sheep segment sums: last read in P3
+    if (blockIdx.x == 0)  // sheep segment sums: last read by the rank phases
       for (int j = threadIdx.x; j < (int)gridDim.x; j += kPT) ps.seg[0][j] = 0ull;
     nid[0] += r0;
     if (r0 > (int)F0) ext[0] += r0 - (int)F0;
