@@ -868,9 +868,9 @@ def run_ours(args, rank, world, local):
         ev = [torch.cuda.Event() for _ in range(2)]
         n_start = abm.STATS_FIELD_OFFSETS["n_start"] // 4  # int32 words of n_start[0], n_start[1]
         ew.step(W)
-        nb = ew.image_bytes()
+        nb = ew.image_bytes()  # the checkpoint image of the state: slots up to the extents
         img_in = torch.empty(nb, dtype=torch.uint8).pin_memory()
-        img_out = torch.empty(nb, dtype=torch.uint8).pin_memory()
+        img_out = torch.empty(ew.image_capacity(), dtype=torch.uint8).pin_memory()  # fits any final state
         ew.save_into(img_in)  # the state after the warm-up steps, as a host checkpoint
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -888,16 +888,17 @@ def run_ours(args, rank, world, local):
                 b = (i - 1) & 1
                 ev[b].synchronize()
                 ea += int(sview[b][0, n_start]) + int(sview[b][0, n_start + 1])
-        ew.save_into(img_out)  # the run's output: the whole state, device -> host
+        nb_out = ew.save_into(img_out)  # the run's output: the whole state, device -> host
         e2e_dt = time.perf_counter() - t0
         line["e2e"] = {"value": ea / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": nb / max(ne, 1),
-                       "d2h_bytes_per_step": abm.STATS_BYTES + nb / max(ne, 1),
-                       "steps": ne, "state_bytes": nb,
+                       "d2h_bytes_per_step": abm.STATS_BYTES + nb_out / max(ne, 1),
+                       "steps": ne, "state_bytes": nb, "state_bytes_out": nb_out,
                        "same_trajectory_as_timed_run": ew.counters() == gw.counters(),
                        "note": "abm_load of the state from pinned host memory, then per step one abm_step "
                                "call whose statistics row is copied to pinned host memory and read by the "
                                "host one step later (double-buffered), then abm_save of the final state "
-                               "to pinned host memory; wall clock"}
+                               "to pinned host memory (checkpoint images hold the slots up to each "
+                               "species' extent); wall clock"}
         del ew, img_in, img_out
         line["selective_update"] = selective_update_leg(torch, engine, abm, autotune, hbm_peak)
         line["batched"] = batched_leg(torch, engine, capacity, autotune, abm, hbm_peak)

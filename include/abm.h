@@ -459,11 +459,23 @@ typedef struct abm_world_counters {
 /* Host copy of the counters (synchronises `stream`). */
 abm_status abm_world_counters_get(abm_world* w, abm_world_counters* out, void* stream);
 
-/* Checkpoint: the whole state as a flat byte image in host memory.
- * abm_save with buf = NULL returns the size in *bytes. abm_load restores a
- * world created with the same config. Both synchronise `stream`. */
+/* Checkpoint: the state as a flat byte image in host memory -- the counters,
+ * then per species the live flags and records of slots [0, extent), then the
+ * grass. Slots at or past a species' extent hold no agent (the extent is the
+ * high-water mark of occupied slots), so the image carries only what the
+ * state depends on and its size follows the extent, not the capacity.
+ * abm_save with buf = NULL returns the size the current state needs in
+ * *bytes; with a buffer of *bytes >= that size it writes the image and sets
+ * *bytes to its size (ABM_ERR_ARG for a smaller buffer). abm_load restores a
+ * world created with the same config from an image of `bytes` >= its size;
+ * slots at or past the image's extents come back empty (flag and record
+ * zero, as in a world that never used them). abm_image_capacity gives the
+ * largest image the world can produce (every slot below the capacity in
+ * use), a size that fits any later state. abm_save and abm_load synchronise
+ * `stream` (abm_save also to read the counters). */
 abm_status abm_save(abm_world* w, void* buf, size_t* bytes, void* stream);
 abm_status abm_load(abm_world* w, const void* buf, size_t bytes, void* stream);
+abm_status abm_image_capacity(abm_world* w, size_t* bytes);
 
 /* ========================================================================== */
 /* Batched predation: many independent models in one persistent launch        */

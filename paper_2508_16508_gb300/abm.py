@@ -136,6 +136,7 @@ def _sig(L):
         "abm_world_counters_get": ([vp, C.POINTER(abm_world_counters), vp], st),
         "abm_save": ([vp, vp, C.POINTER(C.c_size_t), vp], st),
         "abm_load": ([vp, vp, C.c_size_t, vp], st),
+        "abm_image_capacity": ([vp, C.POINTER(C.c_size_t)], st),
         "abm_batch_create": ([C.POINTER(abm_batch_model), i32, vp, pp], st),
         "abm_batch_destroy": ([vp], st),
         "abm_batch_tune": ([vp, i32, i32, i32], st),

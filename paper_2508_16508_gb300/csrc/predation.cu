@@ -701,31 +701,48 @@ extern "C" abm_status abm_world_counters_get(abm_world* w, abm_world_counters* o
   return ABM_OK;
 }
 
-// checkpoint image: [WorldCtr][active0][agent0][active1][agent1][regrow]
-static size_t image_bytes(const abm_world* w) {
+// checkpoint image: [WorldCtr][active0][agent0][active1][agent1][regrow],
+// each species' arrays cut at its extent (slots at or past the extent are
+// empty: never written, or emptied by abm_load)
+static size_t image_bytes(const abm_world* w, const WorldCtr& h) {
   size_t b = sizeof(WorldCtr);
-  for (int s = 0; s < 2; ++s) b += (size_t)w->d.sp[s].cap * (sizeof(int32_t) + sizeof(int4));
+  for (int s = 0; s < 2; ++s) b += (size_t)h.extent[s] * (sizeof(int32_t) + sizeof(int4));
   return b + (size_t)w->d.ncells * sizeof(int32_t);
+}
+
+extern "C" abm_status abm_image_capacity(abm_world* w, size_t* bytes) {
+  if (!w || !bytes) return ABM_ERR_ARG;
+  WorldCtr h;
+  std::memset(&h, 0, sizeof(h));
+  h.extent[0] = w->d.sp[0].cap;
+  h.extent[1] = w->d.sp[1].cap;
+  *bytes = image_bytes(w, h);
+  return ABM_OK;
 }
 
 extern "C" abm_status abm_save(abm_world* w, void* buf, size_t* bytes, void* stream) {
   if (!w || !bytes) return ABM_ERR_ARG;
-  const size_t need = image_bytes(w);
+  cudaStream_t st = (cudaStream_t)stream;
+  WorldCtr h;
+  ABM_CUDA_TRY(cudaMemcpyAsync(&h, w->d.ctr, sizeof(WorldCtr), cudaMemcpyDeviceToHost, st));
+  ABM_CUDA_TRY(cudaStreamSynchronize(st));
+  const size_t need = image_bytes(w, h);
   if (!buf) {
     *bytes = need;
     return ABM_OK;
   }
   if (*bytes < need) return ABM_ERR_ARG;
-  cudaStream_t st = (cudaStream_t)stream;
   char* p = (char*)buf;
-  ABM_CUDA_TRY(cudaMemcpyAsync(p, w->d.ctr, sizeof(WorldCtr), cudaMemcpyDeviceToHost, st));
+  std::memcpy(p, &h, sizeof(WorldCtr));
   p += sizeof(WorldCtr);
   for (int s = 0; s < 2; ++s) {
-    const size_t n = (size_t)w->d.sp[s].cap;
-    ABM_CUDA_TRY(cudaMemcpyAsync(p, w->d.sp[s].active, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    p += n * sizeof(int32_t);
-    ABM_CUDA_TRY(cudaMemcpyAsync(p, w->d.sp[s].agent, n * sizeof(int4), cudaMemcpyDeviceToHost, st));
-    p += n * sizeof(int4);
+    const size_t n = (size_t)h.extent[s];
+    if (n) {
+      ABM_CUDA_TRY(cudaMemcpyAsync(p, w->d.sp[s].active, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      p += n * sizeof(int32_t);
+      ABM_CUDA_TRY(cudaMemcpyAsync(p, w->d.sp[s].agent, n * sizeof(int4), cudaMemcpyDeviceToHost, st));
+      p += n * sizeof(int4);
+    }
   }
   ABM_CUDA_TRY(cudaMemcpyAsync(p, w->d.regrow, (size_t)w->d.ncells * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   ABM_CUDA_TRY(cudaStreamSynchronize(st));
@@ -742,21 +759,28 @@ __global__ void k_reset_tables(WorldDev w) {
 }
 
 extern "C" abm_status abm_load(abm_world* w, const void* buf, size_t bytes, void* stream) {
-  if (!w || !buf || bytes != image_bytes(w)) return ABM_ERR_ARG;
+  if (!w || !buf || bytes < sizeof(WorldCtr)) return ABM_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   const char* p = (const char*)buf;
   WorldCtr h;
   std::memcpy(&h, p, sizeof(h));
   for (int s = 0; s < 2; ++s)
     if (h.extent[s] < 0 || h.extent[s] > w->d.sp[s].cap) return ABM_ERR_ARG;
+  if (bytes < image_bytes(w, h)) return ABM_ERR_ARG;
   ABM_CUDA_TRY(cudaMemcpyAsync(w->d.ctr, p, sizeof(WorldCtr), cudaMemcpyHostToDevice, st));
   p += sizeof(WorldCtr);
   for (int s = 0; s < 2; ++s) {
-    const size_t n = (size_t)w->d.sp[s].cap;
-    ABM_CUDA_TRY(cudaMemcpyAsync(w->d.sp[s].active, p, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    p += n * sizeof(int32_t);
-    ABM_CUDA_TRY(cudaMemcpyAsync(w->d.sp[s].agent, p, n * sizeof(int4), cudaMemcpyHostToDevice, st));
-    p += n * sizeof(int4);
+    const size_t n = (size_t)h.extent[s], cap = (size_t)w->d.sp[s].cap;
+    if (n) {
+      ABM_CUDA_TRY(cudaMemcpyAsync(w->d.sp[s].active, p, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+      p += n * sizeof(int32_t);
+      ABM_CUDA_TRY(cudaMemcpyAsync(w->d.sp[s].agent, p, n * sizeof(int4), cudaMemcpyHostToDevice, st));
+      p += n * sizeof(int4);
+    }
+    if (n < cap) {  // past the extent: empty slots, as in a world that never used them
+      ABM_CUDA_TRY(cudaMemsetAsync(w->d.sp[s].active + n, 0, (cap - n) * sizeof(int32_t), st));
+      ABM_CUDA_TRY(cudaMemsetAsync(w->d.sp[s].agent + n, 0, (cap - n) * sizeof(int4), st));
+    }
     const int ntiles = w->cap_pad[s] / kPredTile;
     ABM_CUDA_TRY(cudaMemsetAsync(w->d.sp[s].tiles, 0, sizeof(u64) * (size_t)ntiles, st));
   }

@@ -256,14 +256,23 @@ class World:
         call("abm_load", self.h, buf, len(image), _stream(stream))
 
     def image_bytes(self) -> int:
+        """Size of the checkpoint image of the current state (slots up to the extents)."""
         n = C.c_size_t(0)
         call("abm_save", self.h, None, C.byref(n), None)
         return n.value
 
-    def save_into(self, host: torch.Tensor, stream=None):
-        """Checkpoint into a host uint8 tensor (pinned for full copy speed)."""
+    def image_capacity(self) -> int:
+        """Largest checkpoint image this world can produce (fits any later state)."""
+        n = C.c_size_t(0)
+        call("abm_image_capacity", self.h, C.byref(n))
+        return n.value
+
+    def save_into(self, host: torch.Tensor, stream=None) -> int:
+        """Checkpoint into a host uint8 tensor (pinned for full copy speed) of at
+        least image_bytes(); returns the image's size."""
         n = C.c_size_t(host.numel())
         call("abm_save", self.h, ptr(host), C.byref(n), _stream(stream))
+        return n.value
 
     def load_from(self, host: torch.Tensor, stream=None):
         """Restore from a host uint8 tensor written by save / save_into."""

@@ -160,6 +160,39 @@ def test_checkpoint_resume_bit_exact(eng):
     compare_state(b, ow, "resumed")
 
 
+def test_checkpoint_image_follows_the_extent(eng):
+    """The image holds each species' slots up to its extent: its size follows
+    the extents, a larger buffer serves for both calls, a smaller one is
+    refused, and a world that had run further than the image comes back with
+    the slots past the image's extents empty -- the same state, slot for slot,
+    as the oracle's."""
+    from paper_2508_16508_gb300 import abm
+    c = dict(workloads.PRED_SMALL)
+    a, ow = make(eng, c)
+    a.step(40)
+    ow.step(40)
+    cnt = a.counters()
+    nb = a.image_bytes()
+    cells = c["side"] * c["side"]
+    hdr = nb - sum(e * 20 for e in cnt["extent"]) - 4 * cells
+    assert 0 < hdr <= 256  # the counters
+    assert a.image_capacity() == hdr + 20 * sum(c["cap"]) + 4 * cells
+    big = torch.zeros(a.image_capacity() + 100, dtype=torch.uint8)
+    assert a.save_into(big) == nb
+    with pytest.raises(abm.AbmError):
+        a.save_into(torch.zeros(nb - 1, dtype=torch.uint8))
+    b, _ = make(eng, c)
+    b.step(90)  # further than the image: larger extents, other records
+    assert any(x > y for x, y in zip(b.counters()["extent"], cnt["extent"]))
+    with pytest.raises(abm.AbmError):
+        b.load_from(big[: nb - 1])
+    b.load_from(big)
+    compare_state(b, ow, "loaded")
+    b.step(30)
+    ow.step(30)
+    compare_state(b, ow, "resumed")
+
+
 def test_overflow_truncates_like_oracle(eng):
     params = workloads.predation_params(sheep_repro=0.5, wolf_repro=0.5, sheep_gain=6)
     c = dict(side=10, n0=(30, 10), cap=(40, 20), seed=3, model=0, params=params)
