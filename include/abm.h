@@ -375,7 +375,11 @@ typedef struct abm_step_stats {
 
 abm_status abm_create(const abm_config* cfg, void* stream, abm_world** out);
 abm_status abm_destroy(abm_world* w);
-/* Advance `nsteps` steps. stats: device abm_step_stats[nsteps] (nullable).
+/* Advance `nsteps` steps. stats: abm_step_stats[nsteps] (nullable) in memory
+ * the kernels can write: device memory, or pinned host memory mapped into the
+ * device's address space (cudaHostAlloc; with unified addressing its host
+ * pointer serves), which the host may read once the call's work on `stream`
+ * has completed -- the statistics then reach the host with no copy.
  * want_energy != 0 also fills the energy totals (one extra reduction per step). */
 abm_status abm_step(abm_world* w, int32_t nsteps, abm_step_stats* stats, int32_t want_energy,
                     void* stream);

@@ -996,9 +996,19 @@ __global__ void __launch_bounds__(kPT, MINB) k_persistent(WorldDev w, int nsteps
     grid_sync(ps.bar, w.err, bar_target);
     clk.lap(4);
   }
-  // the last step's wolf ranks and births
+  // the last step's wolf ranks and births (every warp is free: the whole CTA ranks)
   if (nsteps > 0) {
-    if (wolf_team) wolf_ranks(t - 1);
+    const int* accw = ps.acc + 4 * ((t - 1) & 1);
+    const int starved1 = book_thread() ? accw[1] : 0, eaten = book_thread() ? accw[2] : 0;
+    const int kseg1 = (((ext[1] + 127) >> 7) + (int)gridDim.x - 1) / (int)gridDim.x;  // as in the count phase
+    u32 F1, P1;
+    rank_phase<1>(w, ext[1], kseg1, F1, P1, s_red, s_pre, reinterpret_cast<u32*>(s_cell));
+    if (threadIdx.x == 0) {
+      s_wolf[0] = (int)F1;
+      s_wolf[1] = (int)P1;
+      s_wolf[2] = starved1;
+      s_wolf[3] = eaten;
+    }
     __syncthreads();
     const Births wb = wolf_counters(t - 1);
     grid_sync(ps.bar, w.err, bar_target);

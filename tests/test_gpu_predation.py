@@ -193,6 +193,24 @@ def test_checkpoint_image_follows_the_extent(eng):
     compare_state(b, ow, "resumed")
 
 
+@pytest.mark.parametrize("engine", ENGINES)
+def test_stats_into_pinned_host_memory(eng, engine):
+    """abm_step writes its statistics rows straight into pinned host memory
+    (unified addressing): the rows equal those written to device memory."""
+    from paper_2508_16508_gb300 import abm
+    c = dict(workloads.PRED_SMALL)
+    a, _ = make(eng, c, engine=engine)
+    b, _ = make(eng, c, engine=engine)
+    dev = a.new_stats(12)
+    host = torch.zeros((12, abm.STATS_WORDS), dtype=torch.int32).pin_memory()
+    for i in range(12):  # one call per step, as an end-to-end loop makes them
+        a.step(1, dev[i:i + 1])
+        b.step(1, host[i:i + 1])
+    torch.cuda.synchronize()
+    assert torch.equal(dev.cpu(), host)
+    assert eng.decode_stats(host)[11]["step"] == 11
+
+
 def test_overflow_truncates_like_oracle(eng):
     params = workloads.predation_params(sheep_repro=0.5, wolf_repro=0.5, sheep_gain=6)
     c = dict(side=10, n0=(30, 10), cap=(40, 20), seed=3, model=0, params=params)
