@@ -409,9 +409,12 @@ def batched_leg(torch, engine, capacity, autotune, abm, hbm_peak, n_models=None,
     out["fixed"] = {"ms": t_fixed, "agent_steps_per_s": agents / (t_fixed * 1e-3),
                     "slots": info["slots"], "live_flag_sweep_gbs": sweep_bytes / (t_fixed * 1e-3) / 1e9}
     # the same models with extent sweeps (a stronger plain baseline: placeholders past
-    # the highest slot ever used are never visited)
+    # the highest slot ever used are never visited), with the launch shape tuned for it
+    tfe = autotune.tune_batch(models, steps, abm.SWEEP_EXTENT) if tune else default
+    out["launch_fixed_extent"] = shape(tfe)
+    out["tune_trials_fixed_extent_ms"] = trials(tfe)
     b = engine.Batch(models)
-    b.tune(th, cps, models_per_cta=g)
+    b.tune(tfe["threads"], tfe["ctas_per_sm"], models_per_cta=tfe.get("models_per_cta", 1))
     e0.record()
     b.run(steps, sweep=abm.SWEEP_EXTENT)
     e1.record()
@@ -453,9 +456,12 @@ def batched_leg(torch, engine, capacity, autotune, abm, hbm_peak, n_models=None,
                       "peak_sum": int(hw.sum()),
                       "wasted_capacity": (int(learned.sum()) - int(hw.sum())) / int(hw.sum())}
     # learned capacities (memory) with extent sweeps (work): compared with the
-    # extent-sweep fixed run, the fair plain baseline for it
-    res = capacity.run_learned(models, learned, fixed, steps, sweep=abm.SWEEP_EXTENT, threads=tl["threads"],
-                               ctas_per_sm=tl["ctas_per_sm"], models_per_cta=tl.get("models_per_cta", 1))
+    # extent-sweep fixed run, the fair plain baseline for it; its own tuned shape
+    tle = autotune.tune_batch(lmodels, steps, abm.SWEEP_EXTENT) if tune else default
+    out["launch_learned_extent"] = shape(tle)
+    out["tune_trials_learned_extent_ms"] = trials(tle)
+    res = capacity.run_learned(models, learned, fixed, steps, sweep=abm.SWEEP_EXTENT, threads=tle["threads"],
+                               ctas_per_sm=tle["ctas_per_sm"], models_per_cta=tle.get("models_per_cta", 1))
     t_le = res["ms_learned"] + res["ms_rerun"] + t_mlp
     out["learned_extent_sweep"] = {"ms": t_le, "ms_run": res["ms_learned"], "ms_rerun": res["ms_rerun"],
                                    "agent_steps_per_s": agents / (t_le * 1e-3),
