@@ -291,19 +291,22 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_count_fused(ScanArg
       for (int j = 0; j < kLaneSlots; ++j)
         if (base + j < a.n) ml |= (u32)(s.active[base + j] != 0) << j;
     }
-    u32 ma = 0, mb = 0, mr = 0;
+    // the draws' outcomes as 16-bit masks (bit j: slot base + j), combined
+    // with the live mask once per 16 slots
+    u32 dr = 0, dc = 0;
 #pragma unroll
     for (int m = 0; m < kLaneSlots / 2; ++m) {
       const int slot = base + 2 * m;
       // slots 2j and 2j+1 share draw j: words (x, y) and (z, w) = (remove, choose)
       const uint4 u = philox_rk(make_uint4(a.step, (u32)slot >> 1, ABM_P_MASK, 0u), a.rk);
-      const u32 l0 = (ml >> (2 * m)) & 1u, l1 = (ml >> (2 * m + 1)) & 1u;
-      const u32 rm0 = l0 & (u32)(u.x < a.threshold), rm1 = l1 & (u32)(u.z < a.threshold);
-      const u32 al0 = l0 & ~rm0, al1 = l1 & ~rm1;
-      ma |= ((u32)(slot < a.n && !al0) | ((u32)(slot + 1 < a.n && !al1) << 1)) << (2 * m);
-      mb |= ((al0 & (u32)(u.y < a.threshold)) | ((al1 & (u32)(u.w < a.threshold)) << 1)) << (2 * m);
-      mr |= (rm0 | (rm1 << 1)) << (2 * m);
+      dr |= (u.x < a.threshold ? 1u << (2 * m) : 0u) | (u.z < a.threshold ? 2u << (2 * m) : 0u);
+      dc |= (u.y < a.threshold ? 1u << (2 * m) : 0u) | (u.w < a.threshold ? 2u << (2 * m) : 0u);
     }
+    const u32 valid = base + kLaneSlots <= a.n ? 0xFFFFu : (base < a.n ? (1u << (a.n - base)) - 1u : 0u);
+    const u32 mr = ml & dr;         // removed: live and drawn
+    const u32 al = ml & ~dr;        // still live
+    const u32 ma = valid & ~al;     // free after the removals
+    const u32 mb = al & dc;         // chosen among the live
     const u32 nl = ml & ~mr;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
