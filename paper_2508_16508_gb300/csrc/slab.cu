@@ -400,6 +400,20 @@ __global__ void __launch_bounds__(THREADS, MOVE ? (768 / THREADS > 0 ? 768 / THR
   griddep_wait();
   const SlabDev& s = a.s;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int seg = a.chunk / WARPS;
+  const int wlo = blockIdx.x * a.chunk + warp * seg;
+  const int whi = min(a.n, wlo + seg);
+  // the plane words of the warp's first step, requested ahead of the prefix
+  // sums; each step then requests the next step's words before its own work,
+  // so a warp waits for one round trip in all, not one per step
+  u32 wa_next = 0, wb_next = 0;
+  {
+    const int base = wlo + lane * kLaneSlots;
+    if (wlo < whi && base < a.n) {
+      wa_next = a.planeA[base >> 5];
+      if (OP == OP_FUSED) wb_next = a.planeB[base >> 5];
+    }
+  }
   u32 pa = 0, pb = 0, ta = 0, tb = 0;
   for (int j = threadIdx.x; j < a.G; j += THREADS) {
     const u32 x = a.totals[2 * j], y = a.totals[2 * j + 1];
@@ -430,15 +444,21 @@ __global__ void __launch_bounds__(THREADS, MOVE ? (768 / THREADS > 0 ? 768 / THR
   // ranks land at list_a + *list_base (the permutation's second half)
   int32_t* const list_a = a.list_a + (OP == OP_SELECT && a.list_base ? *a.list_base : 0);
   int* const stage = s_stage + warp * kWarpStep;
-  const int seg = a.chunk / WARPS;
-  const int wlo = blockIdx.x * a.chunk + warp * seg;
-  const int whi = min(a.n, wlo + seg);
   for (int b0 = wlo; b0 < whi; b0 += kWarpStep) {
     const int base = b0 + lane * kLaneSlots;
+    const u32 wa = wa_next, wb = wb_next;
+    {
+      const int nbase = base + kWarpStep;
+      wa_next = wb_next = 0;
+      if (b0 + kWarpStep < whi && nbase < a.n) {
+        wa_next = a.planeA[nbase >> 5];
+        if (OP == OP_FUSED) wb_next = a.planeB[nbase >> 5];
+      }
+    }
     u32 ma = 0, mb = 0;
     if (base < a.n) {
-      ma = (a.planeA[base >> 5] >> (16 * (lane & 1))) & 0xFFFFu;
-      if (OP == OP_FUSED) mb = (a.planeB[base >> 5] >> (16 * (lane & 1))) & 0xFFFFu;
+      ma = (wa >> (16 * (lane & 1))) & 0xFFFFu;
+      if (OP == OP_FUSED) mb = (wb >> (16 * (lane & 1))) & 0xFFFFu;
     }
     const u32 c = (u32)__popc(ma) | ((u32)__popc(mb) << 16);
     u32 inc = c;
