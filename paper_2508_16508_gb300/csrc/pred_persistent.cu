@@ -964,7 +964,7 @@ __global__ void __launch_bounds__(kPT, MINB) k_persistent(WorldDev w, int nsteps
     p_move<1, kPWarps>(w, t, ext[1], cl, carried, mf);
     grid_wait(ps.bar, w.err, bar_target);
     clk.lap(2);
-    // ---- P4 (same phase): sheep births (every CTA's lists are complete); sheep counters
+    // ---- P4: sheep births (every CTA's lists are complete: the split barrier's wait); sheep counters
     int starved0 = 0, grass = 0;
     if (book_thread()) {  // written in P2: loaded ahead of the births' own loads
       starved0 = acc[0];
