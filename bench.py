@@ -373,21 +373,23 @@ def batched_leg(torch, engine, capacity, autotune, abm, hbm_peak, n_models=None,
     fixed = workloads.fixed_caps(tab["side"])[:n_models]
     models = [dict(side=int(tab["side"][i]), seed=B["philox_seed"], model=i, params=tab["params"][i],
                    cap=fixed[i], n0=tab["n0"][i]) for i in range(n_models)]
-    default = {"threads": 512, "ctas_per_sm": 2, "models_per_cta": 1}
+    default = {"threads": 512, "ctas_per_sm": 2, "models_per_cta": 1, "agents_per_thread": 16}
     tf = autotune.tune_batch(models, steps, abm.SWEEP_CAPACITY) if tune else default
-    th, cps, g = tf["threads"], tf["ctas_per_sm"], tf.get("models_per_cta", 1)
-    trials = lambda tt: [[x["threads"], x["ctas_per_sm"], x.get("models_per_cta", 1), round(x["ms"], 2)]  # noqa: E731
+    th, cps, g, apt = tf["threads"], tf["ctas_per_sm"], tf.get("models_per_cta", 1), tf.get("agents_per_thread", 16)
+    trials = lambda tt: [[x["threads"], x["ctas_per_sm"], x.get("models_per_cta", 1),  # noqa: E731
+                          x.get("agents_per_thread", 16), round(x["ms"], 2)]
                          for x in tt.get("trials", [])]
     shape = lambda tt: (f"{tt['threads']} threads x {tt['ctas_per_sm']} CTAs/SM x {tt.get('models_per_cta', 1)} "  # noqa: E731
-                        f"models/CTA" + (" (autotuned)" if tune else ""))
+                        f"models/CTA x {tt.get('agents_per_thread', 16)} slots/thread"
+                        + (" (autotuned)" if tune else ""))
     out = {"workload": B["name"] if n_models == B["n_models"] and steps == B["steps"]
            else f"{n_models} models of {B['name']}, {steps} steps",
            "models": n_models, "steps": steps,
            "launch_fixed": shape(tf),
-           "tune_trials_fixed_ms": trials(tf), "tune_trial_columns": ["threads", "ctas_per_sm", "models_per_cta", "ms"]}
+           "tune_trials_fixed_ms": trials(tf), "tune_trial_columns": ["threads", "ctas_per_sm", "models_per_cta", "agents_per_thread", "ms"]}
     # plain fixed capacity (one persistent launch for all 500 steps)
     b = engine.Batch(models)
-    b.tune(th, cps, models_per_cta=g)
+    b.tune(th, cps, models_per_cta=g, agents_per_thread=apt)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     b.run(steps, sweep=abm.SWEEP_CAPACITY)
@@ -414,7 +416,8 @@ def batched_leg(torch, engine, capacity, autotune, abm, hbm_peak, n_models=None,
     out["launch_fixed_extent"] = shape(tfe)
     out["tune_trials_fixed_extent_ms"] = trials(tfe)
     b = engine.Batch(models)
-    b.tune(tfe["threads"], tfe["ctas_per_sm"], models_per_cta=tfe.get("models_per_cta", 1))
+    b.tune(tfe["threads"], tfe["ctas_per_sm"], models_per_cta=tfe.get("models_per_cta", 1),
+           agents_per_thread=tfe.get("agents_per_thread", 16))
     e0.record()
     b.run(steps, sweep=abm.SWEEP_EXTENT)
     e1.record()
@@ -440,7 +443,8 @@ def batched_leg(torch, engine, capacity, autotune, abm, hbm_peak, n_models=None,
     out["launch_learned"] = shape(tl)
     out["tune_trials_learned_ms"] = trials(tl)
     res = capacity.run_learned(models, learned, fixed, steps, threads=tl["threads"], ctas_per_sm=tl["ctas_per_sm"],
-                               models_per_cta=tl.get("models_per_cta", 1))
+                               models_per_cta=tl.get("models_per_cta", 1),
+                               agents_per_thread=tl.get("agents_per_thread", 16))
     t_learned = res["ms_learned"] + res["ms_rerun"] + t_mlp
     out["_digest_learned"] = res["digest"]
     n_over = np.array([max(c["overflow"]) for c in res["counters"]])
@@ -461,7 +465,8 @@ def batched_leg(torch, engine, capacity, autotune, abm, hbm_peak, n_models=None,
     out["launch_learned_extent"] = shape(tle)
     out["tune_trials_learned_extent_ms"] = trials(tle)
     res = capacity.run_learned(models, learned, fixed, steps, sweep=abm.SWEEP_EXTENT, threads=tle["threads"],
-                               ctas_per_sm=tle["ctas_per_sm"], models_per_cta=tle.get("models_per_cta", 1))
+                               ctas_per_sm=tle["ctas_per_sm"], models_per_cta=tle.get("models_per_cta", 1),
+                               agents_per_thread=tle.get("agents_per_thread", 16))
     t_le = res["ms_learned"] + res["ms_rerun"] + t_mlp
     out["learned_extent_sweep"] = {"ms": t_le, "ms_run": res["ms_learned"], "ms_rerun": res["ms_rerun"],
                                    "agent_steps_per_s": agents / (t_le * 1e-3),

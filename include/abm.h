@@ -526,6 +526,13 @@ abm_status abm_batch_tune(abm_batch* b, int32_t threads, int32_t ctas_per_sm, in
  * otherwise; abm_batch_tune resets it to 1 when a new CTA size would break
  * that). Results never depend on it. Host only. */
 abm_status abm_batch_models_per_cta(abm_batch* b, int32_t models_per_cta);
+/* Launch shape: agent slots per thread in each chunk of the per-species
+ * sweeps (8, 16 or 32, default 16; 32 only with at most 512 threads per CTA,
+ * ABM_ERR_ARG otherwise, and abm_batch_tune resets it to 16 when a larger CTA
+ * is chosen): a group of T threads reads the live flags of
+ * agents_per_thread * T slots (128-bit loads), lists the live ones and shares
+ * them out, chunk by chunk. Results never depend on it. Host only. */
+abm_status abm_batch_agents_per_thread(abm_batch* b, int32_t agents_per_thread);
 /* Advance every model by nsteps (asynchronous on `stream`). */
 abm_status abm_batch_run(abm_batch* b, int32_t nsteps, int32_t sweep, void* stream);
 /* Host copy of every model's counters (out: host abm_batch_counters[n]; synchronises `stream`). */

@@ -160,6 +160,7 @@ def _sig(L):
         "abm_batch_digest": ([vp, vp, vp], st),
         "abm_batch_capacity": ([vp, i32, vp], st),
         "abm_batch_models_per_cta": ([vp, i32], st),
+        "abm_batch_agents_per_thread": ([vp, i32], st),
         "abm_batch_rerun_overflowed": ([vp, vp, i32, vp, vp, vp], st),
         "abm_digest": ([vp, vp, vp], st),
         "abm_world_slab": ([vp, i32, pp, vp], st),

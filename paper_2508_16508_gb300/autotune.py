@@ -62,7 +62,7 @@ def _time(fn) -> float:
 
 def tune_batch(models: list, steps: int, sweep: int, trial_steps: int | None = None, rounds: int = 1,
                use_cache: bool = True, **_ignored) -> dict:
-    """Pick (threads, ctas_per_sm, models_per_cta) for a batch of models. By default every
+    """Pick (threads, ctas_per_sm, models_per_cta, agents_per_thread) for a batch of models. By default every
     candidate runs the whole batch for all `steps` from the initial state, so
     each times exactly the work it will be chosen for (populations change a
     lot over a run, so a short slice of it misjudges the shapes); a smaller
@@ -71,39 +71,44 @@ def tune_batch(models: list, steps: int, sweep: int, trial_steps: int | None = N
     sig = {"n": len(models), "steps": steps, "sweep": sweep,
            "sides": np.histogram([m["side"] for m in models], bins=8)[0].tolist(),
            "cap": int(sum(int(m["cap"][0]) + int(m["cap"][1]) for m in models))}
-    key = _key("batch2", sig)
+    key = _key("batch3", sig)
     if use_cache:
         hit = _load().get(key)
         if hit:
             return hit
     # shapes whose CTAs can all be resident at 64 registers per thread: CTA
-    # size, CTAs per SM, models per CTA (groups of at least 128 threads)
-    cands = [(256, 1, 1), (256, 2, 1), (256, 4, 1), (512, 1, 1), (512, 2, 1), (1024, 1, 1),
-             (256, 4, 2), (512, 2, 2), (512, 2, 4), (1024, 1, 2), (1024, 1, 4)]
+    # size, CTAs per SM, models per CTA (groups of at least 128 threads), agent
+    # slots per thread in a sweep chunk (16 everywhere; 8 and 32 on the shapes
+    # that came closest with 16; 32 needs at most 512 threads)
+    cands = [(256, 1, 1, 16), (256, 2, 1, 16), (256, 4, 1, 16), (512, 1, 1, 16), (512, 2, 1, 16),
+             (1024, 1, 1, 16), (256, 4, 2, 16), (512, 2, 2, 16), (512, 2, 4, 16), (1024, 1, 2, 16),
+             (1024, 1, 4, 16), (512, 2, 1, 8), (1024, 1, 1, 8), (256, 4, 1, 8), (1024, 1, 2, 8),
+             (512, 2, 1, 32), (256, 4, 1, 32), (512, 2, 2, 32), (256, 4, 2, 32)]
     acc = {cnd: 0.0 for cnd in cands}
     if trial_steps is None or trial_steps >= steps:
         for _ in range(rounds):
-            for th, cps, g in cands:
+            for th, cps, g, a in cands:
                 b = engine.Batch(models)
-                b.tune(th, cps, models_per_cta=g)
-                acc[(th, cps, g)] += _time(lambda: b.run(steps, sweep=sweep))
+                b.tune(th, cps, models_per_cta=g, agents_per_thread=a)
+                acc[(th, cps, g, a)] += _time(lambda: b.run(steps, sweep=sweep))
                 b.check()
                 del b
     else:
         b = engine.Batch(models)
         b.run(2, sweep=sweep)
         for _ in range(rounds):
-            for th, cps, g in cands:
-                b.tune(th, cps, models_per_cta=g)
-                acc[(th, cps, g)] += _time(lambda: b.run(trial_steps, sweep=sweep))
+            for th, cps, g, a in cands:
+                b.tune(th, cps, models_per_cta=g, agents_per_thread=a)
+                acc[(th, cps, g, a)] += _time(lambda: b.run(trial_steps, sweep=sweep))
         b.check()
         del b
     torch.cuda.empty_cache()
-    results = sorted((ms, th, cps, g) for (th, cps, g), ms in acc.items())
-    ms, th, cps, g = results[0]
-    best = {"threads": th, "ctas_per_sm": cps, "models_per_cta": g, "steps_per_launch": max(steps, 1),
-            "trial_ms": ms,
-            "trials": [{"threads": t, "ctas_per_sm": c, "models_per_cta": gg, "ms": m} for m, t, c, gg in results],
+    results = sorted((ms, th, cps, g, a) for (th, cps, g, a), ms in acc.items())
+    ms, th, cps, g, a = results[0]
+    best = {"threads": th, "ctas_per_sm": cps, "models_per_cta": g, "agents_per_thread": a,
+            "steps_per_launch": max(steps, 1), "trial_ms": ms,
+            "trials": [{"threads": t, "ctas_per_sm": c, "models_per_cta": gg, "agents_per_thread": aa, "ms": m}
+                       for m, t, c, gg, aa in results],
             "tuned_at": time.strftime("%Y-%m-%dT%H:%M:%S")}
     _store(key, best)
     return best

@@ -172,7 +172,7 @@ def peak_counts(models: list, horizon: int, sweep: int = abm.SWEEP_EXTENT, chunk
 
 def run_learned(models: list, learned_caps: np.ndarray, fixed_caps: np.ndarray, steps: int,
                 sweep: int = abm.SWEEP_CAPACITY, threads: int = 512, ctas_per_sm: int = 2,
-                models_per_cta: int = 1) -> dict:
+                models_per_cta: int = 1, agents_per_thread: int = 16) -> dict:
     """Learned-capacity batch run: one launch at the learned capacities, then
     abm_batch_rerun_overflowed reruns every model whose slab overflowed at its
     fixed capacity and reports through the same batch. Returns the per-model
@@ -180,7 +180,7 @@ def run_learned(models: list, learned_caps: np.ndarray, fixed_caps: np.ndarray, 
     times (the rerun's includes setting up its batch)."""
     lm = [dict(m, cap=(int(c[0]), int(c[1]))) for m, c in zip(models, learned_caps)]
     b = engine.Batch(lm)
-    b.tune(threads, ctas_per_sm, models_per_cta=models_per_cta)
+    b.tune(threads, ctas_per_sm, models_per_cta=models_per_cta, agents_per_thread=agents_per_thread)
     e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
     e0.record()
     b.run(steps, sweep=sweep)

@@ -124,10 +124,10 @@ __device__ __forceinline__ void group_scan2(int g, int gt, u32 a, u32 b, u32& ex
   tot_b = (u32)tot;
 }
 
-// Live agents of a chunk of 16 * T slots, listed in shared memory (offsets
-// within the chunk, in the order of the threads' masks) so that all T threads
-// share the work whatever the chunk's density. m = the thread's 16-bit live
-// mask over slots base16[j]; returns the list's length.
+// Live agents of a chunk of A * T slots (A = slots per thread, 8, 16 or 32),
+// listed in shared memory (offsets within the chunk, in the order of the
+// threads' masks) so that all T threads share the work whatever the chunk's
+// density. m = the thread's A-bit live mask; returns the list's length.
 template <int T, int G>
 __device__ __forceinline__ int chunk_list(int g, int gt, u32 m, int first_off, int stride_off, unsigned short* s_list, u64* s_warp) {
   u32 ex, ex2, tot, tot2;
@@ -163,25 +163,26 @@ __device__ __forceinline__ void move_agent(const BatchDev& b, const MCtx& c, int
   }
 }
 
-template <int T, int G>
+template <int T, int G, int A>
 __device__ __forceinline__ void b_move(int g, int gt, const BatchDev& b, MCtx& c, int S, int sweep, int t, unsigned short* s_list,
                                        u64* s_warp, u32* s_live, int live_words) {
+  static_assert(A == 8 || A == 16 || A == 32, "slots per thread per chunk: 8, 16 or 32");
   const int32_t* act = b.active[S] + c.m.oa[S];
   const int4* ag = b.agent[S] + c.m.oa[S];
   // the sweep's live flags also go into a shared-memory bitmask (when it fits)
   // that the scan of the same species reads instead of the flags: nothing
   // changes this species' flags between its move and its scan
   const bool keep = sweep <= 32 * live_words;
-  // per chunk: four 128-bit loads of live flags per thread (int4 q0 + u*T),
+  // per chunk: A / 4 128-bit loads of live flags per thread (int4 q0 + u*T),
   // the live slots listed, then two agents in flight per thread (copying the
   // next chunk's flags into shared memory ahead, with cp.async, measured slower
   // overall: faster at full capacity, slower with extent sweeps)
-  for (int c0 = 0; c0 < sweep; c0 += 16 * T) {
+  for (int c0 = 0; c0 < sweep; c0 += A * T) {
     const int q0 = (c0 >> 2) + gt;
     const int nq = (sweep + 3) >> 2;
     u32 m = 0;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < A / 4; ++u) {
       const int q = q0 + u * T;
       const int4 a = q < nq ? reinterpret_cast<const int4*>(act)[q] : make_int4(0, 0, 0, 0);
       m |= ((u32)(a.x != 0) | ((u32)(a.y != 0) << 1) | ((u32)(a.z != 0) << 2) | ((u32)(a.w != 0) << 3)) << (4 * u);
@@ -190,7 +191,7 @@ __device__ __forceinline__ void b_move(int g, int gt, const BatchDev& b, MCtx& c
     if (keep) {
       // the nibbles of 8 neighbouring threads make one bitmask word (slots 4 (q0 + u T) .. + 32)
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < A / 4; ++u) {
         u32 v = ((m >> (4 * u)) & 0xFu) << (4 * (gt & 7));
         v |= __shfl_xor_sync(0xFFFFFFFFu, v, 1);
         v |= __shfl_xor_sync(0xFFFFFFFFu, v, 2);
@@ -263,9 +264,9 @@ __device__ __forceinline__ u32 scan_agent(const BatchDev& b, const MCtx& c, int 
 
 // eat (claim winners), select parents, kill the starving, compact the free
 // slots and the parents (ranks by block scans, chunk by chunk). Thread i holds
-// the 16 contiguous slots 16 i.. of a chunk for the ranks; the live agents of
+// the A contiguous slots A i.. of a chunk for the ranks; the live agents of
 // the chunk are listed and shared by all threads.
-template <int T, int G>
+template <int T, int G, int A>
 __device__ __forceinline__ void b_scan(int g, int gt, const BatchDev& b, MCtx& c, int S, int sweep, int t, u64* s_warp,
                                        int* s_acc, unsigned short* s_list, u32* s_par, const u32* s_live,
                                        int live_words) {
@@ -276,30 +277,31 @@ __device__ __forceinline__ void b_scan(int g, int gt, const BatchDev& b, MCtx& c
   const bool kept = sweep <= 32 * live_words;  // the move left this sweep's flags in s_live
   int starved = 0, won = 0;
   u32 pf = 0, pp = 0;
-  for (int c0 = 0; c0 < sweep; c0 += 16 * T) {
-    const int base = c0 + 16 * gt;
+  constexpr u32 kMaskA = A == 32 ? 0xFFFFFFFFu : (1u << (A & 31)) - 1u;
+  for (int c0 = 0; c0 < sweep; c0 += A * T) {
+    const int base = c0 + A * gt;
     u32 m = 0, valid = 0;
     if (kept) {
-      if (base < sweep) m = (s_live[base >> 5] >> (base & 16)) & 0xFFFFu;
+      if (base < sweep) m = (s_live[base >> 5] >> (base & 31)) & kMaskA;
     } else {
 #pragma unroll
-      for (int v = 0; v < 4; ++v) {
+      for (int v = 0; v < A / 4; ++v) {
         int4 q = make_int4(0, 0, 0, 0);
         if (base + 4 * v < sweep) q = reinterpret_cast<const int4*>(act)[(base >> 2) + v];
         m |= ((u32)(q.x != 0) | ((u32)(q.y != 0) << 1) | ((u32)(q.z != 0) << 2) | ((u32)(q.w != 0) << 3)) << (4 * v);
       }
     }
 #pragma unroll
-    for (int j = 0; j < 16; ++j) valid |= (u32)(base + j < sweep) << j;
+    for (int j = 0; j < A; ++j) valid |= (u32)(base + j < sweep) << j;
     m &= valid;
     const u32 fr = ~m & valid;
     // a chunk without live agents whose free slots all rank past the free-list
     // bound only adds to the free count
     if ((int)pf >= bound && !gsync_or<G>(g, T, m != 0)) {
-      pf += (u32)min(16 * T, sweep - c0);
+      pf += (u32)min(A * T, sweep - c0);
       continue;
     }
-    const int tot = chunk_list<T, G>(g, gt, m, 16 * gt, 1, s_list, s_warp);
+    const int tot = chunk_list<T, G>(g, gt, m, A * gt, 1, s_list, s_warp);
     for (int e = gt; e < tot; e += T) {
       const int off = s_list[e];
       const u32 r = scan_agent<T, G>(b, c, S, t, c0 + off);
@@ -308,10 +310,10 @@ __device__ __forceinline__ void b_scan(int g, int gt, const BatchDev& b, MCtx& c
       won += (r >> 2) & 1u;
     }
     gsync<G>(g, T);
-    u32 par = (s_par[gt >> 1] >> (16 * (gt & 1))) & 0xFFFFu;
+    u32 par = (s_par[(A * gt) >> 5] >> ((A * gt) & 31)) & kMaskA;
     u32 ex_f, ex_p, tot_f, tot_p;
     group_scan2<T, G>(g, gt, __popc(fr), __popc(par), ex_f, ex_p, tot_f, tot_p, s_warp);
-    if (!(gt & 1)) s_par[gt >> 1] = 0u;  // both halves were read before the scan's barrier
+    if (((A * gt) & 31) == 0) s_par[(A * gt) >> 5] = 0u;  // the word's parts were read before the scan's barrier
     u32 rf = pf + ex_f, rp = pp + ex_p;
     u32 frm = fr;
     while (frm) {
@@ -386,8 +388,9 @@ __device__ __forceinline__ void b_count_births(const BatchDev& b, MCtx& c, int S
   if (c.P[S] > avail) c.overflow[S] = 1;
 }
 
-// N threads per CTA, G models per CTA (groups of N / G threads)
-template <int N, int G>
+// N threads per CTA, G models per CTA (groups of N / G threads), A slots per
+// thread in a chunk of the sweeps
+template <int N, int G, int A>
 __global__ void __launch_bounds__(N, (1024 / N > 0 ? 1024 / N : 1)) k_batch_run(BatchDev b, int nsteps, int sweep_extent,
                                                                         int live_words) {
   constexpr int T = N / G;
@@ -396,8 +399,8 @@ __global__ void __launch_bounds__(N, (1024 / N > 0 ? 1024 / N : 1)) k_batch_run(
   __shared__ u64 s_warp_all[G][T / 32 + 1];
   __shared__ int s_acc_all[G][4];
   __shared__ int s_idx_all[G];
-  __shared__ unsigned short s_list_all[G][16 * T];  // live agents of a chunk
-  __shared__ u32 s_par_all[G][16 * T / 32];         // parent bits of a chunk
+  __shared__ unsigned short s_list_all[G][A * T];  // live agents of a chunk
+  __shared__ u32 s_par_all[G][A * T / 32];         // parent bits of a chunk
   const int g = (int)threadIdx.x / T, gt = (int)threadIdx.x % T;
   MCtx& c = s_c[g];
   u64* s_warp = s_warp_all[g];
@@ -406,7 +409,7 @@ __global__ void __launch_bounds__(N, (1024 / N > 0 ? 1024 / N : 1)) k_batch_run(
   unsigned short* s_list = s_list_all[g];
   u32* s_par = s_par_all[g];
   u32* s_live = s_live_all + (size_t)g * live_words;
-  if (gt < 16 * T / 32) s_par[gt] = 0u;
+  if (gt < A * T / 32) s_par[gt] = 0u;
   while (true) {
     gsync<G>(g, T);
     if (gt == 0) s_idx = (int)atomicAdd(&b.ctrl[0], 1u);
@@ -439,9 +442,9 @@ __global__ void __launch_bounds__(N, (1024 / N > 0 ? 1024 / N : 1)) k_batch_run(
       const int sw0 = sweep_extent ? c.extent[0] : c.m.cap[0];
       gsync<G>(g, T);
       // sheep: move + grass claims; eat, select, die, compact
-      b_move<T, G>(g, gt, b, c, 0, sw0, t, s_list, s_warp, s_live, live_words);
+      b_move<T, G, A>(g, gt, b, c, 0, sw0, t, s_list, s_warp, s_live, live_words);
       gsync<G>(g, T);
-      b_scan<T, G>(g, gt, b, c, 0, sw0, t, s_warp, s_acc, s_list, s_par, s_live, live_words);
+      b_scan<T, G, A>(g, gt, b, c, 0, sw0, t, s_warp, s_acc, s_list, s_par, s_live, live_words);
       gsync<G>(g, T);
       const int avail0 = c.F[0] + (sweep_extent ? c.m.cap[0] - c.extent[0] : 0);
       const int r0 = min(c.P[0], avail0);
@@ -450,7 +453,7 @@ __global__ void __launch_bounds__(N, (1024 / N > 0 ? 1024 / N : 1)) k_batch_run(
       // claim only needs the cell to hold a live sheep; every newborn lamb
       // sits with its live parent)
       b_births<T, G>(g, gt, b, c, 0, r0, t);
-      b_move<T, G>(g, gt, b, c, 1, sw1, t, s_list, s_warp, s_live, live_words);
+      b_move<T, G, A>(g, gt, b, c, 1, sw1, t, s_list, s_warp, s_live, live_words);
       gsync<G>(g, T);
       if (gt == 0) {
         b_count_births(b, c, 0, r0, s_acc[0], avail0);
@@ -459,7 +462,7 @@ __global__ void __launch_bounds__(N, (1024 / N > 0 ? 1024 / N : 1)) k_batch_run(
         s_acc[0] = s_acc[1] = 0;
       }
       gsync<G>(g, T);
-      b_scan<T, G>(g, gt, b, c, 1, sw1, t, s_warp, s_acc, s_list, s_par, s_live, live_words);
+      b_scan<T, G, A>(g, gt, b, c, 1, sw1, t, s_warp, s_acc, s_list, s_par, s_live, live_words);
       gsync<G>(g, T);
       const int avail1 = c.F[1] + (sweep_extent ? c.m.cap[1] - c.extent[1] : 0);
       const int r1 = min(c.P[1], avail1);
@@ -617,7 +620,7 @@ struct abm_batch {
   BModel* models_dev;
   std::vector<BModel> models;
   long long slots[2], cells;
-  int threads, ctas_per_sm, steps_per_launch, models_per_cta;
+  int threads, ctas_per_sm, steps_per_launch, models_per_cta, agents_per_thread;
   // fixed-capacity rerun of the models whose slabs overflowed (abm_batch_rerun_overflowed)
   abm_batch* rerun;
   std::vector<int> rerun_of;  // per model: its index in `rerun`, or -1
@@ -746,6 +749,7 @@ extern "C" abm_status abm_batch_create(const abm_batch_model* models, int32_t n,
   b->ctas_per_sm = 4;
   b->steps_per_launch = 1 << 30;
   b->models_per_cta = 1;
+  b->agents_per_thread = 16;
   *out = b;
   return ABM_OK;
 }
@@ -758,6 +762,7 @@ extern "C" abm_status abm_batch_tune(abm_batch* b, int32_t threads, int32_t ctas
   b->ctas_per_sm = ctas_per_sm;
   b->steps_per_launch = steps_per_launch;
   if (threads / b->models_per_cta < 128) b->models_per_cta = 1;
+  if (threads > 512 && b->agents_per_thread == 32) b->agents_per_thread = 16;
   return ABM_OK;
 }
 
@@ -765,7 +770,7 @@ extern "C" abm_status abm_batch_tune(abm_batch* b, int32_t threads, int32_t ctas
 // dynamic shared memory (G live-flag bitmasks) is set per device, raised when
 // a batch needs more; the bitmasks shrink (their models then read their flags
 // twice) when the CTA's shared memory is short.
-template <int N, int GG>
+template <int N, int GG, int A>
 static abm_status batch_launch(const BatchDev& d, int grid, int nsteps, int ext, int live_words, cudaStream_t st) {
   static std::atomic<int> limit_set[64];
   static std::atomic<int> max_dyn[64];
@@ -777,22 +782,59 @@ static abm_status batch_launch(const BatchDev& d, int grid, int nsteps, int ext,
     int optin = 0;
     cudaFuncAttributes fa;
     ABM_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    ABM_CUDA_TRY(cudaFuncGetAttributes(&fa, k_batch_run<N, GG>));
+    ABM_CUDA_TRY(cudaFuncGetAttributes(&fa, k_batch_run<N, GG, A>));
     maxd = std::max(0, optin - (int)fa.sharedSizeBytes);
     if (cache) max_dyn[dev].store(maxd, std::memory_order_relaxed);
   }
   while (live_words > 0 && sizeof(u32) * (size_t)live_words * GG > (size_t)maxd) live_words /= 2;
   const int smem = (int)(sizeof(u32) * (size_t)live_words * GG);
   if (!cache || limit_set[dev].load(std::memory_order_acquire) < smem) {
-    ABM_CUDA_TRY(cudaFuncSetAttribute(k_batch_run<N, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    ABM_CUDA_TRY(cudaFuncSetAttribute(k_batch_run<N, GG, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     if (cache) {
       int cur = limit_set[dev].load(std::memory_order_relaxed);
       while (cur < smem && !limit_set[dev].compare_exchange_weak(cur, smem)) {
       }
     }
   }
-  k_batch_run<N, GG><<<grid, N, smem, st>>>(d, nsteps, ext, live_words);
+  k_batch_run<N, GG, A><<<grid, N, smem, st>>>(d, nsteps, ext, live_words);
   ABM_LAUNCH_CHECK();
+  return ABM_OK;
+}
+
+// the launch shapes instantiated: (threads, models per CTA) for A slots per
+// thread (32 slots only up to 512 threads: a chunk's list must fit the CTA's
+// static shared memory)
+template <int A>
+static abm_status batch_shape(const abm_batch* b, int grid, int s, int ext, int live_words, cudaStream_t st) {
+  if constexpr (A == 32) {
+    switch (b->threads * 10 + b->models_per_cta) {
+      case 1281: return batch_launch<128, 1, A>(b->d, grid, s, ext, live_words, st);
+      case 2561: return batch_launch<256, 1, A>(b->d, grid, s, ext, live_words, st);
+      case 2562: return batch_launch<256, 2, A>(b->d, grid, s, ext, live_words, st);
+      case 5121: return batch_launch<512, 1, A>(b->d, grid, s, ext, live_words, st);
+      case 5122: return batch_launch<512, 2, A>(b->d, grid, s, ext, live_words, st);
+      case 5124: return batch_launch<512, 4, A>(b->d, grid, s, ext, live_words, st);
+      default: return ABM_ERR_ARG;
+    }
+  } else {
+    switch (b->threads * 10 + b->models_per_cta) {
+      case 1281: return batch_launch<128, 1, A>(b->d, grid, s, ext, live_words, st);
+      case 2561: return batch_launch<256, 1, A>(b->d, grid, s, ext, live_words, st);
+      case 2562: return batch_launch<256, 2, A>(b->d, grid, s, ext, live_words, st);
+      case 5121: return batch_launch<512, 1, A>(b->d, grid, s, ext, live_words, st);
+      case 5122: return batch_launch<512, 2, A>(b->d, grid, s, ext, live_words, st);
+      case 5124: return batch_launch<512, 4, A>(b->d, grid, s, ext, live_words, st);
+      case 10242: return batch_launch<1024, 2, A>(b->d, grid, s, ext, live_words, st);
+      case 10244: return batch_launch<1024, 4, A>(b->d, grid, s, ext, live_words, st);
+      default: return batch_launch<1024, 1, A>(b->d, grid, s, ext, live_words, st);
+    }
+  }
+}
+
+extern "C" abm_status abm_batch_agents_per_thread(abm_batch* b, int32_t agents_per_thread) {
+  if (!b || (agents_per_thread != 8 && agents_per_thread != 16 && agents_per_thread != 32)) return ABM_ERR_ARG;
+  if (agents_per_thread == 32 && b->threads > 512) return ABM_ERR_ARG;
+  b->agents_per_thread = agents_per_thread;
   return ABM_OK;
 }
 
@@ -818,18 +860,9 @@ extern "C" abm_status abm_batch_run(abm_batch* b, int32_t nsteps, int32_t sweep,
   live_words = std::min(live_words, kBatchLiveWordsMax / G);
   for (int done = 0; done < nsteps;) {
     const int s = std::min(nsteps - done, b->steps_per_launch);
-    abm_status e;
-    switch (b->threads * 10 + G) {
-      case 1281: e = batch_launch<128, 1>(b->d, grid, s, ext, live_words, st); break;
-      case 2561: e = batch_launch<256, 1>(b->d, grid, s, ext, live_words, st); break;
-      case 2562: e = batch_launch<256, 2>(b->d, grid, s, ext, live_words, st); break;
-      case 5121: e = batch_launch<512, 1>(b->d, grid, s, ext, live_words, st); break;
-      case 5122: e = batch_launch<512, 2>(b->d, grid, s, ext, live_words, st); break;
-      case 5124: e = batch_launch<512, 4>(b->d, grid, s, ext, live_words, st); break;
-      case 10242: e = batch_launch<1024, 2>(b->d, grid, s, ext, live_words, st); break;
-      case 10244: e = batch_launch<1024, 4>(b->d, grid, s, ext, live_words, st); break;
-      default: e = batch_launch<1024, 1>(b->d, grid, s, ext, live_words, st); break;
-    }
+    const abm_status e = b->agents_per_thread == 8    ? batch_shape<8>(b, grid, s, ext, live_words, st)
+                         : b->agents_per_thread == 32 ? batch_shape<32>(b, grid, s, ext, live_words, st)
+                                                      : batch_shape<16>(b, grid, s, ext, live_words, st);
     if (e != ABM_OK) return e;
     ABM_LAUNCH_CHECK();
     done += s;
@@ -989,6 +1022,7 @@ extern "C" abm_status abm_batch_rerun_overflowed(abm_batch* b, const int32_t* ca
   r->ctas_per_sm = b->ctas_per_sm;
   r->steps_per_launch = b->steps_per_launch;
   r->models_per_cta = b->models_per_cta;
+  r->agents_per_thread = b->agents_per_thread;
   e = abm_batch_run(r, steps, sweep, stream);
   const int nr = (int)rm.size();
   if (e == ABM_OK && (cudaMalloc(&b->rerun_idx, sizeof(int32_t) * (size_t)nr) != cudaSuccess ||

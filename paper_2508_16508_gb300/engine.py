@@ -367,9 +367,11 @@ class Batch:
         except Exception:
             pass
 
-    def tune(self, threads: int, ctas_per_sm: int, steps_per_launch: int = 1 << 30, models_per_cta: int = 1):
+    def tune(self, threads: int, ctas_per_sm: int, steps_per_launch: int = 1 << 30, models_per_cta: int = 1,
+             agents_per_thread: int = 16):
         call("abm_batch_tune", self.h, threads, ctas_per_sm, steps_per_launch)
         call("abm_batch_models_per_cta", self.h, models_per_cta)
+        call("abm_batch_agents_per_thread", self.h, agents_per_thread)
 
     def run(self, nsteps: int, sweep: int = abm.SWEEP_CAPACITY, stream=None):
         call("abm_batch_run", self.h, nsteps, sweep, _stream(stream))

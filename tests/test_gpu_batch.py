@@ -54,12 +54,17 @@ def compare_model(b, m, ow, where):
 
 
 @pytest.mark.parametrize("sweep", [0, 1])
-@pytest.mark.parametrize("threads,spl,mpc", [(256, 1 << 30, 1), (128, 7, 1), (512, 13, 1), (256, 11, 2), (512, 1 << 30, 4),
-                                             (1024, 9, 2), (1024, 1 << 30, 4), (512, 17, 2)])
-def test_random_batch_vs_oracle(eng, sweep, threads, spl, mpc):
-    models = random_models(20, 100 + threads + sweep + 7 * mpc)
+@pytest.mark.parametrize("threads,spl,mpc,apt", [(256, 1 << 30, 1, 16), (128, 7, 1, 16), (512, 13, 1, 16),
+                                                 (256, 11, 2, 16), (512, 1 << 30, 4, 16), (1024, 9, 2, 16),
+                                                 (1024, 1 << 30, 4, 16), (512, 17, 2, 16), (256, 1 << 30, 1, 8),
+                                                 (128, 7, 1, 8), (1024, 9, 2, 8), (512, 17, 4, 8),
+                                                 (512, 1 << 30, 1, 32), (256, 13, 2, 32), (128, 5, 1, 32)])
+def test_random_batch_vs_oracle(eng, sweep, threads, spl, mpc, apt):
+    """Every launch shape (CTA size, steps per launch, models per CTA, slots
+    per thread in a sweep chunk) gives the oracle's models."""
+    models = random_models(20, 100 + threads + sweep + 7 * mpc + apt)
     b = eng.Batch(models)
-    b.tune(threads, 2 if threads < 1024 else 1, spl, models_per_cta=mpc)
+    b.tune(threads, 2 if threads < 1024 else 1, spl, models_per_cta=mpc, agents_per_thread=apt)
     b.run(45, sweep=sweep)
     cnt = b.counters()
     for m, md in enumerate(models):
