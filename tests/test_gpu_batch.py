@@ -151,3 +151,28 @@ def test_sampler_models_full_horizon(eng, sweep):
         for k in ("n_active", "next_id", "hw", "overflow", "step"):
             assert cnt[m][k] == oc[k], (pick[m], k, cnt[m][k], oc[k])
         assert cnt[m]["agent_steps"] == agents
+
+
+def test_batch_run_replays_from_a_cuda_graph(eng):
+    """A batch run's launches can be captured in a CUDA graph and replayed: the
+    model queue resets itself at the end of every launch, so three replays of a
+    captured 10-step launch give the same models as 30 eager steps."""
+    models = random_models(12, 4242)
+    a = eng.Batch(models)
+    a.tune(256, 2, 10)
+    a.run(30)
+    warm = eng.Batch(models)  # the launch shape's first use (attributes) outside the capture
+    warm.tune(256, 2, 10)
+    warm.run(10)
+    torch.cuda.synchronize()
+    b = eng.Batch(models)
+    b.tune(256, 2, 10)
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        b.run(10, stream=s)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(a.digest(), b.digest())
+    assert [c["step"] for c in b.counters()] == [30] * len(models)
