@@ -868,8 +868,9 @@ def run_ours(args, rank, world, local):
              "P4_sheep_births", "P5_wolf_eat_select", "closing_wolf_ranks"))}
         line["phases_us_per_step"]["same_trajectory"] = pw.counters() == gw.counters()
         del pw
-        # end to end through the public API: one abm_step per step, then the
-        # step's statistics read back to pinned host memory
+        # end to end through the public API: the state loaded from host memory,
+        # one abm_step per step with its statistics row written into pinned host
+        # memory, the final state saved to host memory
         ew = engine.World(c["side"], c["seed"], c["model"] + rank, c["params"], c["cap"], c["n0"])
         ew.tune(tw["engine"], tw["ctas_per_sm"])
         ne = K
