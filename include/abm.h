@@ -466,8 +466,9 @@ abm_status abm_world_counters_get(abm_world* w, abm_world_counters* out, void* s
 /* Checkpoint: the state as a flat byte image in host memory -- the counters,
  * then per species the live flags and records of slots [0, extent), then the
  * grass. Slots at or past a species' extent hold no agent (the extent is the
- * high-water mark of occupied slots), so the image carries only what the
- * state depends on and its size follows the extent, not the capacity.
+ * high-water mark of occupied slots; edits made through abm_world_slab count
+ * once abm_world_slab_commit has folded them back), so the image carries only
+ * what the state depends on and its size follows the extent, not the capacity.
  * abm_save with buf = NULL returns the size the current state needs in
  * *bytes; with a buffer of *bytes >= that size it writes the image and sets
  * *bytes to its size (ABM_ERR_ARG for a smaller buffer). abm_load restores a
