@@ -91,6 +91,7 @@ struct ScanArgs {
   int use_rec_idx;         // OP_UPDATE with a record mask
   u32 step, threshold;     // OP_FUSED
   u32 rk[20];              // OP_FUSED: Philox round keys of the slab's key (seed, model), round r at 2r, 2r+1
+  u32 mk[5];               // OP_FUSED: the call's mask draws' constant parts (mask_pair_consts)
   int32_t* list_a;         // slots by rank: selected / free (caller's out_idx or scratch)
   int32_t* list_b;         // slots by rank: chosen (fused call)
   int32_t* out_count;      // device outputs (nullable)
@@ -257,6 +258,51 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_count(ScanArgs a) {
   }
 }
 
+// The selective-update call's mask draws are Philox4x32-10 blocks on the
+// counter (step, j, MASK, 0), j = slot >> 1: only the second word varies
+// within a call, so the first round, one multiply of the second and one of
+// the third depend on the call alone. mask_pair_consts works them out on the
+// host (round r: (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1,
+// lo(M0 c0)), M0 = 0xD2511F53, M1 = 0xCD9E8D57, round keys k = rk); the
+// device finishes the block from them. Same outputs as philox_rk.
+static void mask_pair_consts(u32 step, const u32 (&rk)[20], u32 (&mk)[5]) {
+  const auto wide = [](u32 m, u32 x, u32& hi, u32& lo) {
+    const uint64_t p = (uint64_t)m * (uint64_t)x;
+    hi = (u32)(p >> 32);
+    lo = (u32)p;
+  };
+  u32 h0, l0, h1, l1;
+  // round 0 on (step, j, MASK, 0) -> (A ^ j, B, C, D)
+  wide(0xD2511F53u, step, h0, l0);
+  wide(0xCD9E8D57u, (u32)ABM_P_MASK, h1, l1);
+  const u32 A = h1 ^ rk[0], B = l1, C = h0 ^ 0u ^ rk[1], D = l0;
+  // round 1: the third word C is constant -> (E, F, hi(M0 (A ^ j)) ^ G, lo(M0 (A ^ j)))
+  wide(0xCD9E8D57u, C, h1, l1);
+  const u32 E = h1 ^ B ^ rk[2], F = l1, G = D ^ rk[3];
+  // round 2: the first word E is constant -> (hi(M1 z) ^ H, lo(M1 z), I ^ w, J)
+  wide(0xD2511F53u, E, h0, l0);
+  mk[0] = A;
+  mk[1] = G;
+  mk[2] = F ^ rk[4];  // H
+  mk[3] = h0 ^ rk[5];  // I
+  mk[4] = l0;          // J
+}
+
+__device__ __forceinline__ uint4 mask_pair_draw(u32 j, const u32 (&mk)[5], const u32 (&rk)[20]) {
+  const u32 x = mk[0] ^ j;                                         // round 0
+  const u32 a_lo = 0xD2511F53u * x, a_hi = __umulhi(0xD2511F53u, x);  // round 1
+  const u32 z = a_hi ^ mk[1];
+  const u32 b_lo = 0xCD9E8D57u * z, b_hi = __umulhi(0xCD9E8D57u, z);  // round 2
+  uint4 c = make_uint4(b_hi ^ mk[2], b_lo, mk[3] ^ a_lo, mk[4]);
+#pragma unroll
+  for (int r = 3; r < 10; ++r) {
+    const u32 p0_lo = 0xD2511F53u * c.x, p0_hi = __umulhi(0xD2511F53u, c.x);
+    const u32 p1_lo = 0xCD9E8D57u * c.z, p1_hi = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(p1_hi ^ c.y ^ rk[2 * r], p1_lo, p0_hi ^ c.w ^ rk[2 * r + 1], p0_lo);
+  }
+  return c;
+}
+
 // Pass 1 of the selective-update call: as k_count, with the live flags as a
 // 16-bit mask per lane (any nonzero flag is live) read by two 32-byte loads
 // and written back as 0/1 in whole 8-slot (32-byte) groups; the lane's eight
@@ -298,7 +344,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_count_fused(ScanArg
     for (int m = 0; m < kLaneSlots / 2; ++m) {
       const int slot = base + 2 * m;
       // slots 2j and 2j+1 share draw j: words (x, y) and (z, w) = (remove, choose)
-      const uint4 u = philox_rk(make_uint4(a.step, (u32)slot >> 1, ABM_P_MASK, 0u), a.rk);
+      const uint4 u = mask_pair_draw((u32)slot >> 1, a.mk, a.rk);
       dr |= (u.x < a.threshold ? 1u << (2 * m) : 0u) | (u.z < a.threshold ? 2u << (2 * m) : 0u);
       dc |= (u.y < a.threshold ? 1u << (2 * m) : 0u) | (u.w < a.threshold ? 2u << (2 * m) : 0u);
     }
@@ -1210,6 +1256,7 @@ extern "C" abm_status abm_selective_update(abm_slab* s, uint32_t step, uint32_t 
   if (!s || k < 0 || (k > 0 && (!records || !deltas))) return ABM_ERR_ARG;
   ScanArgs a = base_args(s);
   philox_round_keys(s->d.seed, s->d.model, a.rk);
+  mask_pair_consts(step, a.rk, a.mk);
   a.rec = records;
   a.rec2 = deltas;
   a.k = k;
